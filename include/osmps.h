@@ -1,0 +1,243 @@
+/*
+ * osmps.h -- C ABI of the GB300 two-site variational ground-state search.
+ *
+ * The operations follow "Open source Matrix Product States" (arXiv 1703.00387):
+ * the effective Hamiltonian of Sec. 3.4 (Fig. LanczosMPS), its lowest
+ * eigenpair by Lanczos, the eigendecomposition split of Sec. 2
+ * (Eq. AAD_ULLUD, Eq. ThetaAL) with the truncation rule of Eq. elocal, and the
+ * sweeps of Sec. 3.4.
+ *
+ * Conventions (all tensors real float64, row-major, contiguous):
+ *   MPS site tensor      A[a, s, b]        (chi_l, d, chi_r)            Eq. mps
+ *   MPO site tensor      W[w, t, s, w2]    (w_left, d, d, w_right)      Eq. mpo / Eq. MPOdef
+ *                        t = outgoing (bra) physical index, s = incoming (ket);
+ *                        W[w,:,:,w2] is the operator in row w, column w2 of M^[k].
+ *                        Lower-triangular channel order: the left environment's
+ *                        last channel and the right environment's first channel
+ *                        are the identity channels.
+ *   Environments         L[a2, w, a], R[b2, w, b]: first index bra, last ket.
+ *   Two-site tensor      theta[a, s1, s2, c]  (chi_l, d1, d2, chi_r)
+ *
+ * Memory: every pointer argument named as a tensor is a DEVICE pointer owned
+ * by the caller, unless the comment says "host". The caller keeps it alive
+ * until the stream has been synchronised. Scalars returned through "host"
+ * pointers are written after the call synchronises its stream.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream). Calls are asynchronous on it unless they return host values.
+ *
+ * Errors: every call returns an osmps_status, never aborts and never prints.
+ * osmps_last_error() returns a message for the calling thread's last failure.
+ * No call falls back to the CPU: a missing GPU or a CUDA error is reported.
+ */
+#ifndef OSMPS_H
+#define OSMPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OSMPS_OK = 0,
+  OSMPS_EINVAL = 1,   /* null pointer, aliasing output, bad enum value     */
+  OSMPS_ESHAPE = 2,   /* inconsistent or non-positive dimensions            */
+  OSMPS_ENOMEM = 3,   /* device allocation failed                           */
+  OSMPS_ECUDA = 4,    /* a CUDA / cuSOLVER call failed                      */
+  OSMPS_ENOCONV = 5,  /* Lanczos hit max_iter above tol (best pair written) */
+  OSMPS_ETIMEOUT = 6, /* a bounded device wait gave up                      */
+  OSMPS_ENAN = 7,     /* non-finite value detected                          */
+  OSMPS_EUNSUPPORTED = 8
+} osmps_status;
+
+/* Arithmetic of the contractions (H_eff.theta and the environment updates).
+ * Lanczos orthogonalisation, the tridiagonal eigensolve, the Gram matrix and
+ * its eigendecomposition, and energies are always float64.               */
+typedef enum {
+  OSMPS_PREC_FP64 = 0,   /* plain float64 on CUDA cores / DMMA                       */
+  OSMPS_PREC_BF16X3 = 1, /* tcgen05 bf16 tensor cores, hi+lo split, 3 products, f32 acc */
+  OSMPS_PREC_TF32X3 = 2  /* tcgen05 tf32 tensor cores, hi+lo split, 3 products, f32 acc */
+} osmps_precision;
+
+typedef struct osmps_ctx osmps_ctx;
+
+const char* osmps_last_error(void);
+const char* osmps_status_string(osmps_status s);
+
+/* Create a context on `device` (makes it current for the calling thread).
+ * ws_bytes: initial device workspace; the context grows it on demand.
+ * Owns the workspace, a cuSOLVER handle and a device error flag.            */
+osmps_status osmps_ctx_create(int device, size_t ws_bytes, osmps_ctx** out);
+osmps_status osmps_ctx_destroy(osmps_ctx* ctx);
+/* Bytes of device memory currently held by the context's workspace.         */
+size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx);
+
+/* H_eff . theta (Sec. 3.4, Fig. LanczosMPS: L, M^[k], M^[k+1] and R contracted
+ * step by step with theta instead of forming the (chi^2 d^2)^2 matrix):
+ *   y[a2,t1,t2,c2] = sum L[a2,w,a] W1[w,t1,s1,w1] W2[w1,t2,s2,w2] R[c2,w2,c] theta[a,s1,s2,c]
+ * L: (chi_l, wl, chi_l); W1: (wl, d1, d1, wm); W2: (wm, d2, d2, wr);
+ * R: (chi_r, wr, chi_r); theta, y: (chi_l, d1, d2, chi_r).
+ * y must not alias theta (EINVAL). Scratch comes from the context workspace. */
+osmps_status osmps_heff_apply(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                              const double* R, const double* theta, double* y, int64_t chi_l,
+                              int64_t d1, int64_t d2, int64_t chi_r, int64_t wl, int64_t wm,
+                              int64_t wr, int precision, void* stream);
+
+/* Environment update (Sec. 3.4: the fixed sites are contracted into L and R
+ * one site at a time).
+ * side 0 (grow L past site k):
+ *   env_out[b2,w2,b] = sum A[a2,t,b2] env_in[a2,w,a] W[w,t,s,w2] A[a,s,b]
+ *   env_in: (chi_l, w_in, chi_l), W: (w_in, d, d, w_out), env_out: (chi_r, w_out, chi_r)
+ * side 1 (grow R past site k):
+ *   env_out[a2,w,a] = sum A[a2,t,b2] W[w,t,s,w2] env_in[b2,w2,b] A[a,s,b]
+ *   env_in: (chi_r, w_in, chi_r), W: (w_out, d, d, w_in), env_out: (chi_l, w_out, chi_l)
+ * A: (chi_l, d, chi_r).                                                      */
+osmps_status osmps_env_update(osmps_ctx* ctx, int side, const double* env_in, const double* A,
+                              const double* W, double* env_out, int64_t chi_l, int64_t d,
+                              int64_t chi_r, int64_t w_in, int64_t w_out, int precision,
+                              void* stream);
+
+/* Lowest eigenpair of H_eff (Sec. 3.4) by Lanczos with full float64
+ * reorthogonalisation, starting from theta_inout (normalised internally).
+ * Stops when the residual estimate beta_j |s_j| <= tol, after max_iter
+ * matrix-vector products (1 <= max_iter <= 512), or when the Krylov space is
+ * exhausted. On return theta_inout holds the normalised Ritz vector.
+ * energy_out, iters_out, resid_out: host pointers (resid_out may be NULL).
+ * Returns ENOCONV when max_iter was reached above tol (the best pair is still
+ * written). Synchronises `stream`.                                          */
+osmps_status osmps_lanczos_ground(osmps_ctx* ctx, const double* L, const double* W1,
+                                  const double* W2, const double* R, double* theta_inout,
+                                  int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r,
+                                  int64_t wl, int64_t wm, int64_t wr, int max_iter, double tol,
+                                  int precision, double* energy_out, int* iters_out,
+                                  double* resid_out, void* stream);
+
+/* Two-site tensor (Sec. 2, "Contractions"): theta[a,s1,s2,c] = sum_b A1[a,s1,b] A2[b,s2,c].
+ * A1: (chi_l, d1, chi_m), A2: (chi_m, d2, chi_r), theta: (chi_l, d1, d2, chi_r). */
+osmps_status osmps_theta_form(osmps_ctx* ctx, const double* A1, const double* A2, double* theta,
+                              int64_t chi_l, int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
+                              void* stream);
+
+/* Split theta with truncation by the eigendecomposition route (Sec. 2,
+ * Eq. AAD_ULLUD and Eq. ThetaAL), Gram matrix and eigensolver in float64.
+ * move_right = 1: G = M M^T with M = theta as (chi_l d1) x (d2 chi_r);
+ *   A1 = kept eigenvectors (left-canonical), A2 = U^T M renormalised.
+ * move_right = 0: G = M^T M; A2 = V^T (right-canonical), A1 = M V renormalised.
+ * Kept number chi' = min(chi_max, smallest n >= 1 with sum_{i>=n} lambda_i^2
+ * <= eps_local), lambda^2 normalised to sum 1 (Eq. elocal; Sec. 3.4).
+ * A1 must hold chi_l*d1*min(chi_max, chi_l*d1, d2*chi_r) doubles and A2
+ * min(...)*d2*chi_r; they are written with the actual chi'.
+ * Host outputs: chi_new_out, discarded_out (sum of dropped lambda^2),
+ * entropy_out (-sum lambda'^2 log lambda'^2 over kept, renormalised values),
+ * lam2_out (optional host array of min(chi_l d1, d2 chi_r) values,
+ * descending). Synchronises `stream`.                                       */
+osmps_status osmps_split(osmps_ctx* ctx, const double* theta, double* A1, double* A2,
+                         int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r, int move_right,
+                         int64_t chi_max, double eps_local, int64_t* chi_new_out,
+                         double* discarded_out, double* entropy_out, double* lam2_out,
+                         void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Whole-chain handles and sweeps (Sec. 3.4).
+ * ------------------------------------------------------------------------- */
+typedef struct osmps_mps osmps_mps;
+typedef struct osmps_mpo osmps_mpo;
+
+/* MPS with L sites, physical dims d[L] and a bond-dimension cap chi_cap used to
+ * size the device storage. host_tensors[k] points to a HOST array of
+ * chi[k]*d[k]*chi[k+1] doubles (chi has L+1 entries, chi[0] = chi[L] = 1).
+ * The tensors are copied to the device. No canonical form is assumed.      */
+osmps_status osmps_mps_create(osmps_ctx* ctx, int64_t L, const int64_t* d, const int64_t* chi,
+                              const double* const* host_tensors, int64_t chi_cap,
+                              osmps_mps** out);
+osmps_status osmps_mps_destroy(osmps_mps* mps);
+/* Current bond dimensions (host array of L+1 entries).                     */
+osmps_status osmps_mps_bond_dims(const osmps_mps* mps, int64_t* chi_out);
+/* Copy site k to a HOST buffer of at least chi[k]*d[k]*chi[k+1] doubles.    */
+osmps_status osmps_mps_get_tensor(const osmps_mps* mps, int64_t k, double* host_out);
+/* Device pointer of site k (valid until the next sweep or destroy).        */
+const double* osmps_mps_device_tensor(const osmps_mps* mps, int64_t k);
+
+/* MPO with L sites; host_W[k] is a HOST array of w[k]*d[k]*d[k]*w[k+1]
+ * doubles (w has L+1 entries, w[0] = w[L] = 1).                             */
+osmps_status osmps_mpo_create(osmps_ctx* ctx, int64_t L, const int64_t* d, const int64_t* w,
+                              const double* const* host_W, osmps_mpo** out);
+osmps_status osmps_mpo_destroy(osmps_mpo* mpo);
+
+typedef struct {
+  int64_t chi_max;        /* maximal bond dimension                                  */
+  double eps_local;       /* truncation tolerance (<0: 1e-12 / (4 L), Sec. 3.4)    */
+  double lanczos_tol;     /* residual tolerance of each Lanczos solve              */
+  int lanczos_max_iter;   /* Lanczos cap per step (paper default 100)              */
+  int n_sweeps;           /* number of full L->R->L sweeps                          */
+  int precision;          /* osmps_precision of the contractions                   */
+  int refine_sweeps;      /* extra float64 sweeps after n_sweeps                    */
+} osmps_sweep_params;
+
+typedef struct {
+  double energy;             /* final <psi|H|psi>, evaluated in float64                */
+  double last_step_energy;   /* Lanczos eigenvalue of the last step                    */
+  double max_discarded;      /* largest discarded weight of any split                  */
+  double entropy_center;     /* bond entropy at the centre bond (last visit)           */
+  int64_t max_chi;           /* largest bond dimension reached                         */
+  int64_t steps;             /* two-site steps performed                               */
+  int64_t lanczos_iters;     /* total matrix-vector products                           */
+  int64_t nonconverged;      /* steps whose Lanczos stopped at max_iter above tol      */
+  double seconds;            /* wall time of the call                                  */
+  double* step_energies;     /* optional HOST array (caller-owned) of length
+                                2 (L-1) (n_sweeps + refine_sweeps), or NULL          */
+  int64_t* step_iters;       /* optional HOST array, same length, or NULL              */
+} osmps_sweep_stats;
+
+/* Bring `mps` to mixed-canonical form with the orthogonality centre at
+ * site `center` (0 <= center < L-1) by QR shifts (Sec. 2 "Shifting", Eq. oc),
+ * normalise it, and build the left environments of sites < center and the
+ * right environments of sites > center+1 for `mpo` (contractions in
+ * `precision`). Afterwards osmps_sweep_step may run at pair (center,
+ * center+1). Synchronises `stream`.                                         */
+osmps_status osmps_mps_canonicalize(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo,
+                                    int64_t center, int precision, void* stream);
+
+typedef struct {
+  double energy;     /* Lanczos eigenvalue of H_eff (precision of the contractions) */
+  double resid;      /* Lanczos residual estimate                                   */
+  double discarded;  /* discarded weight of the split                               */
+  double entropy;    /* bond entropy of the kept, renormalised spectrum             */
+  int64_t chi_new;   /* new bond dimension between the two sites                   */
+  int iters;         /* matrix-vector products used                                 */
+  int converged;     /* 1 if the Lanczos residual met the tolerance                 */
+} osmps_step_stats;
+
+/* One two-site step at the pair (k, k+1) (Sec. 3.4): theta = A_k A_{k+1},
+ * Lanczos on H_eff (params->lanczos_tol / lanczos_max_iter / precision), the
+ * eigendecomposition split with truncation (params->chi_max, eps_local), and
+ * the environment update on the side the centre leaves: move_right = 1 grows
+ * L to site k+1 (centre moves to k+1), 0 grows R to site k (centre stays at k).
+ * Requires the centre at k or k+1 with environments in place (after
+ * osmps_mps_canonicalize or a previous step). out: host pointer or NULL.
+ * Synchronises `stream` (the new bond dimension is decided on the host).   */
+osmps_status osmps_sweep_step(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo, int64_t k,
+                              int move_right, const osmps_sweep_params* params,
+                              osmps_step_stats* out, void* stream);
+
+/* Run two-site sweeps on `mps` in place: right-canonicalise it (QR shifts,
+ * Sec. 2), build the right environments, then for every sweep optimise the
+ * pairs (0,1)...(L-2,L-1) left to right and back (2 (L-1) steps per sweep):
+ * theta formation, Lanczos, split with truncation, environment update.
+ * Finally the energy is evaluated in float64 by contracting <psi|H|psi>.
+ * stats is a host pointer (may be NULL). Synchronises `stream`.            */
+osmps_status osmps_sweep(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo,
+                         const osmps_sweep_params* params, osmps_sweep_stats* stats,
+                         void* stream);
+
+/* <psi|H|psi> / <psi|psi> in float64 for the MPS as it stands (host result). */
+osmps_status osmps_energy(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo* mpo,
+                          double* energy_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSMPS_H */

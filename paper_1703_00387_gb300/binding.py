@@ -1,0 +1,323 @@
+"""Thin ctypes binding of libosmps (C ABI in include/osmps.h).
+
+Functions keep the C names. Device tensors are torch float64 CUDA tensors
+(contiguous); dimensions are read from their shapes, and every call is
+argument marshalling only: the arithmetic runs in the library's kernels.
+There is no fallback: if the library is missing or a call fails, an
+``OsmpsError`` is raised.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libosmps.so")
+
+PRECISION = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+STATUS = {0: "OSMPS_OK", 1: "OSMPS_EINVAL", 2: "OSMPS_ESHAPE", 3: "OSMPS_ENOMEM", 4: "OSMPS_ECUDA",
+          5: "OSMPS_ENOCONV", 6: "OSMPS_ETIMEOUT", 7: "OSMPS_ENAN", 8: "OSMPS_EUNSUPPORTED"}
+ENOCONV = 5
+
+_c = ctypes
+_i64 = _c.c_int64
+_vp = _c.c_void_p
+_dp = _c.POINTER(_c.c_double)
+
+
+class OsmpsError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class SweepParams(_c.Structure):
+    _fields_ = [("chi_max", _i64), ("eps_local", _c.c_double), ("lanczos_tol", _c.c_double),
+                ("lanczos_max_iter", _c.c_int), ("n_sweeps", _c.c_int), ("precision", _c.c_int),
+                ("refine_sweeps", _c.c_int)]
+
+
+class SweepStats(_c.Structure):
+    _fields_ = [("energy", _c.c_double), ("last_step_energy", _c.c_double),
+                ("max_discarded", _c.c_double), ("entropy_center", _c.c_double),
+                ("max_chi", _i64), ("steps", _i64), ("lanczos_iters", _i64),
+                ("nonconverged", _i64), ("seconds", _c.c_double),
+                ("step_energies", _dp), ("step_iters", _c.POINTER(_i64))]
+
+
+class StepStats(_c.Structure):
+    _fields_ = [("energy", _c.c_double), ("resid", _c.c_double), ("discarded", _c.c_double),
+                ("entropy", _c.c_double), ("chi_new", _i64), ("iters", _c.c_int),
+                ("converged", _c.c_int)]
+
+
+_LIB = None
+
+_SIGS = {
+    "osmps_last_error": (_c.c_char_p, []),
+    "osmps_status_string": (_c.c_char_p, [_c.c_int]),
+    "osmps_ctx_create": (_c.c_int, [_c.c_int, _c.c_size_t, _c.POINTER(_vp)]),
+    "osmps_ctx_destroy": (_c.c_int, [_vp]),
+    "osmps_ctx_workspace_bytes": (_c.c_size_t, [_vp]),
+    "osmps_heff_apply": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 + [_c.c_int, _vp]),
+    "osmps_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_c.c_int, _vp]),
+    "osmps_lanczos_ground": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 +
+                             [_c.c_int, _c.c_double, _c.c_int, _dp, _c.POINTER(_c.c_int), _dp, _vp]),
+    "osmps_theta_form": (_c.c_int, [_vp, _vp, _vp, _vp] + [_i64] * 5 + [_vp]),
+    "osmps_split": (_c.c_int, [_vp, _vp, _vp, _vp] + [_i64] * 4 +
+                    [_c.c_int, _i64, _c.c_double, _c.POINTER(_i64), _dp, _dp, _dp, _vp]),
+    "osmps_mps_create": (_c.c_int, [_vp, _i64, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_dp),
+                                    _i64, _c.POINTER(_vp)]),
+    "osmps_mps_destroy": (_c.c_int, [_vp]),
+    "osmps_mps_bond_dims": (_c.c_int, [_vp, _c.POINTER(_i64)]),
+    "osmps_mps_get_tensor": (_c.c_int, [_vp, _i64, _dp]),
+    "osmps_mps_device_tensor": (_vp, [_vp, _i64]),
+    "osmps_mpo_create": (_c.c_int, [_vp, _i64, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_dp),
+                                    _c.POINTER(_vp)]),
+    "osmps_mpo_destroy": (_c.c_int, [_vp]),
+    "osmps_mps_canonicalize": (_c.c_int, [_vp, _vp, _vp, _i64, _c.c_int, _vp]),
+    "osmps_sweep_step": (_c.c_int, [_vp, _vp, _vp, _i64, _c.c_int, _c.POINTER(SweepParams),
+                                    _c.POINTER(StepStats), _vp]),
+    "osmps_sweep": (_c.c_int, [_vp, _vp, _vp, _c.POINTER(SweepParams), _c.POINTER(SweepStats), _vp]),
+    "osmps_energy": (_c.c_int, [_vp, _vp, _vp, _dp, _vp]),
+}
+
+
+def lib():
+    """Load libosmps.so (built in-tree by ``build.build()``); raise if absent."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise OsmpsError(4, f"{LIB_PATH} is missing: build it with paper_1703_00387_gb300.build")
+        handle = _c.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = handle
+    return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status, allow=()):
+    if status != 0 and status not in allow:
+        raise OsmpsError(status, lib().osmps_last_error().decode(errors="replace"))
+    return status
+
+
+def _prec(p):
+    return PRECISION[p] if isinstance(p, str) else int(p)
+
+
+def _dev(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return _vp(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+class Context:
+    """Owns an osmps_ctx (workspace, cuSOLVER handle, error flags) on one device."""
+
+    def __init__(self, device=0, ws_bytes=0):
+        self.ptr = _vp()
+        _check(lib().osmps_ctx_create(int(device), int(ws_bytes), _c.byref(self.ptr)))
+        self.device = device
+
+    def workspace_bytes(self):
+        return int(lib().osmps_ctx_workspace_bytes(self.ptr))
+
+    def close(self):
+        if self.ptr:
+            lib().osmps_ctx_destroy(self.ptr)
+            self.ptr = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def osmps_heff_apply(ctx, L, W1, W2, R, theta, y, precision="bf16x3", stream=None):
+    chi_l, d1, d2, chi_r = theta.shape
+    wl, wm, wr = W1.shape[0], W1.shape[3], W2.shape[3]
+    _check(lib().osmps_heff_apply(ctx.ptr, _dev(L, "L"), _dev(W1, "W1"), _dev(W2, "W2"),
+                                  _dev(R, "R"), _dev(theta, "theta"), _dev(y, "y"), chi_l, d1, d2,
+                                  chi_r, wl, wm, wr, _prec(precision), _stream(stream)))
+    return y
+
+
+def osmps_env_update(ctx, side, env_in, A, W, env_out, precision="bf16x3", stream=None):
+    chi_l, d, chi_r = A.shape
+    if side == 0:
+        w_in, w_out = W.shape[0], W.shape[3]
+    else:
+        w_in, w_out = W.shape[3], W.shape[0]
+    _check(lib().osmps_env_update(ctx.ptr, int(side), _dev(env_in, "env_in"), _dev(A, "A"),
+                                  _dev(W, "W"), _dev(env_out, "env_out"), chi_l, d, chi_r, w_in,
+                                  w_out, _prec(precision), _stream(stream)))
+    return env_out
+
+
+def osmps_lanczos_ground(ctx, L, W1, W2, R, theta, max_iter=100, tol=1e-12, precision="fp64",
+                         stream=None, allow_noconv=True):
+    """Returns (energy, iterations, residual estimate, converged)."""
+    chi_l, d1, d2, chi_r = theta.shape
+    wl, wm, wr = W1.shape[0], W1.shape[3], W2.shape[3]
+    e = _c.c_double()
+    it = _c.c_int()
+    res = _c.c_double()
+    st = lib().osmps_lanczos_ground(ctx.ptr, _dev(L, "L"), _dev(W1, "W1"), _dev(W2, "W2"),
+                                    _dev(R, "R"), _dev(theta, "theta"), chi_l, d1, d2, chi_r, wl,
+                                    wm, wr, int(max_iter), float(tol), _prec(precision),
+                                    _c.byref(e), _c.byref(it), _c.byref(res), _stream(stream))
+    _check(st, allow=(ENOCONV,) if allow_noconv else ())
+    return e.value, it.value, res.value, st == 0
+
+
+def osmps_theta_form(ctx, A1, A2, theta, stream=None):
+    chi_l, d1, chi_m = A1.shape
+    _, d2, chi_r = A2.shape
+    _check(lib().osmps_theta_form(ctx.ptr, _dev(A1, "A1"), _dev(A2, "A2"), _dev(theta, "theta"),
+                                  chi_l, d1, chi_m, d2, chi_r, _stream(stream)))
+    return theta
+
+
+def osmps_split(ctx, theta, A1, A2, move_right, chi_max, eps_local, stream=None):
+    """Returns (chi_new, discarded, entropy, lam2 numpy array). A1/A2 are flat
+    buffers large enough for the largest possible chi_new; reshape them to
+    (chi_l, d1, chi_new) / (chi_new, d2, chi_r)."""
+    chi_l, d1, d2, chi_r = theta.shape
+    n = min(chi_l * d1, d2 * chi_r)
+    lam2 = np.zeros(n)
+    chn = _i64()
+    disc = _c.c_double()
+    ent = _c.c_double()
+    _check(lib().osmps_split(ctx.ptr, _dev(theta, "theta"), _dev(A1, "A1"), _dev(A2, "A2"), chi_l,
+                             d1, d2, chi_r, int(move_right), int(chi_max), float(eps_local),
+                             _c.byref(chn), _c.byref(disc), _c.byref(ent),
+                             lam2.ctypes.data_as(_dp), _stream(stream)))
+    return chn.value, disc.value, ent.value, lam2
+
+
+class MPS:
+    """Device-resident MPS handle (osmps_mps)."""
+
+    def __init__(self, ctx, tensors, chi_cap):
+        tensors = [np.ascontiguousarray(t, dtype=np.float64) for t in tensors]
+        self.ctx = ctx
+        self.L = len(tensors)
+        d = (_i64 * self.L)(*[t.shape[1] for t in tensors])
+        chi = (_i64 * (self.L + 1))(*([t.shape[0] for t in tensors] + [tensors[-1].shape[2]]))
+        self._keep = tensors
+        ptrs = (_dp * self.L)(*[t.ctypes.data_as(_dp) for t in tensors])
+        self.ptr = _vp()
+        _check(lib().osmps_mps_create(ctx.ptr, self.L, d, chi, ptrs, int(chi_cap), _c.byref(self.ptr)))
+        self.d = [t.shape[1] for t in tensors]
+        self._keep = None
+
+    def bond_dims(self):
+        out = (_i64 * (self.L + 1))()
+        _check(lib().osmps_mps_bond_dims(self.ptr, out))
+        return list(out)
+
+    def tensor(self, k):
+        chi = self.bond_dims()
+        out = np.empty((chi[k], self.d[k], chi[k + 1]))
+        _check(lib().osmps_mps_get_tensor(self.ptr, int(k), out.ctypes.data_as(_dp)))
+        return out
+
+    def tensors(self):
+        return [self.tensor(k) for k in range(self.L)]
+
+    def close(self):
+        if self.ptr:
+            lib().osmps_mps_destroy(self.ptr)
+            self.ptr = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MPO:
+    """Device-resident MPO handle (osmps_mpo); W[k] has shape (w_k, d, d, w_{k+1})."""
+
+    def __init__(self, ctx, W):
+        W = [np.ascontiguousarray(x, dtype=np.float64) for x in W]
+        self.ctx = ctx
+        self.L = len(W)
+        d = (_i64 * self.L)(*[x.shape[1] for x in W])
+        w = (_i64 * (self.L + 1))(*([x.shape[0] for x in W] + [W[-1].shape[3]]))
+        ptrs = (_dp * self.L)(*[x.ctypes.data_as(_dp) for x in W])
+        self.ptr = _vp()
+        _check(lib().osmps_mpo_create(ctx.ptr, self.L, d, w, ptrs, _c.byref(self.ptr)))
+
+    def close(self):
+        if self.ptr:
+            lib().osmps_mpo_destroy(self.ptr)
+            self.ptr = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sweep_params(chi_max, n_sweeps=1, precision="fp64", eps_local=-1.0, lanczos_tol=1e-12,
+                 lanczos_max_iter=100, refine_sweeps=0):
+    return SweepParams(int(chi_max), float(eps_local), float(lanczos_tol), int(lanczos_max_iter),
+                       int(n_sweeps), _prec(precision), int(refine_sweeps))
+
+
+def osmps_mps_canonicalize(ctx, mps, mpo, center, precision="fp64", stream=None):
+    _check(lib().osmps_mps_canonicalize(ctx.ptr, mps.ptr, mpo.ptr, int(center), _prec(precision),
+                                        _stream(stream)))
+
+
+def osmps_sweep_step(ctx, mps, mpo, k, move_right, params, stream=None):
+    out = StepStats()
+    _check(lib().osmps_sweep_step(ctx.ptr, mps.ptr, mpo.ptr, int(k), int(move_right),
+                                  _c.byref(params), _c.byref(out), _stream(stream)))
+    return {f: getattr(out, f) for f, _ in StepStats._fields_}
+
+
+def osmps_sweep(ctx, mps, mpo, params, stream=None, record_steps=True):
+    stats = SweepStats()
+    nsteps = 2 * (mps.L - 1) * (params.n_sweeps + params.refine_sweeps)
+    if record_steps:
+        energies = np.zeros(max(nsteps, 1))
+        iters = np.zeros(max(nsteps, 1), dtype=np.int64)
+        stats.step_energies = energies.ctypes.data_as(_dp)
+        stats.step_iters = iters.ctypes.data_as(_c.POINTER(_i64))
+    _check(lib().osmps_sweep(ctx.ptr, mps.ptr, mpo.ptr, _c.byref(params), _c.byref(stats),
+                             _stream(stream)))
+    out = {f: getattr(stats, f) for f, _ in SweepStats._fields_ if not f.startswith("step_")}
+    if record_steps:
+        out["step_energies"] = energies[:nsteps]
+        out["step_iters"] = iters[:nsteps]
+    return out
+
+
+def osmps_energy(ctx, mps, mpo, stream=None):
+    e = _c.c_double()
+    _check(lib().osmps_energy(ctx.ptr, mps.ptr, mpo.ptr, _c.byref(e), _stream(stream)))
+    return e.value

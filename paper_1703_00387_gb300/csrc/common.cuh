@@ -1,0 +1,244 @@
+// Internal declarations shared by the translation units of libosmps.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "osmps.h"
+
+namespace osmps {
+
+// ---------------------------------------------------------------------------
+// Errors: every failing path records a message (thread-local) and returns a
+// status; nothing aborts or prints.
+// ---------------------------------------------------------------------------
+osmps_status set_error(osmps_status s, const char* fmt, ...);
+void clear_error();
+
+#define OSMPS_TRY(expr)                          \
+  do {                                           \
+    osmps_status st_ = (expr);                   \
+    if (st_ != OSMPS_OK) return st_;             \
+  } while (0)
+
+#define OSMPS_CUDA(call)                                                                 \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return ::osmps::set_error(OSMPS_ECUDA, "%s failed: %s (%s:%d)", #call,             \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);             \
+  } while (0)
+
+#define OSMPS_LAUNCH_CHECK()                                                             \
+  do {                                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess)                                                               \
+      return ::osmps::set_error(OSMPS_ECUDA, "kernel launch failed: %s (%s:%d)",         \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);             \
+  } while (0)
+
+#define OSMPS_SOLVER(call)                                                               \
+  do {                                                                                   \
+    cusolverStatus_t s_ = (call);                                                        \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                   \
+      return ::osmps::set_error(OSMPS_ECUDA, "%s failed: cusolver status %d (%s:%d)",    \
+                                #call, (int)s_, __FILE__, __LINE__);                     \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Workspace: named slots that grow on demand. A slot is owned by one code
+// path at a time; nested calls use disjoint slots. Growing a slot
+// synchronises the stream first, so earlier work on the old buffer is done.
+// ---------------------------------------------------------------------------
+enum Slot {
+  SLOT_HEFF_T1 = 0,
+  SLOT_HEFF_T2,
+  SLOT_HEFF_T3,
+  SLOT_HEFF_LOP,
+  SLOT_HEFF_ROP,
+  SLOT_HEFF_XOP,
+  SLOT_HEFF_SMALL,
+  SLOT_ENV_X,
+  SLOT_ENV_Y,
+  SLOT_ENV_OPA,
+  SLOT_ENV_OPB,
+  SLOT_ENV_MAT,
+  SLOT_LZ_BASIS,
+  SLOT_LZ_W,
+  SLOT_LZ_SCAL,
+  SLOT_LZ_PART,
+  SLOT_SPLIT_G,
+  SLOT_SPLIT_EV,
+  SLOT_SPLIT_WORK,
+  SLOT_SPLIT_TMP,
+  SLOT_QR_WORK,
+  SLOT_QR_TAU,
+  SLOT_QR_R,
+  SLOT_SWEEP_THETA,
+  SLOT_SWEEP_ENV,
+  SLOT_SWEEP_ENV2,
+  SLOT_RED,
+  SLOT_COUNT
+};
+
+struct Buffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace osmps
+
+struct osmps_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cusolverDnHandle_t solver = nullptr;
+  osmps::Buffer slots[osmps::SLOT_COUNT];
+  int* dev_flags = nullptr;      // device error flags (bit 0: bounded wait gave up)
+  int* dev_info = nullptr;       // cuSOLVER info
+  double* host_pinned = nullptr; // small pinned host staging area
+  size_t host_pinned_count = 0;
+  // Operator prepared by heff_prepare (converted L/R operands, reordered W).
+  bool heff_ready = false;
+  int heff_prec = -1;
+  int64_t heff_dims[7] = {0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace osmps {
+
+// Returns a device pointer of at least `bytes` for `slot`, growing it if
+// needed. On failure returns nullptr and records ENOMEM/ECUDA.
+void* ws_get(osmps_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, osmps_status* st);
+
+// Ensure the pinned host staging area holds `count` doubles.
+osmps_status pinned_reserve(osmps_ctx* ctx, size_t count);
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+// ---------------------------------------------------------------------------
+// Float64 strided batched GEMM: C[b] = alpha * A[b] B[b] + beta * C[b] with
+// element (m,k) of A at A[b*sab + m*sam + k*sak] (likewise B (k,n), C (m,n)).
+// ---------------------------------------------------------------------------
+struct GemmF64 {
+  int64_t M = 0, N = 0, K = 0, batch = 1;
+  const double* A = nullptr;
+  int64_t sam = 0, sak = 0, sab = 0;
+  const double* B = nullptr;
+  int64_t sbk = 0, sbn = 0, sbb = 0;
+  double* C = nullptr;
+  int64_t scm = 0, scn = 0, scb = 0;
+  double alpha = 1.0, beta = 0.0;
+};
+osmps_status gemm_f64(const GemmF64& g, cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// Split-precision tensor-core GEMM (tcgen05):
+//   C[M,N] = sum over the products (hi,hi), (hi,lo), (lo,hi) of A_p B_p^T
+// A: M rows, B: N rows, each row holds [hi(0..Kp) | lo(0..Kp)] in the operand
+// type (bf16 or tf32 in a 32-bit container), Kp a multiple of 64.
+// Output: float32 or float64, row-major with leading dimension ldc.
+// ---------------------------------------------------------------------------
+enum TcKind { TC_BF16 = 0, TC_TF32 = 1 };
+enum TcOut { TC_OUT_F32 = 0, TC_OUT_F64 = 1 };
+struct GemmTc {
+  int kind = TC_BF16;
+  int64_t M = 0, N = 0, Kp = 0;
+  const void* A = nullptr;  // row stride = 2*Kp elements
+  const void* B = nullptr;
+  void* C = nullptr;
+  int64_t ldc = 0;
+  int out = TC_OUT_F32;
+};
+osmps_status gemm_tc(osmps_ctx* ctx, const GemmTc& g, cudaStream_t stream);
+inline size_t tc_elem_bytes(int kind) { return kind == TC_BF16 ? 2 : 4; }
+
+// Split a float64 (or float32) matrix view into the hi|lo operand layout.
+// Source element (row r, col k) with r = r0*n1 + r1 (r1 < n1) lives at
+// src[r0*s0 + r1*s1 + k*sk]. Destination row r holds hi at [0,K), zeros at
+// [K,Kp), lo at [Kp, Kp+K), zeros up to 2Kp.
+struct SplitView {
+  const void* src = nullptr;
+  bool src_f32 = false;
+  int64_t rows = 0, n1 = 1, K = 0;
+  int64_t s0 = 0, s1 = 0, sk = 1;
+};
+osmps_status split_operand(const SplitView& v, int kind, void* dst, int64_t Kp, cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// Small contractions with an MPO tensor ("W-steps"): for every fiber
+// (o1, o2, c): out[o1*os1 + o2*os2 + o*ostride + c] = sum_i Mat[i][o] in[o1*is1 + o2*is2 + i*istride + c]
+// Mat is P x Q (row-major, float64, on the device).
+// ---------------------------------------------------------------------------
+struct Fiber {
+  int64_t P = 0, Q = 0;
+  int64_t n_o1 = 1, n_o2 = 1, nc = 0;
+  int64_t is1 = 0, is2 = 0, istride = 0;
+  int64_t os1 = 0, os2 = 0, ostride = 0;
+};
+osmps_status fiber_contract_f64(const Fiber& f, const double* Mat, const double* in, double* out,
+                                cudaStream_t stream);
+osmps_status fiber_contract_f32(const Fiber& f, const double* Mat, const float* in, float* out,
+                                cudaStream_t stream);
+// Same, but the output is written into a split operand: plain output offset
+// off = row*Kcols + col is stored as hi at dst[row*2Kp + col], lo at
+// dst[row*2Kp + Kp + col].
+osmps_status fiber_contract_f32_split(const Fiber& f, const double* Mat, const float* in,
+                                      void* dst, int kind, int64_t Kcols, int64_t Kp,
+                                      cudaStream_t stream);
+osmps_status zero_pad_columns(void* dst, int kind, int64_t rows, int64_t Kcols, int64_t Kp,
+                              cudaStream_t stream);
+
+// Reorder an MPO tensor for a W-step: Mat[i][o] with i and o composed from
+// the four indices of W[w,t,s,w2] (dims dw, d, d, dw2) by the given maps.
+// code selects one of the fixed orders used by the contractions.
+enum WOrder {
+  WORD_IN_W_S__OUT_T_W2 = 0,   // i = (w, s),  o = (t, w2)   [left side]
+  WORD_IN_S_W2__OUT_W_T = 1    // i = (s, w2), o = (w, t)    [right side]
+};
+osmps_status w_reorder(const double* W, int64_t dw, int64_t d, int64_t dw2, int order, double* Mat,
+                       cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// Vector primitives (float64) used by Lanczos and normalisations.
+// ---------------------------------------------------------------------------
+osmps_status vec_norm2(osmps_ctx* ctx, const double* x, int64_t n, double* dev_out, cudaStream_t s);
+osmps_status vec_scale_by_inv_sqrt(double* x, int64_t n, const double* dev_norm2, cudaStream_t s);
+osmps_status vec_scale_by_inv(double* y, const double* x, int64_t n, const double* dev_div,
+                              cudaStream_t s);
+osmps_status check_finite(osmps_ctx* ctx, const double* x, int64_t n, cudaStream_t s, bool* ok);
+
+// Internal entry points shared between translation units (no argument checks).
+osmps_status heff_apply_impl(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                             const double* R, const double* theta, double* y, int64_t chi_l,
+                             int64_t d1, int64_t d2, int64_t chi_r, int64_t wl, int64_t wm,
+                             int64_t wr, int precision, cudaStream_t stream, bool prepared);
+osmps_status heff_prepare(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                          const double* R, int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r,
+                          int64_t wl, int64_t wm, int64_t wr, int precision, cudaStream_t stream);
+osmps_status env_update_impl(osmps_ctx* ctx, int side, const double* env_in, const double* A,
+                             const double* W, double* env_out, int64_t chi_l, int64_t d,
+                             int64_t chi_r, int64_t w_in, int64_t w_out, int precision,
+                             cudaStream_t stream);
+osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                          const double* R, double* theta, int64_t chi_l, int64_t d1, int64_t d2,
+                          int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int max_iter,
+                          double tol, int precision, double* energy, int* iters, double* resid,
+                          cudaStream_t stream);
+osmps_status theta_form_impl(const double* A1, const double* A2, double* theta, int64_t chi_l,
+                             int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
+                             cudaStream_t stream);
+osmps_status split_impl(osmps_ctx* ctx, const double* theta, double* A1, double* A2,
+                        int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r, int move_right,
+                        int64_t chi_max, double eps_local, int64_t* chi_new, double* discarded,
+                        double* entropy, double* lam2_out, cudaStream_t stream);
+
+inline bool valid_precision(int p) {
+  return p == OSMPS_PREC_FP64 || p == OSMPS_PREC_BF16X3 || p == OSMPS_PREC_TF32X3;
+}
+
+}  // namespace osmps

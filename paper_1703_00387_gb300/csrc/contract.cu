@@ -1,0 +1,402 @@
+// Effective-Hamiltonian application, environment updates and theta formation.
+//
+// H_eff.theta (Sec. 3.4, Fig. LanczosMPS) is evaluated as four stages:
+//   1. T1[a2,w,s1,s2,c]  = sum_a L[a2,w,a] theta[a,s1,s2,c]          GEMM, M=chi_l*wl, K=chi_l, N=d1*d2*chi_r
+//   2. T2[a2,t1,w1,s2,c] = sum_{w,s1} T1 W1[w,t1,s1,w1]               W-step (fiber contraction)
+//   3. T3[a2,t1,t2,w2,c] = sum_{w1,s2} T2 W2[w1,t2,s2,w2]             W-step
+//   4. y[a2,t1,t2,c2]    = sum_{w2,c} T3 R[c2,w2,c]                   GEMM, M=chi_l*d1*d2, K=wr*chi_r, N=chi_r
+// With OSMPS_PREC_FP64 the GEMMs run on the float64 DMMA kernel. With the
+// split precisions they run on tcgen05 (gemm_tc): L and R are split into
+// hi|lo operands once per operator (heff_prepare), theta once per product,
+// T1/T2 are float32 and stage 3 writes T3 directly as a split operand.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace osmps {
+
+static osmps_status prepare_f64_copies(osmps_ctx* ctx, const double* L, const double* R,
+                                       int64_t chi_l, int64_t chi_r, int64_t wl, int64_t wr,
+                                       cudaStream_t stream);
+
+static int tc_kind(int precision) { return precision == OSMPS_PREC_TF32X3 ? TC_TF32 : TC_BF16; }
+
+osmps_status heff_prepare(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                          const double* R, int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r,
+                          int64_t wl, int64_t wm, int64_t wr, int precision, cudaStream_t stream) {
+  osmps_status st = OSMPS_OK;
+  ctx->heff_ready = false;
+  const int64_t P1 = wl * d1, Q1 = d1 * wm, P2 = wm * d2, Q2 = d2 * wr;
+  double* small = (double*)ws_get(ctx, SLOT_HEFF_SMALL, (P1 * Q1 + P2 * Q2) * sizeof(double), stream, &st);
+  if (!small) return st;
+  OSMPS_TRY(w_reorder(W1, wl, d1, wm, WORD_IN_W_S__OUT_T_W2, small, stream));
+  OSMPS_TRY(w_reorder(W2, wm, d2, wr, WORD_IN_W_S__OUT_T_W2, small + P1 * Q1, stream));
+  if (precision == OSMPS_PREC_FP64) {
+    OSMPS_TRY(prepare_f64_copies(ctx, L, R, chi_l, chi_r, wl, wr, stream));
+  } else {
+    const int kind = tc_kind(precision);
+    const size_t es = tc_elem_bytes(kind);
+    const int64_t Kp1 = round_up(chi_l, 64), Kp3 = round_up(wr * chi_r, 64);
+    void* lop = ws_get(ctx, SLOT_HEFF_LOP, (size_t)(chi_l * wl) * 2 * Kp1 * es, stream, &st);
+    if (!lop) return st;
+    void* rop = ws_get(ctx, SLOT_HEFF_ROP, (size_t)chi_r * 2 * Kp3 * es, stream, &st);
+    if (!rop) return st;
+    SplitView lv;
+    lv.src = L; lv.rows = chi_l * wl; lv.K = chi_l; lv.s0 = chi_l; lv.sk = 1;
+    OSMPS_TRY(split_operand(lv, kind, lop, Kp1, stream));
+    SplitView rv;
+    rv.src = R; rv.rows = chi_r; rv.K = wr * chi_r; rv.s0 = wr * chi_r; rv.sk = 1;
+    OSMPS_TRY(split_operand(rv, kind, rop, Kp3, stream));
+  }
+  ctx->heff_prec = precision;
+  const int64_t dims[7] = {chi_l, d1, d2, chi_r, wl, wm, wr};
+  for (int i = 0; i < 7; ++i) ctx->heff_dims[i] = dims[i];
+  ctx->heff_ready = true;
+  return OSMPS_OK;
+}
+
+// y = H_eff theta for the operator last passed to heff_prepare.
+static osmps_status heff_apply_prepared(osmps_ctx* ctx, const double* theta, double* y,
+                                        cudaStream_t stream) {
+  const int64_t chi_l = ctx->heff_dims[0], d1 = ctx->heff_dims[1], d2 = ctx->heff_dims[2],
+                chi_r = ctx->heff_dims[3], wl = ctx->heff_dims[4], wm = ctx->heff_dims[5],
+                wr = ctx->heff_dims[6];
+  const int precision = ctx->heff_prec;
+  osmps_status st = OSMPS_OK;
+  const int64_t N1 = d1 * d2 * chi_r;
+  const int64_t P1 = wl * d1, Q1 = d1 * wm, P2 = wm * d2, Q2 = d2 * wr;
+  const double* mat1 = (const double*)ctx->slots[SLOT_HEFF_SMALL].ptr;
+  const double* mat2 = mat1 + P1 * Q1;
+
+  Fiber f2;  // stage 2: outer (a2, s2), i = (w, s1), o = (t1, w1), inner c
+  f2.P = P1; f2.Q = Q1; f2.n_o1 = chi_l; f2.n_o2 = d2; f2.nc = chi_r;
+  f2.is1 = wl * d1 * d2 * chi_r; f2.is2 = chi_r; f2.istride = d2 * chi_r;
+  f2.os1 = d1 * wm * d2 * chi_r; f2.os2 = chi_r; f2.ostride = d2 * chi_r;
+  Fiber f3;  // stage 3: outer (a2, t1), i = (w1, s2), o = (t2, w2), inner c
+  f3.P = P2; f3.Q = Q2; f3.n_o1 = chi_l * d1; f3.n_o2 = 1; f3.nc = chi_r;
+  f3.is1 = wm * d2 * chi_r; f3.is2 = 0; f3.istride = chi_r;
+  f3.os1 = d2 * wr * chi_r; f3.os2 = 0; f3.ostride = chi_r;
+
+  if (precision == OSMPS_PREC_FP64) {
+    double* T1 = (double*)ws_get(ctx, SLOT_HEFF_T1, (size_t)(chi_l * wl) * N1 * 8, stream, &st);
+    if (!T1) return st;
+    double* T2 = (double*)ws_get(ctx, SLOT_HEFF_T2, (size_t)(chi_l * d1 * wm) * d2 * chi_r * 8, stream, &st);
+    if (!T2) return st;
+    double* T3 = (double*)ws_get(ctx, SLOT_HEFF_T3, (size_t)(chi_l * d1 * d2) * wr * chi_r * 8, stream, &st);
+    if (!T3) return st;
+    GemmF64 g1;
+    g1.M = chi_l * wl; g1.N = N1; g1.K = chi_l;
+    g1.A = (const double*)ctx->slots[SLOT_HEFF_LOP].ptr;  // float64 L kept by prepare_f64
+    g1.sam = chi_l; g1.sak = 1;
+    g1.B = theta; g1.sbk = N1; g1.sbn = 1;
+    g1.C = T1; g1.scm = N1; g1.scn = 1;
+    OSMPS_TRY(gemm_f64(g1, stream));
+    OSMPS_TRY(fiber_contract_f64(f2, mat1, T1, T2, stream));
+    OSMPS_TRY(fiber_contract_f64(f3, mat2, T2, T3, stream));
+    GemmF64 g4;
+    g4.M = chi_l * d1 * d2; g4.N = chi_r; g4.K = wr * chi_r;
+    g4.A = T3; g4.sam = wr * chi_r; g4.sak = 1;
+    g4.B = (const double*)ctx->slots[SLOT_HEFF_ROP].ptr; g4.sbk = 1; g4.sbn = wr * chi_r;
+    g4.C = y; g4.scm = chi_r; g4.scn = 1;
+    return gemm_f64(g4, stream);
+  }
+
+  const int kind = tc_kind(precision);
+  const size_t es = tc_elem_bytes(kind);
+  const int64_t Kp1 = round_up(chi_l, 64), Kp3 = round_up(wr * chi_r, 64);
+  void* xop = ws_get(ctx, SLOT_HEFF_XOP, (size_t)N1 * 2 * Kp1 * es, stream, &st);
+  if (!xop) return st;
+  float* T1 = (float*)ws_get(ctx, SLOT_HEFF_T1, (size_t)(chi_l * wl) * N1 * 4, stream, &st);
+  if (!T1) return st;
+  float* T2 = (float*)ws_get(ctx, SLOT_HEFF_T2, (size_t)(chi_l * d1 * wm) * d2 * chi_r * 4, stream, &st);
+  if (!T2) return st;
+  const int64_t M4 = chi_l * d1 * d2;
+  void* t3op = ws_get(ctx, SLOT_HEFF_T3, (size_t)M4 * 2 * Kp3 * es, stream, &st);
+  if (!t3op) return st;
+
+  SplitView xv;  // theta^T: row n = (s1,s2,c), column k = a, element theta[a*N1 + n]
+  xv.src = theta; xv.rows = N1; xv.K = chi_l; xv.s0 = 1; xv.sk = N1;
+  OSMPS_TRY(split_operand(xv, kind, xop, Kp1, stream));
+  GemmTc g1;
+  g1.kind = kind; g1.M = chi_l * wl; g1.N = N1; g1.Kp = Kp1;
+  g1.A = ctx->slots[SLOT_HEFF_LOP].ptr; g1.B = xop; g1.C = T1; g1.ldc = N1; g1.out = TC_OUT_F32;
+  OSMPS_TRY(gemm_tc(ctx, g1, stream));
+  OSMPS_TRY(fiber_contract_f32(f2, mat1, T1, T2, stream));
+  OSMPS_TRY(zero_pad_columns(t3op, kind, M4, wr * chi_r, Kp3, stream));
+  OSMPS_TRY(fiber_contract_f32_split(f3, mat2, T2, t3op, kind, wr * chi_r, Kp3, stream));
+  GemmTc g4;
+  g4.kind = kind; g4.M = M4; g4.N = chi_r; g4.Kp = Kp3;
+  g4.A = t3op; g4.B = ctx->slots[SLOT_HEFF_ROP].ptr; g4.C = y; g4.ldc = chi_r; g4.out = TC_OUT_F64;
+  return gemm_tc(ctx, g4, stream);
+}
+
+// Float64 path: keep copies of L and R in the operand slots so the prepared
+// operator does not depend on the caller's buffers staying unchanged.
+static osmps_status prepare_f64_copies(osmps_ctx* ctx, const double* L, const double* R,
+                                       int64_t chi_l, int64_t chi_r, int64_t wl, int64_t wr,
+                                       cudaStream_t stream) {
+  osmps_status st = OSMPS_OK;
+  void* lc = ws_get(ctx, SLOT_HEFF_LOP, (size_t)chi_l * wl * chi_l * 8, stream, &st);
+  if (!lc) return st;
+  void* rc = ws_get(ctx, SLOT_HEFF_ROP, (size_t)chi_r * wr * chi_r * 8, stream, &st);
+  if (!rc) return st;
+  OSMPS_CUDA(cudaMemcpyAsync(lc, L, (size_t)chi_l * wl * chi_l * 8, cudaMemcpyDeviceToDevice, stream));
+  OSMPS_CUDA(cudaMemcpyAsync(rc, R, (size_t)chi_r * wr * chi_r * 8, cudaMemcpyDeviceToDevice, stream));
+  return OSMPS_OK;
+}
+
+osmps_status heff_apply_impl(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                             const double* R, const double* theta, double* y, int64_t chi_l,
+                             int64_t d1, int64_t d2, int64_t chi_r, int64_t wl, int64_t wm,
+                             int64_t wr, int precision, cudaStream_t stream, bool prepared) {
+  if (!prepared)
+    OSMPS_TRY(heff_prepare(ctx, L, W1, W2, R, chi_l, d1, d2, chi_r, wl, wm, wr, precision, stream));
+  return heff_apply_prepared(ctx, theta, y, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Environment updates (Sec. 3.4: contraction of the fixed sites into L / R).
+// ---------------------------------------------------------------------------
+static osmps_status env_left_f64(osmps_ctx* ctx, const double* Lin, const double* A,
+                                 const double* W, double* Lout, int64_t chi_l, int64_t d,
+                                 int64_t chi_r, int64_t w_in, int64_t w_out, cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  double* X = (double*)ws_get(ctx, SLOT_ENV_X, (size_t)chi_l * w_in * d * chi_r * 8, s, &st);
+  if (!X) return st;
+  double* Y = (double*)ws_get(ctx, SLOT_ENV_Y, (size_t)chi_l * d * w_out * chi_r * 8, s, &st);
+  if (!Y) return st;
+  double* Mat = (double*)ws_get(ctx, SLOT_ENV_OPA, (size_t)w_in * d * d * w_out * 8, s, &st);
+  if (!Mat) return st;
+  OSMPS_TRY(w_reorder(W, w_in, d, w_out, WORD_IN_W_S__OUT_T_W2, Mat, s));
+  // X[a2, w, s, b] = sum_a Lin[a2, w, a] A[a, s, b]
+  GemmF64 g1;
+  g1.M = chi_l * w_in; g1.N = d * chi_r; g1.K = chi_l;
+  g1.A = Lin; g1.sam = chi_l; g1.sak = 1;
+  g1.B = A; g1.sbk = d * chi_r; g1.sbn = 1;
+  g1.C = X; g1.scm = d * chi_r; g1.scn = 1;
+  OSMPS_TRY(gemm_f64(g1, s));
+  // Y[a2, t, w2, b] = sum_{w,s} X[a2, w, s, b] W[w, t, s, w2]
+  Fiber f;
+  f.P = w_in * d; f.Q = d * w_out; f.n_o1 = chi_l; f.n_o2 = 1; f.nc = chi_r;
+  f.is1 = w_in * d * chi_r; f.istride = chi_r; f.os1 = d * w_out * chi_r; f.ostride = chi_r;
+  OSMPS_TRY(fiber_contract_f64(f, Mat, X, Y, s));
+  // Lout[b2, (w2, b)] = sum_{(a2,t)} A[(a2,t), b2] Y[(a2,t), (w2,b)]
+  GemmF64 g2;
+  g2.M = chi_r; g2.N = w_out * chi_r; g2.K = chi_l * d;
+  g2.A = A; g2.sam = 1; g2.sak = chi_r;
+  g2.B = Y; g2.sbk = w_out * chi_r; g2.sbn = 1;
+  g2.C = Lout; g2.scm = w_out * chi_r; g2.scn = 1;
+  return gemm_f64(g2, s);
+}
+
+static osmps_status env_right_f64(osmps_ctx* ctx, const double* Rin, const double* A,
+                                  const double* W, double* Rout, int64_t chi_l, int64_t d,
+                                  int64_t chi_r, int64_t w_in, int64_t w_out, cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  double* X = (double*)ws_get(ctx, SLOT_ENV_X, (size_t)chi_l * d * w_in * chi_r * 8, s, &st);
+  if (!X) return st;
+  double* Y = (double*)ws_get(ctx, SLOT_ENV_Y, (size_t)chi_l * w_out * d * chi_r * 8, s, &st);
+  if (!Y) return st;
+  double* Mat = (double*)ws_get(ctx, SLOT_ENV_OPA, (size_t)w_out * d * d * w_in * 8, s, &st);
+  if (!Mat) return st;
+  OSMPS_TRY(w_reorder(W, w_out, d, w_in, WORD_IN_S_W2__OUT_W_T, Mat, s));
+  // X[(a,s), w2, b2] = sum_b A[(a,s), b] Rin[b2, w2, b]   (batched over w2)
+  GemmF64 g1;
+  g1.M = chi_l * d; g1.N = chi_r; g1.K = chi_r; g1.batch = w_in;
+  g1.A = A; g1.sam = chi_r; g1.sak = 1; g1.sab = 0;
+  g1.B = Rin; g1.sbk = 1; g1.sbn = w_in * chi_r; g1.sbb = chi_r;
+  g1.C = X; g1.scm = w_in * chi_r; g1.scn = 1; g1.scb = chi_r;
+  OSMPS_TRY(gemm_f64(g1, s));
+  // Y[a, w, t, b2] = sum_{s,w2} X[a, s, w2, b2] W[w, t, s, w2]
+  Fiber f;
+  f.P = d * w_in; f.Q = w_out * d; f.n_o1 = chi_l; f.n_o2 = 1; f.nc = chi_r;
+  f.is1 = d * w_in * chi_r; f.istride = chi_r; f.os1 = w_out * d * chi_r; f.ostride = chi_r;
+  OSMPS_TRY(fiber_contract_f64(f, Mat, X, Y, s));
+  // Rout[a2, w, a] = sum_{(t,b2)} A[a2, (t,b2)] Y[a, w, (t,b2)]   (batched over w)
+  GemmF64 g2;
+  g2.M = chi_l; g2.N = chi_l; g2.K = d * chi_r; g2.batch = w_out;
+  g2.A = A; g2.sam = d * chi_r; g2.sak = 1; g2.sab = 0;
+  g2.B = Y; g2.sbk = 1; g2.sbn = w_out * d * chi_r; g2.sbb = d * chi_r;
+  g2.C = Rout; g2.scm = w_out * chi_l; g2.scn = 1; g2.scb = chi_l;
+  return gemm_f64(g2, s);
+}
+
+// Split-precision left update: the two GEMMs on tcgen05, the W-step in float32.
+static osmps_status env_left_tc(osmps_ctx* ctx, const double* Lin, const double* A,
+                                const double* W, double* Lout, int64_t chi_l, int64_t d,
+                                int64_t chi_r, int64_t w_in, int64_t w_out, int precision,
+                                cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  const int kind = tc_kind(precision);
+  const size_t es = tc_elem_bytes(kind);
+  const int64_t Kp1 = round_up(chi_l, 64), Kp2 = round_up(chi_l * d, 64);
+  const int64_t rowsA = std::max<int64_t>(chi_l * w_in, chi_r);
+  const int64_t rowsB = std::max<int64_t>(d * chi_r, w_out * chi_r);
+  const int64_t KpA = std::max(Kp1, Kp2);
+  void* opa = ws_get(ctx, SLOT_ENV_OPA, (size_t)rowsA * 2 * KpA * es + 4096, s, &st);
+  if (!opa) return st;
+  void* opb = ws_get(ctx, SLOT_ENV_OPB, (size_t)rowsB * 2 * KpA * es, s, &st);
+  if (!opb) return st;
+  float* X = (float*)ws_get(ctx, SLOT_ENV_X, (size_t)chi_l * w_in * d * chi_r * 4, s, &st);
+  if (!X) return st;
+  float* Y = (float*)ws_get(ctx, SLOT_ENV_Y, (size_t)chi_l * d * w_out * chi_r * 4, s, &st);
+  if (!Y) return st;
+  double* Mt = (double*)ws_get(ctx, SLOT_ENV_MAT, (size_t)w_in * d * d * w_out * 8, s, &st);
+  if (!Mt) return st;
+  OSMPS_TRY(w_reorder(W, w_in, d, w_out, WORD_IN_W_S__OUT_T_W2, Mt, s));
+  // X = Lin[(a2,w), a] . A[a, (s,b)]
+  SplitView la; la.src = Lin; la.rows = chi_l * w_in; la.K = chi_l; la.s0 = chi_l; la.sk = 1;
+  OSMPS_TRY(split_operand(la, kind, opa, Kp1, s));
+  SplitView at; at.src = A; at.rows = d * chi_r; at.K = chi_l; at.s0 = 1; at.sk = d * chi_r;
+  OSMPS_TRY(split_operand(at, kind, opb, Kp1, s));
+  GemmTc g1; g1.kind = kind; g1.M = chi_l * w_in; g1.N = d * chi_r; g1.Kp = Kp1;
+  g1.A = opa; g1.B = opb; g1.C = X; g1.ldc = d * chi_r; g1.out = TC_OUT_F32;
+  OSMPS_TRY(gemm_tc(ctx, g1, s));
+  Fiber f;
+  f.P = w_in * d; f.Q = d * w_out; f.n_o1 = chi_l; f.n_o2 = 1; f.nc = chi_r;
+  f.is1 = w_in * d * chi_r; f.istride = chi_r; f.os1 = d * w_out * chi_r; f.ostride = chi_r;
+  OSMPS_TRY(fiber_contract_f32(f, Mt, X, Y, s));
+  // Lout[b2, (w2,b)] = sum_{(a2,t)} A^T[b2, (a2,t)] Y^T[(w2,b), (a2,t)]
+  SplitView aT; aT.src = A; aT.rows = chi_r; aT.K = chi_l * d; aT.s0 = 1; aT.sk = chi_r;
+  OSMPS_TRY(split_operand(aT, kind, opa, Kp2, s));
+  SplitView yT; yT.src = Y; yT.src_f32 = true; yT.rows = w_out * chi_r; yT.K = chi_l * d;
+  yT.s0 = 1; yT.sk = w_out * chi_r;
+  OSMPS_TRY(split_operand(yT, kind, opb, Kp2, s));
+  GemmTc g2; g2.kind = kind; g2.M = chi_r; g2.N = w_out * chi_r; g2.Kp = Kp2;
+  g2.A = opa; g2.B = opb; g2.C = Lout; g2.ldc = w_out * chi_r; g2.out = TC_OUT_F64;
+  return gemm_tc(ctx, g2, s);
+}
+
+static osmps_status env_right_tc(osmps_ctx* ctx, const double* Rin, const double* A,
+                                 const double* W, double* Rout, int64_t chi_l, int64_t d,
+                                 int64_t chi_r, int64_t w_in, int64_t w_out, int precision,
+                                 cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  const int kind = tc_kind(precision);
+  const size_t es = tc_elem_bytes(kind);
+  const int64_t Kp1 = round_up(chi_r, 64), Kp2 = round_up(d * chi_r, 64);
+  const int64_t KpA = std::max(Kp1, Kp2);
+  const int64_t rowsA = std::max<int64_t>(chi_l * d, chi_l);
+  const int64_t rowsB = std::max<int64_t>(w_in * chi_r, w_out * chi_l);
+  void* opa = ws_get(ctx, SLOT_ENV_OPA, (size_t)rowsA * 2 * KpA * es + 4096, s, &st);
+  if (!opa) return st;
+  void* opb = ws_get(ctx, SLOT_ENV_OPB, (size_t)rowsB * 2 * KpA * es, s, &st);
+  if (!opb) return st;
+  float* X = (float*)ws_get(ctx, SLOT_ENV_X, (size_t)chi_l * d * w_in * chi_r * 4, s, &st);
+  if (!X) return st;
+  float* Y = (float*)ws_get(ctx, SLOT_ENV_Y, (size_t)chi_l * w_out * d * chi_r * 4, s, &st);
+  if (!Y) return st;
+  double* Mt = (double*)ws_get(ctx, SLOT_ENV_MAT, (size_t)w_out * d * d * w_in * 8, s, &st);
+  if (!Mt) return st;
+  OSMPS_TRY(w_reorder(W, w_out, d, w_in, WORD_IN_S_W2__OUT_W_T, Mt, s));
+  // X[(a,s), (w2,b2)] = sum_b A[(a,s), b] Rin[b2, w2, b]; B rows ordered (w2, b2)
+  SplitView av; av.src = A; av.rows = chi_l * d; av.K = chi_r; av.s0 = chi_r; av.sk = 1;
+  OSMPS_TRY(split_operand(av, kind, opa, Kp1, s));
+  SplitView rv; rv.src = Rin; rv.rows = w_in * chi_r; rv.n1 = chi_r; rv.K = chi_r;
+  rv.s0 = chi_r; rv.s1 = w_in * chi_r; rv.sk = 1;  // row (w2, b2) -> b2*(w_in chi_r) + w2*chi_r
+  OSMPS_TRY(split_operand(rv, kind, opb, Kp1, s));
+  GemmTc g1; g1.kind = kind; g1.M = chi_l * d; g1.N = w_in * chi_r; g1.Kp = Kp1;
+  g1.A = opa; g1.B = opb; g1.C = X; g1.ldc = w_in * chi_r; g1.out = TC_OUT_F32;
+  OSMPS_TRY(gemm_tc(ctx, g1, s));
+  // Y[a, w, t, b2] = sum_{s,w2} X[a, s, w2, b2] W[w, t, s, w2]
+  Fiber f;
+  f.P = d * w_in; f.Q = w_out * d; f.n_o1 = chi_l; f.n_o2 = 1; f.nc = chi_r;
+  f.is1 = d * w_in * chi_r; f.istride = chi_r; f.os1 = w_out * d * chi_r; f.ostride = chi_r;
+  OSMPS_TRY(fiber_contract_f32(f, Mt, X, Y, s));
+  // Rout[a2, (w,a)] = sum_{(t,b2)} A[a2, (t,b2)] Y[(w,a), (t,b2)] with Y rows (a,w) reordered
+  SplitView a2; a2.src = A; a2.rows = chi_l; a2.K = d * chi_r; a2.s0 = d * chi_r; a2.sk = 1;
+  OSMPS_TRY(split_operand(a2, kind, opa, Kp2, s));
+  SplitView yv; yv.src = Y; yv.src_f32 = true; yv.rows = w_out * chi_l; yv.n1 = chi_l;
+  yv.K = d * chi_r; yv.s0 = d * chi_r; yv.s1 = w_out * d * chi_r; yv.sk = 1;  // row (w, a)
+  OSMPS_TRY(split_operand(yv, kind, opb, Kp2, s));
+  GemmTc g2; g2.kind = kind; g2.M = chi_l; g2.N = w_out * chi_l; g2.Kp = Kp2;
+  g2.A = opa; g2.B = opb; g2.C = Rout; g2.ldc = w_out * chi_l; g2.out = TC_OUT_F64;
+  return gemm_tc(ctx, g2, s);
+}
+
+osmps_status env_update_impl(osmps_ctx* ctx, int side, const double* env_in, const double* A,
+                             const double* W, double* env_out, int64_t chi_l, int64_t d,
+                             int64_t chi_r, int64_t w_in, int64_t w_out, int precision,
+                             cudaStream_t stream) {
+  if (precision == OSMPS_PREC_FP64) {
+    if (side == 0) return env_left_f64(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
+    return env_right_f64(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
+  }
+  if (side == 0)
+    return env_left_tc(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, precision, stream);
+  return env_right_tc(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, precision, stream);
+}
+
+osmps_status theta_form_impl(const double* A1, const double* A2, double* theta, int64_t chi_l,
+                             int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
+                             cudaStream_t stream) {
+  GemmF64 g;
+  g.M = chi_l * d1; g.N = d2 * chi_r; g.K = chi_m;
+  g.A = A1; g.sam = chi_m; g.sak = 1;
+  g.B = A2; g.sbk = d2 * chi_r; g.sbn = 1;
+  g.C = theta; g.scm = d2 * chi_r; g.scn = 1;
+  return gemm_f64(g, stream);
+}
+
+}  // namespace osmps
+
+using namespace osmps;
+
+static bool dims_ok(std::initializer_list<int64_t> v) {
+  for (int64_t x : v)
+    if (x <= 0 || x > ((int64_t)1 << 31)) return false;
+  return true;
+}
+
+extern "C" {
+
+osmps_status osmps_heff_apply(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                              const double* R, const double* theta, double* y, int64_t chi_l,
+                              int64_t d1, int64_t d2, int64_t chi_r, int64_t wl, int64_t wm,
+                              int64_t wr, int precision, void* stream) {
+  clear_error();
+  if (!ctx || !L || !W1 || !W2 || !R || !theta || !y)
+    return set_error(OSMPS_EINVAL, "osmps_heff_apply: null argument");
+  if ((const void*)y == (const void*)theta)
+    return set_error(OSMPS_EINVAL, "osmps_heff_apply: y aliases theta");
+  if (!valid_precision(precision))
+    return set_error(OSMPS_EINVAL, "osmps_heff_apply: precision %d", precision);
+  if (!dims_ok({chi_l, d1, d2, chi_r, wl, wm, wr}))
+    return set_error(OSMPS_ESHAPE, "osmps_heff_apply: non-positive or oversized dimension");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  return heff_apply_impl(ctx, L, W1, W2, R, theta, y, chi_l, d1, d2, chi_r, wl, wm, wr, precision,
+                         (cudaStream_t)stream, false);
+}
+
+osmps_status osmps_env_update(osmps_ctx* ctx, int side, const double* env_in, const double* A,
+                              const double* W, double* env_out, int64_t chi_l, int64_t d,
+                              int64_t chi_r, int64_t w_in, int64_t w_out, int precision,
+                              void* stream) {
+  clear_error();
+  if (!ctx || !env_in || !A || !W || !env_out)
+    return set_error(OSMPS_EINVAL, "osmps_env_update: null argument");
+  if (side != 0 && side != 1) return set_error(OSMPS_EINVAL, "osmps_env_update: side %d", side);
+  if (env_out == env_in || env_out == A)
+    return set_error(OSMPS_EINVAL, "osmps_env_update: env_out aliases an input");
+  if (!valid_precision(precision))
+    return set_error(OSMPS_EINVAL, "osmps_env_update: precision %d", precision);
+  if (!dims_ok({chi_l, d, chi_r, w_in, w_out}))
+    return set_error(OSMPS_ESHAPE, "osmps_env_update: non-positive or oversized dimension");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  return env_update_impl(ctx, side, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, precision,
+                         (cudaStream_t)stream);
+}
+
+osmps_status osmps_theta_form(osmps_ctx* ctx, const double* A1, const double* A2, double* theta,
+                              int64_t chi_l, int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
+                              void* stream) {
+  clear_error();
+  if (!ctx || !A1 || !A2 || !theta) return set_error(OSMPS_EINVAL, "osmps_theta_form: null argument");
+  if (theta == A1 || theta == A2) return set_error(OSMPS_EINVAL, "osmps_theta_form: theta aliases an input");
+  if (!dims_ok({chi_l, d1, chi_m, d2, chi_r}))
+    return set_error(OSMPS_ESHAPE, "osmps_theta_form: non-positive or oversized dimension");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  return theta_form_impl(A1, A2, theta, chi_l, d1, chi_m, d2, chi_r, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// Context, error reporting, workspace and float64 vector primitives.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace osmps {
+
+static thread_local char g_err[1024] = "";
+
+osmps_status set_error(osmps_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+void* ws_get(osmps_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, osmps_status* st) {
+  Buffer& b = ctx->slots[slot];
+  if (bytes == 0) bytes = 256;
+  if (b.bytes >= bytes) return b.ptr;
+  size_t want = bytes + bytes / 8;
+  want = (want + 255) & ~size_t(255);
+  if (b.ptr) {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+      *st = set_error(OSMPS_ECUDA, "workspace grow: stream sync failed: %s", cudaGetErrorString(e));
+      return nullptr;
+    }
+    cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *st = set_error(OSMPS_ENOMEM, "workspace slot %d: cudaMalloc(%zu) failed: %s", (int)slot, want,
+                    cudaGetErrorString(e));
+    return nullptr;
+  }
+  b.ptr = p;
+  b.bytes = want;
+  return p;
+}
+
+osmps_status pinned_reserve(osmps_ctx* ctx, size_t count) {
+  if (ctx->host_pinned_count >= count) return OSMPS_OK;
+  if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  ctx->host_pinned = nullptr;
+  ctx->host_pinned_count = 0;
+  size_t n = count < 4096 ? 4096 : count;
+  OSMPS_CUDA(cudaMallocHost((void**)&ctx->host_pinned, n * sizeof(double)));
+  ctx->host_pinned_count = n;
+  return OSMPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Reductions: fixed-order two-stage sums (deterministic run to run).
+// ---------------------------------------------------------------------------
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 1024;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[RED_THREADS / 32];
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < RED_THREADS / 32) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) v = warp_sum(v);
+  return v;
+}
+
+__global__ void k_sumsq_partial(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v = x[i];
+    acc = fma(v, v, acc);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_sum_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+static int red_blocks(int64_t n) {
+  int64_t b = cdiv(n, RED_THREADS * 4);
+  if (b < 1) b = 1;
+  if (b > RED_MAX_BLOCKS) b = RED_MAX_BLOCKS;
+  return (int)b;
+}
+
+osmps_status vec_norm2(osmps_ctx* ctx, const double* x, int64_t n, double* dev_out, cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  double* part = (double*)ws_get(ctx, SLOT_RED, RED_MAX_BLOCKS * sizeof(double), s, &st);
+  if (!part) return st;
+  int nb = red_blocks(n);
+  k_sumsq_partial<<<nb, RED_THREADS, 0, s>>>(x, n, part);
+  k_sum_final<<<1, RED_THREADS, 0, s>>>(part, nb, dev_out);
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+__global__ void k_scale_inv_sqrt(double* __restrict__ x, int64_t n, const double* __restrict__ nrm2) {
+  double f = 1.0 / sqrt(*nrm2);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+
+__global__ void k_scale_inv(double* __restrict__ y, const double* __restrict__ x, int64_t n,
+                            const double* __restrict__ div) {
+  double f = 1.0 / (*div);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * f;
+}
+
+static int ew_blocks(int64_t n) {
+  int64_t b = cdiv(n, 256 * 4);
+  if (b < 1) b = 1;
+  if (b > 65536) b = 65536;
+  return (int)b;
+}
+
+osmps_status vec_scale_by_inv_sqrt(double* x, int64_t n, const double* dev_norm2, cudaStream_t s) {
+  k_scale_inv_sqrt<<<ew_blocks(n), 256, 0, s>>>(x, n, dev_norm2);
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+osmps_status vec_scale_by_inv(double* y, const double* x, int64_t n, const double* dev_div,
+                              cudaStream_t s) {
+  k_scale_inv<<<ew_blocks(n), 256, 0, s>>>(y, x, n, dev_div);
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+__global__ void k_nonfinite(const double* __restrict__ x, int64_t n, int* __restrict__ flag) {
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 4);
+}
+
+osmps_status check_finite(osmps_ctx* ctx, const double* x, int64_t n, cudaStream_t s, bool* ok) {
+  OSMPS_CUDA(cudaMemsetAsync(ctx->dev_flags + 1, 0, sizeof(int), s));
+  k_nonfinite<<<ew_blocks(n), 256, 0, s>>>(x, n, ctx->dev_flags + 1);
+  OSMPS_LAUNCH_CHECK();
+  int h = 0;
+  OSMPS_CUDA(cudaMemcpyAsync(&h, ctx->dev_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  OSMPS_CUDA(cudaStreamSynchronize(s));
+  *ok = (h == 0);
+  return OSMPS_OK;
+}
+
+}  // namespace osmps
+
+using namespace osmps;
+
+extern "C" {
+
+const char* osmps_last_error(void) { return g_err; }
+
+const char* osmps_status_string(osmps_status s) {
+  switch (s) {
+    case OSMPS_OK: return "OSMPS_OK";
+    case OSMPS_EINVAL: return "OSMPS_EINVAL";
+    case OSMPS_ESHAPE: return "OSMPS_ESHAPE";
+    case OSMPS_ENOMEM: return "OSMPS_ENOMEM";
+    case OSMPS_ECUDA: return "OSMPS_ECUDA";
+    case OSMPS_ENOCONV: return "OSMPS_ENOCONV";
+    case OSMPS_ETIMEOUT: return "OSMPS_ETIMEOUT";
+    case OSMPS_ENAN: return "OSMPS_ENAN";
+    case OSMPS_EUNSUPPORTED: return "OSMPS_EUNSUPPORTED";
+  }
+  return "OSMPS_UNKNOWN";
+}
+
+osmps_status osmps_ctx_create(int device, size_t ws_bytes, osmps_ctx** out) {
+  clear_error();
+  if (!out) return set_error(OSMPS_EINVAL, "osmps_ctx_create: out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return set_error(OSMPS_ECUDA, "osmps_ctx_create: no CUDA device (%s)", cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= ndev)
+    return set_error(OSMPS_EINVAL, "osmps_ctx_create: device %d out of range [0,%d)", device, ndev);
+  OSMPS_CUDA(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  OSMPS_CUDA(cudaGetDeviceProperties(&prop, device));
+  if (prop.major < 10)
+    return set_error(OSMPS_EUNSUPPORTED, "osmps_ctx_create: device %d is sm_%d%d; sm_103 required",
+                     device, prop.major, prop.minor);
+  osmps_ctx* ctx = new osmps_ctx();
+  ctx->device = device;
+  ctx->sm_count = prop.multiProcessorCount;
+  if (cudaMalloc(&ctx->dev_flags, 16 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->dev_info, 16 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    osmps_ctx_destroy(ctx);
+    return set_error(OSMPS_ENOMEM, "osmps_ctx_create: flag allocation failed");
+  }
+  cudaMemset(ctx->dev_flags, 0, 16 * sizeof(int));
+  cudaMemset(ctx->dev_info, 0, 16 * sizeof(int));
+  if (cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS) {
+    osmps_ctx_destroy(ctx);
+    return set_error(OSMPS_ECUDA, "osmps_ctx_create: cusolverDnCreate failed");
+  }
+  if (ws_bytes > 0) {
+    osmps_status st = OSMPS_OK;
+    if (!ws_get(ctx, SLOT_HEFF_T1, ws_bytes, 0, &st)) {
+      osmps_ctx_destroy(ctx);
+      return st;
+    }
+  }
+  osmps_status st = pinned_reserve(ctx, 4096);
+  if (st != OSMPS_OK) {
+    osmps_ctx_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return OSMPS_OK;
+}
+
+osmps_status osmps_ctx_destroy(osmps_ctx* ctx) {
+  if (!ctx) return OSMPS_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (int i = 0; i < SLOT_COUNT; ++i)
+    if (ctx->slots[i].ptr) cudaFree(ctx->slots[i].ptr);
+  if (ctx->dev_flags) cudaFree(ctx->dev_flags);
+  if (ctx->dev_info) cudaFree(ctx->dev_info);
+  if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  delete ctx;
+  return OSMPS_OK;
+}
+
+size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx) {
+  if (!ctx) return 0;
+  size_t t = 0;
+  for (int i = 0; i < SLOT_COUNT; ++i) t += ctx->slots[i].bytes;
+  return t;
+}
+
+}  // extern "C"

@@ -1,0 +1,371 @@
+// Split-precision GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The dense contractions of the effective Hamiltonian (Sec. 3.4,
+// Fig. LanczosMPS) and of the environment updates are GEMMs
+//   C[M,N] = sum_k A[m,k] B[n,k]
+// with float64 data. Each float64 operand x is stored as x_hi + x_lo, both in
+// the tensor-core type (bf16 or tf32), and the product is accumulated in
+// float32 as A_hi B_hi + A_hi B_lo + A_lo B_hi (the A_lo B_lo term is below
+// the accumulator's resolution). Each operand row holds [hi | lo], Kp columns
+// each, so a product is just a K-range of the same two TMA tensors.
+//
+// Kernel structure (one 128 x 256 output tile per CTA, 192 threads):
+//   warp 0, one lane : TMA producer, 4-stage ring of 128B-swizzled tiles
+//   warp 1           : allocates 256 TMEM columns; one lane issues the MMAs
+//                      (M=128, N=256, 4 instructions per 128-byte K slice) and
+//                      commits each stage back to the producer
+//   warps 2..5       : epilogue, TMEM -> registers -> global (f32 or f64)
+// Every mbarrier wait is bounded by %globaltimer (2 s); on expiry the kernel
+// records bit 0 in the context's error flag, drains its own copies (bounded),
+// frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace osmps {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int KSLICE_BYTES = 128;  // K bytes per stage row = one 128B swizzle span
+constexpr int STAGES = 4;
+constexpr int A_STAGE = BM * KSLICE_BYTES;  // 16 KB
+constexpr int B_STAGE = BN * KSLICE_BYTES;  // 32 KB
+constexpr int STAGE_BYTES = A_STAGE + B_STAGE;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255u) == 0) {
+      uint64_t t = globaltimer();
+      if (i == 0) t0 = t;
+      else if (t - t0 > WAIT_LIMIT_NS) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D f32, A/B bf16 (kind::f16) or tf32 (kind::tf32),
+// both K-major, M = 128, N = 256.
+template <int KIND>
+__device__ __forceinline__ uint32_t idesc() {
+  const uint32_t ab = (KIND == TC_BF16) ? 1u : 2u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id,
+                                     uint32_t accumulate) {
+  if (KIND == TC_BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32"
+      " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int KIND, int OUT>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              void* __restrict__ C, int64_t M, int64_t N, int64_t ldc, int nkb, int kelem,
+              int Kp, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accb = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int total = 3 * nkb;
+
+  if (warp == 0 && lane == 0) {
+    // Producer. Iteration it covers K slice kb = it / 3 of product p = it % 3:
+    // p = 0 (hi, hi), 1 (hi, lo), 2 (lo, hi).
+    int issued = 0;
+    bool ok = true;
+    for (int it = 0; it < total; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {
+        ok = false;
+        break;
+      }
+      const int kb = it / 3, p = it % 3;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(sA + s * A_STAGE, &tmA, kb * kelem + (p == 2 ? Kp : 0), m0, &full[s]);
+      tma_load_2d(sB + s * B_STAGE, &tmB, kb * kelem + (p == 1 ? Kp : 0), n0, &full[s]);
+      ++issued;
+    }
+    if (!ok) atomicOr(err, 1);
+    // Drain: the last copy issued into each stage has completed before exit.
+    for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it) {
+      if (!mbar_wait(&full[it % STAGES], (uint32_t)(it / STAGES) & 1u)) atomicOr(err, 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t id = idesc<KIND>();
+    bool ok = true;
+    for (int it = 0; it < total; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t ad = sdesc(smem_u32(sA + s * A_STAGE));
+      const uint64_t bd = sdesc(smem_u32(sB + s * B_STAGE));
+#pragma unroll
+      for (int k = 0; k < KSLICE_BYTES / 32; ++k) {
+        // advance 32 bytes of K inside the swizzle span: +2 in the address field
+        umma<KIND>(tmem, ad + 2u * k, bd + 2u * k, id, (it > 0 || k > 0) ? 1u : 0u);
+      }
+      umma_commit(&empty[s]);
+    }
+    if (!ok) atomicOr(err, 1);
+    umma_commit(accb);
+  } else if (warp >= 2) {
+    const bool ok = mbar_wait(accb, 0);
+    if (!ok) atomicOr(err, 1);
+    tc_fence_after();
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int64_t row = (int64_t)m0 + q * 32 + lane;
+    for (int c = 0; c < BN; c += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
+      if (!ok || row >= M) continue;
+      const int64_t col0 = (int64_t)n0 + c;
+      if (OUT == TC_OUT_F32) {
+        float* dst = reinterpret_cast<float*>(C) + row * ldc + col0;
+        if (col0 + 32 <= N && (ldc & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) & 15) == 0)) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4) {
+            float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+            *reinterpret_cast<float4*>(dst + j) = v;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j < N) dst[j] = __uint_as_float(r[j]);
+        }
+      } else {
+        double* dst = reinterpret_cast<double*>(C) + row * ldc + col0;
+        if (col0 + 32 <= N && (ldc & 1) == 0 && ((reinterpret_cast<uintptr_t>(C) & 15) == 0)) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
+            double2 v = make_double2((double)__uint_as_float(r[j]),
+                                     (double)__uint_as_float(r[j + 1]));
+            *reinterpret_cast<double2*>(dst + j) = v;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j < N) dst[j] = (double)__uint_as_float(r[j]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+osmps_status make_map(CUtensorMap* map, const void* base, int kind, int64_t rows, int64_t Kp,
+                      int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return set_error(OSMPS_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  const size_t es = tc_elem_bytes(kind);
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0)
+    return set_error(OSMPS_EINVAL, "tensor-core operand base not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)(2 * Kp), (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(2 * Kp * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(KSLICE_BYTES / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, kind == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                  2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return set_error(OSMPS_ECUDA, "cuTensorMapEncodeTiled failed (%d): rows=%lld Kp=%lld", (int)r,
+                     (long long)rows, (long long)Kp);
+  return OSMPS_OK;
+}
+
+template <int KIND, int OUT>
+osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g, int* err,
+                    cudaStream_t stream) {
+  static bool configured = false;
+  if (!configured) {
+    OSMPS_CUDA(cudaFuncSetAttribute(k_gemm_tc<KIND, OUT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    configured = true;
+  }
+  const int kelem = KSLICE_BYTES / (int)tc_elem_bytes(KIND);
+  const int nkb = (int)(g.Kp / kelem);
+  dim3 grid((unsigned)cdiv(g.N, BN), (unsigned)cdiv(g.M, BM));
+  k_gemm_tc<KIND, OUT><<<grid, THREADS, SMEM_BYTES, stream>>>(a, b, g.C, g.M, g.N, g.ldc, nkb,
+                                                             kelem, (int)g.Kp, err);
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+}  // namespace
+
+osmps_status gemm_tc(osmps_ctx* ctx, const GemmTc& g, cudaStream_t stream) {
+  if (g.M <= 0 || g.N <= 0) return OSMPS_OK;
+  if (g.Kp <= 0 || g.Kp % 64 != 0)
+    return set_error(OSMPS_ESHAPE, "gemm_tc: Kp=%lld must be a positive multiple of 64",
+                     (long long)g.Kp);
+  if (2 * g.Kp > (int64_t)1 << 31 || cdiv(g.M, BM) > 65535 || g.M > ((int64_t)1 << 31) ||
+      g.N > ((int64_t)1 << 31))
+    return set_error(OSMPS_ESHAPE, "gemm_tc: dimensions exceed the supported range");
+  CUtensorMap ma, mb;
+  OSMPS_TRY(make_map(&ma, g.A, g.kind, g.M, g.Kp, BM));
+  OSMPS_TRY(make_map(&mb, g.B, g.kind, g.N, g.Kp, BN));
+  int* err = ctx->dev_flags;
+  if (g.kind == TC_BF16) {
+    if (g.out == TC_OUT_F32) return launch<TC_BF16, TC_OUT_F32>(ma, mb, g, err, stream);
+    return launch<TC_BF16, TC_OUT_F64>(ma, mb, g, err, stream);
+  }
+  if (g.out == TC_OUT_F32) return launch<TC_TF32, TC_OUT_F32>(ma, mb, g, err, stream);
+  return launch<TC_TF32, TC_OUT_F64>(ma, mb, g, err, stream);
+}
+
+}  // namespace osmps

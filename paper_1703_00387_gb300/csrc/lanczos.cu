@@ -1,0 +1,352 @@
+// Lanczos ground state of H_eff (Sec. 3.4: the local eigenproblem is solved
+// with matrix-vector products only).
+//
+// Krylov vectors, orthogonalisation and the tridiagonal eigensolve are all
+// float64 on the device. Each step applies H_eff (any precision), projects
+// the result against every stored Krylov vector twice (classical
+// Gram-Schmidt, two passes: full reorthogonalisation), normalises, and
+// solves the small tridiagonal problem for the lowest Ritz pair:
+//   * the eigenvalue by Sturm-count multisection (256 points per round),
+//   * its eigenvector by inverse iteration with a partially pivoted
+//     tridiagonal LU (Gaussian elimination with row interchanges).
+// The host reads three numbers per step (energy, residual estimate, beta)
+// to decide whether to stop: residual estimate beta_j |s_j| <= tol.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace osmps {
+
+namespace {
+
+constexpr int MAXIT = 512;
+constexpr int DOT_THREADS = 256;
+constexpr int DOT_GROUP = 8;
+constexpr int DOT_MAX_BLOCKS = 512;
+
+// scalar layout in SLOT_LZ_SCAL (doubles)
+constexpr int OFF_ALPHA = 0;
+constexpr int OFF_BETA = MAXIT;
+constexpr int OFF_C1 = 2 * MAXIT;
+constexpr int OFF_C2 = 3 * MAXIT;
+constexpr int OFF_S = 4 * MAXIT;
+constexpr int OFF_MISC = 5 * MAXIT;  // [0] e, [1] resid, [2] beta, [3] ||w||^2, [4] ||theta||^2
+constexpr int SCAL_COUNT = 5 * MAXIT + 16;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// part[i * nb + b] = sum over block b's elements of V[i][e] * w[e], i < nv.
+__global__ void __launch_bounds__(DOT_THREADS) k_multidot(const double* __restrict__ V, int64_t ld,
+                                                          int nv, const double* __restrict__ w,
+                                                          int64_t n, double* __restrict__ part) {
+  __shared__ double sh[DOT_THREADS / 32][DOT_GROUP];
+  const int nb = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int g0 = 0; g0 < nv; g0 += DOT_GROUP) {
+    double acc[DOT_GROUP];
+#pragma unroll
+    for (int v = 0; v < DOT_GROUP; ++v) acc[v] = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * DOT_THREADS + threadIdx.x; e < n;
+         e += (int64_t)nb * DOT_THREADS) {
+      const double wv = w[e];
+#pragma unroll
+      for (int v = 0; v < DOT_GROUP; ++v)
+        if (g0 + v < nv) acc[v] = fma(V[(int64_t)(g0 + v) * ld + e], wv, acc[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < DOT_GROUP; ++v) {
+      double s = warp_sum(acc[v]);
+      if (lane == 0) sh[warp][v] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < DOT_GROUP && g0 + (int)threadIdx.x < nv) {
+      double s = 0.0;
+      for (int k = 0; k < DOT_THREADS / 32; ++k) s += sh[k][threadIdx.x];
+      part[(int64_t)(g0 + threadIdx.x) * nb + blockIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[i] = sum_b part[i * nb + b] in a fixed order (one block per vector).
+__global__ void k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)blockIdx.x * nb + b];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+  }
+}
+
+// mode 0: w[e] -= sum_i c[i] V[i][e];  mode 1: w[e] = sum_i c[i] V[i][e]
+__global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
+                          const double* __restrict__ c, double* __restrict__ w, int64_t n,
+                          int mode) {
+  __shared__ double cs[MAXIT];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = c[i];
+  __syncthreads();
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < nv; ++i) acc = fma(cs[i], V[(int64_t)i * ld + e], acc);
+    w[e] = (mode == 0) ? (w[e] - acc) : acc;
+  }
+}
+
+__device__ int sturm_count(const double* a, const double* b, int m, double x) {
+  // number of eigenvalues of the tridiagonal (a, b) below x
+  int cnt = 0;
+  double q = a[0] - x;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    if (q == 0.0) q = 1e-300;
+    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// Record alpha_j, beta_j, then the lowest eigenpair of T_{j+1}.
+__global__ void __launch_bounds__(256) k_tridiag(double* __restrict__ sc, int j) {
+  __shared__ double a[MAXIT], b[MAXIT], x[MAXIT], dl[MAXIT], dd[MAXIT], du[MAXIT];
+  __shared__ double lo, hi;
+  __shared__ int best;
+  const int m = j + 1;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    sc[OFF_ALPHA + j] = sc[OFF_C1 + j] + sc[OFF_C2 + j];
+    sc[OFF_BETA + j] = sqrt(sc[OFF_MISC + 3]);
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += blockDim.x) {
+    a[i] = sc[OFF_ALPHA + i];
+    b[i] = sc[OFF_BETA + i];  // b[i] couples i and i+1 (b[j] is the residual norm)
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double l = 1e300, h = -1e300;
+    for (int i = 0; i < m; ++i) {
+      double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+      l = fmin(l, a[i] - r);
+      h = fmax(h, a[i] + r);
+    }
+    double pad = 1e-12 * fmax(fabs(l), fabs(h)) + 1e-300;
+    lo = l - pad;
+    hi = h + pad;
+  }
+  __syncthreads();
+  const int P = blockDim.x;
+  for (int round = 0; round < 12; ++round) {
+    const double L0 = lo, H0 = hi;
+    if (!(H0 - L0 > 4e-16 * fmax(fabs(L0), fabs(H0)))) break;
+    if (tid == 0) best = P;
+    __syncthreads();
+    const double xt = L0 + (H0 - L0) * (double)(tid + 1) / (double)(P + 1);
+    if (sturm_count(a, b, m, xt) >= 1) atomicMin(&best, tid);
+    __syncthreads();
+    if (tid == 0) {
+      const int t = best;
+      const double xh = (t < P) ? L0 + (H0 - L0) * (double)(t + 1) / (double)(P + 1) : H0;
+      const double xl = L0 + (H0 - L0) * (double)t / (double)(P + 1);
+      lo = xl;
+      hi = xh;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double e = 0.5 * (lo + hi);
+    double tnorm = 0.0;
+    for (int i = 0; i < m; ++i) tnorm = fmax(tnorm, fabs(a[i]) + 2.0 * fabs(b[i]));
+    const double tiny = 1e-300 + 1e-18 * tnorm;
+    for (int i = 0; i < m; ++i) x[i] = 1.0 / sqrt((double)m);
+    for (int iter = 0; iter < 3; ++iter) {
+      for (int i = 0; i < m; ++i) {
+        dd[i] = a[i] - e;
+        du[i] = (i < m - 1) ? b[i] : 0.0;
+        dl[i] = (i < m - 1) ? b[i] : 0.0;
+      }
+      // Gaussian elimination with partial pivoting; dl[i] becomes the second
+      // superdiagonal entry of row i after the sweep.
+      for (int i = 0; i + 1 < m; ++i) {
+        if (fabs(dd[i]) >= fabs(dl[i])) {
+          if (dd[i] == 0.0) dd[i] = tiny;
+          const double f = dl[i] / dd[i];
+          dd[i + 1] -= f * du[i];
+          x[i + 1] -= f * x[i];
+          dl[i] = 0.0;
+        } else {
+          const double f = dd[i] / dl[i];
+          dd[i] = dl[i];
+          const double t = dd[i + 1];
+          dd[i + 1] = du[i] - f * t;
+          if (i + 2 < m) {
+            dl[i] = du[i + 1];
+            du[i + 1] = -f * dl[i];
+          } else {
+            dl[i] = 0.0;
+          }
+          du[i] = t;
+          const double bt = x[i];
+          x[i] = x[i + 1];
+          x[i + 1] = bt - f * x[i + 1];
+        }
+      }
+      if (dd[m - 1] == 0.0) dd[m - 1] = tiny;
+      x[m - 1] /= dd[m - 1];
+      if (m > 1) x[m - 2] = (x[m - 2] - du[m - 2] * x[m - 1]) / dd[m - 2];
+      for (int i = m - 3; i >= 0; --i)
+        x[i] = (x[i] - du[i] * x[i + 1] - dl[i] * x[i + 2]) / dd[i];
+      double nrm = 0.0;
+      for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
+      nrm = sqrt(nrm);
+      if (!(nrm > 0.0) || !isfinite(nrm)) {
+        for (int i = 0; i < m; ++i) x[i] = (i == 0) ? 1.0 : 0.0;
+        break;
+      }
+      for (int i = 0; i < m; ++i) x[i] /= nrm;
+    }
+    for (int i = 0; i < m; ++i) sc[OFF_S + i] = x[i];
+    sc[OFF_MISC + 0] = e;
+    sc[OFF_MISC + 1] = b[j] * fabs(x[m - 1]);
+    sc[OFF_MISC + 2] = b[j];
+  }
+}
+
+int dot_blocks(int64_t n) {
+  int64_t b = cdiv(n, DOT_THREADS * 4);
+  if (b < 1) b = 1;
+  if (b > DOT_MAX_BLOCKS) b = DOT_MAX_BLOCKS;
+  return (int)b;
+}
+
+int ew_blocks(int64_t n) {
+  int64_t b = cdiv(n, 256 * 4);
+  if (b < 1) b = 1;
+  if (b > 8192) b = 8192;
+  return (int)b;
+}
+
+osmps_status project(osmps_ctx* ctx, const double* V, int64_t n, int nv, double* w, double* part,
+                     double* coef, cudaStream_t s) {
+  const int nb = dot_blocks(n);
+  k_multidot<<<nb, DOT_THREADS, 0, s>>>(V, n, nv, w, n, part);
+  k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef);
+  k_combine<<<ew_blocks(n), 256, 0, s>>>(V, n, nv, coef, w, n, 0);
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+}  // namespace
+
+osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                          const double* R, double* theta, int64_t chi_l, int64_t d1, int64_t d2,
+                          int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int max_iter,
+                          double tol, int precision, double* energy, int* iters, double* resid,
+                          cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  const int64_t n = chi_l * d1 * d2 * chi_r;
+  if (max_iter > n) max_iter = (int)n;
+  double* V = (double*)ws_get(ctx, SLOT_LZ_BASIS, (size_t)max_iter * n * 8, s, &st);
+  if (!V) return st;
+  double* w = (double*)ws_get(ctx, SLOT_LZ_W, (size_t)n * 8, s, &st);
+  if (!w) return st;
+  double* sc = (double*)ws_get(ctx, SLOT_LZ_SCAL, SCAL_COUNT * 8, s, &st);
+  if (!sc) return st;
+  double* part = (double*)ws_get(ctx, SLOT_LZ_PART, (size_t)MAXIT * DOT_MAX_BLOCKS * 8, s, &st);
+  if (!part) return st;
+  OSMPS_TRY(pinned_reserve(ctx, 16));
+  OSMPS_TRY(heff_prepare(ctx, L, W1, W2, R, chi_l, d1, d2, chi_r, wl, wm, wr, precision, s));
+
+  // v_0 = theta / ||theta||
+  OSMPS_TRY(vec_norm2(ctx, theta, n, sc + OFF_MISC + 4, s));
+  OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC + 4, 8, cudaMemcpyDeviceToHost, s));
+  OSMPS_CUDA(cudaStreamSynchronize(s));
+  if (!(ctx->host_pinned[0] > 0.0) || !std::isfinite(ctx->host_pinned[0]))
+    return set_error(ctx->host_pinned[0] == 0.0 ? OSMPS_EINVAL : OSMPS_ENAN,
+                     "lanczos: start vector has norm^2 %g", ctx->host_pinned[0]);
+  OSMPS_CUDA(cudaMemcpyAsync(V, theta, n * 8, cudaMemcpyDeviceToDevice, s));
+  OSMPS_TRY(vec_scale_by_inv_sqrt(V, n, sc + OFF_MISC + 4, s));
+
+  int m = 0;
+  double e = 0.0, res = 0.0;
+  bool converged = false;
+  for (int j = 0; j < max_iter; ++j) {
+    double* vj = V + (int64_t)j * n;
+    OSMPS_TRY(heff_apply_impl(ctx, nullptr, nullptr, nullptr, nullptr, vj, w, chi_l, d1, d2,
+                              chi_r, wl, wm, wr, precision, s, true));
+    OSMPS_TRY(project(ctx, V, n, j + 1, w, part, sc + OFF_C1, s));
+    OSMPS_TRY(project(ctx, V, n, j + 1, w, part, sc + OFF_C2, s));
+    OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, s));
+    k_tridiag<<<1, 256, 0, s>>>(sc, j);
+    OSMPS_LAUNCH_CHECK();
+    OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC, 3 * 8, cudaMemcpyDeviceToHost, s));
+    OSMPS_CUDA(cudaStreamSynchronize(s));
+    e = ctx->host_pinned[0];
+    res = ctx->host_pinned[1];
+    const double beta = ctx->host_pinned[2];
+    m = j + 1;
+    if (!std::isfinite(e) || !std::isfinite(res))
+      return set_error(OSMPS_ENAN, "lanczos: non-finite Ritz value at step %d", j);
+    if (res <= tol || beta == 0.0 || m == n) {
+      converged = true;
+      break;
+    }
+    if (j + 1 == max_iter) break;
+    OSMPS_TRY(vec_scale_by_inv(V + (int64_t)(j + 1) * n, w, n, sc + OFF_BETA + j, s));
+  }
+  // Ritz vector theta = sum_i s_i v_i, normalised
+  k_combine<<<ew_blocks(n), 256, 0, s>>>(V, n, m, sc + OFF_S, theta, n, 1);
+  OSMPS_LAUNCH_CHECK();
+  OSMPS_TRY(vec_norm2(ctx, theta, n, sc + OFF_MISC + 4, s));
+  OSMPS_TRY(vec_scale_by_inv_sqrt(theta, n, sc + OFF_MISC + 4, s));
+  int flag = 0;
+  OSMPS_CUDA(cudaMemcpyAsync(&flag, ctx->dev_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  OSMPS_CUDA(cudaStreamSynchronize(s));
+  if (flag & 1) {
+    cudaMemsetAsync(ctx->dev_flags, 0, sizeof(int), s);
+    return set_error(OSMPS_ETIMEOUT, "lanczos: a bounded device wait gave up");
+  }
+  *energy = e;
+  *iters = m;
+  if (resid) *resid = res;
+  if (!converged)
+    return set_error(OSMPS_ENOCONV, "lanczos: residual %.3e above tol %.3e after %d steps", res,
+                     tol, m);
+  return OSMPS_OK;
+}
+
+}  // namespace osmps
+
+using namespace osmps;
+
+extern "C" osmps_status osmps_lanczos_ground(osmps_ctx* ctx, const double* L, const double* W1,
+                                             const double* W2, const double* R,
+                                             double* theta_inout, int64_t chi_l, int64_t d1,
+                                             int64_t d2, int64_t chi_r, int64_t wl, int64_t wm,
+                                             int64_t wr, int max_iter, double tol, int precision,
+                                             double* energy_out, int* iters_out,
+                                             double* resid_out, void* stream) {
+  clear_error();
+  if (!ctx || !L || !W1 || !W2 || !R || !theta_inout || !energy_out || !iters_out)
+    return set_error(OSMPS_EINVAL, "osmps_lanczos_ground: null argument");
+  if (max_iter < 1 || max_iter > MAXIT)
+    return set_error(OSMPS_EINVAL, "osmps_lanczos_ground: max_iter %d outside [1, %d]", max_iter,
+                     MAXIT);
+  if (!(tol >= 0.0)) return set_error(OSMPS_EINVAL, "osmps_lanczos_ground: tol %g", tol);
+  if (!valid_precision(precision))
+    return set_error(OSMPS_EINVAL, "osmps_lanczos_ground: precision %d", precision);
+  for (int64_t x : {chi_l, d1, d2, chi_r, wl, wm, wr})
+    if (x <= 0 || x > ((int64_t)1 << 31))
+      return set_error(OSMPS_ESHAPE, "osmps_lanczos_ground: non-positive or oversized dimension");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  return lanczos_impl(ctx, L, W1, W2, R, theta_inout, chi_l, d1, d2, chi_r, wl, wm, wr, max_iter,
+                      tol, precision, energy_out, iters_out, resid_out, (cudaStream_t)stream);
+}

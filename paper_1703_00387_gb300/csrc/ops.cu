@@ -1,0 +1,256 @@
+// Operand preparation and MPO contraction steps.
+//
+// * split_operand: float64/float32 -> [hi | lo] rows in bf16 or tf32 for the
+//   tensor-core GEMM (x = hi + lo + O(2^-17 |x|) for bf16, O(2^-22 |x|) for tf32).
+//   Rows are written K-major; a source whose K index is not contiguous is read
+//   through a 32 x 32 shared-memory transpose so both sides stay coalesced.
+// * fiber contractions: the W-steps of Sec. 3.4, where the MPO tensors
+//   M^[k] (few entries, Eq. MPOdef) act on the small (w, s) index pair of an
+//   intermediate, for every (outer, inner) fiber. These are bandwidth-bound:
+//   one coalesced pass over the input and the output.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace osmps {
+
+namespace {
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+template <int KIND>
+__device__ __forceinline__ void split_store(void* dst, int64_t off_hi, int64_t Kp, double x) {
+  if (KIND == TC_BF16) {
+    __nv_bfloat16 h = __double2bfloat16(x);
+    __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
+    reinterpret_cast<__nv_bfloat16*>(dst)[off_hi] = h;
+    reinterpret_cast<__nv_bfloat16*>(dst)[off_hi + Kp] = l;
+  } else {
+    uint32_t h = to_tf32((float)x);
+    uint32_t l = to_tf32((float)(x - (double)__uint_as_float(h)));
+    reinterpret_cast<uint32_t*>(dst)[off_hi] = h;
+    reinterpret_cast<uint32_t*>(dst)[off_hi + Kp] = l;
+  }
+}
+
+__device__ __forceinline__ double load_src(const void* src, bool f32, int64_t off) {
+  return f32 ? (double)reinterpret_cast<const float*>(src)[off]
+             : reinterpret_cast<const double*>(src)[off];
+}
+
+// K contiguous in the source: thread per (row, k), k fastest.
+template <int KIND>
+__global__ void k_split_direct(SplitView v, void* __restrict__ dst, int64_t Kp) {
+  const int64_t total = v.rows * Kp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / Kp, k = e - r * Kp;
+    double x = 0.0;
+    if (k < v.K) {
+      const int64_t r0 = r / v.n1, r1 = r - r0 * v.n1;
+      x = load_src(v.src, v.src_f32, r0 * v.s0 + r1 * v.s1 + k * v.sk);
+    }
+    split_store<KIND>(dst, r * 2 * Kp + k, Kp, x);
+  }
+}
+
+// K strided in the source: 32x32 tiles transposed through shared memory.
+template <int KIND>
+__global__ void k_split_transpose(SplitView v, void* __restrict__ dst, int64_t Kp) {
+  __shared__ double tile[32][33];
+  const int64_t r_base = (int64_t)blockIdx.x * 32;
+  const int64_t k_base = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t k = k_base + j, r = r_base + tx;  // rows fastest while reading
+    double x = 0.0;
+    if (k < v.K && r < v.rows) {
+      const int64_t r0 = r / v.n1, r1 = r - r0 * v.n1;
+      x = load_src(v.src, v.src_f32, r0 * v.s0 + r1 * v.s1 + k * v.sk);
+    }
+    tile[j][tx] = x;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t r = r_base + j, k = k_base + tx;  // k fastest while writing
+    if (r < v.rows && k < Kp) split_store<KIND>(dst, r * 2 * Kp + k, Kp, tile[tx][j]);
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = cdiv(n, threads);
+  if (b < 1) b = 1;
+  if (b > 65536) b = 65536;
+  return (int)b;
+}
+
+template <typename T, int QMAX, int MODE>  // MODE 0: plain output, 1/2: split bf16/tf32
+__global__ void k_fiber(Fiber f, const double* __restrict__ Mat, const T* __restrict__ in,
+                        T* __restrict__ out, void* __restrict__ sdst, int64_t Kcols, int64_t Kp) {
+  extern __shared__ uint8_t fsm[];
+  T* Ms = reinterpret_cast<T*>(fsm);
+  const int P = (int)f.P, Q = (int)f.Q;
+  for (int i = threadIdx.x; i < P * Q; i += blockDim.x) Ms[i] = (T)Mat[i];
+  __syncthreads();
+  const int64_t total = f.n_o1 * f.n_o2 * f.nc;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e % f.nc;
+    const int64_t o12 = e / f.nc;
+    const int64_t o2 = o12 % f.n_o2, o1 = o12 / f.n_o2;
+    const T* src = in + o1 * f.is1 + o2 * f.is2 + c;
+    T acc[QMAX];
+#pragma unroll
+    for (int o = 0; o < QMAX; ++o) acc[o] = (T)0;
+    for (int i = 0; i < P; ++i) {
+      const T x = src[(int64_t)i * f.istride];
+      const T* mrow = Ms + i * Q;
+#pragma unroll
+      for (int o = 0; o < QMAX; ++o)
+        if (o < Q) acc[o] = fma(mrow[o], x, acc[o]);
+    }
+    const int64_t ob = o1 * f.os1 + o2 * f.os2 + c;
+#pragma unroll
+    for (int o = 0; o < QMAX; ++o) {
+      if (o < Q) {
+        const int64_t off = ob + (int64_t)o * f.ostride;
+        if (MODE == 0) {
+          out[off] = acc[o];
+        } else {
+          const int64_t row = off / Kcols, col = off - row * Kcols;
+          split_store<MODE == 1 ? TC_BF16 : TC_TF32>(sdst, row * 2 * Kp + col, Kp, (double)acc[o]);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int MODE>
+osmps_status fiber_dispatch(const Fiber& f, const double* Mat, const T* in, T* out, void* sdst,
+                            int64_t Kcols, int64_t Kp, cudaStream_t s) {
+  if (f.P <= 0 || f.Q <= 0 || f.nc <= 0 || f.n_o1 <= 0 || f.n_o2 <= 0) return OSMPS_OK;
+  const size_t sm = (size_t)f.P * f.Q * sizeof(T);
+  if (sm > 96 * 1024)
+    return set_error(OSMPS_EUNSUPPORTED, "W-step: MPO block %lld x %lld too large",
+                     (long long)f.P, (long long)f.Q);
+  const int64_t total = f.n_o1 * f.n_o2 * f.nc;
+  const int threads = 256;
+  const int blocks = grid_for(total, threads);
+  if (f.Q <= 8) {
+    auto k = k_fiber<T, 8, MODE>;
+    if (sm > 48 * 1024) OSMPS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp);
+  } else if (f.Q <= 16) {
+    auto k = k_fiber<T, 16, MODE>;
+    if (sm > 48 * 1024) OSMPS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp);
+  } else if (f.Q <= 32) {
+    auto k = k_fiber<T, 32, MODE>;
+    if (sm > 48 * 1024) OSMPS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp);
+  } else if (f.Q <= 64) {
+    auto k = k_fiber<T, 64, MODE>;
+    if (sm > 48 * 1024) OSMPS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp);
+  } else {
+    return set_error(OSMPS_EUNSUPPORTED, "W-step: output block %lld > 64", (long long)f.Q);
+  }
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+template <int KIND>
+__global__ void k_zero_pad(void* dst, int64_t rows, int64_t Kcols, int64_t Kp) {
+  const int64_t w = Kp - Kcols;
+  const int64_t total = rows * w;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / w, k = Kcols + (e - r * w);
+    split_store<KIND>(dst, r * 2 * Kp + k, Kp, 0.0);
+  }
+}
+
+__global__ void k_w_reorder(const double* __restrict__ W, int64_t dw, int64_t d, int64_t dw2,
+                            int order, double* __restrict__ Mat) {
+  const int64_t total = dw * d * d * dw2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    // e enumerates W[w, t, s, w2] in row-major order
+    int64_t w2 = e % dw2, r = e / dw2;
+    int64_t s = r % d;
+    r /= d;
+    int64_t t = r % d, w = r / d;
+    int64_t i, o, Q;
+    if (order == WORD_IN_W_S__OUT_T_W2) {
+      i = w * d + s;
+      o = t * dw2 + w2;
+      Q = d * dw2;
+    } else {
+      i = s * dw2 + w2;
+      o = w * d + t;
+      Q = dw * d;
+    }
+    Mat[i * Q + o] = W[e];
+  }
+}
+
+}  // namespace
+
+osmps_status split_operand(const SplitView& v, int kind, void* dst, int64_t Kp, cudaStream_t s) {
+  if (v.rows <= 0) return OSMPS_OK;
+  if (Kp < v.K || Kp % 64 != 0) return set_error(OSMPS_ESHAPE, "split_operand: bad Kp");
+  if (v.sk == 1 || v.K == 1) {
+    const int blocks = grid_for(v.rows * Kp, 256);
+    if (kind == TC_BF16) k_split_direct<TC_BF16><<<blocks, 256, 0, s>>>(v, dst, Kp);
+    else k_split_direct<TC_TF32><<<blocks, 256, 0, s>>>(v, dst, Kp);
+  } else {
+    if (cdiv(Kp, 32) > 65535) return set_error(OSMPS_ESHAPE, "split_operand: K too large");
+    dim3 grid((unsigned)cdiv(v.rows, 32), (unsigned)cdiv(Kp, 32));
+    dim3 block(32, 8);
+    if (kind == TC_BF16) k_split_transpose<TC_BF16><<<grid, block, 0, s>>>(v, dst, Kp);
+    else k_split_transpose<TC_TF32><<<grid, block, 0, s>>>(v, dst, Kp);
+  }
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+osmps_status fiber_contract_f64(const Fiber& f, const double* Mat, const double* in, double* out,
+                                cudaStream_t s) {
+  return fiber_dispatch<double, 0>(f, Mat, in, out, nullptr, 1, 0, s);
+}
+
+osmps_status fiber_contract_f32(const Fiber& f, const double* Mat, const float* in, float* out,
+                                cudaStream_t s) {
+  return fiber_dispatch<float, 0>(f, Mat, in, out, nullptr, 1, 0, s);
+}
+
+osmps_status fiber_contract_f32_split(const Fiber& f, const double* Mat, const float* in,
+                                      void* dst, int kind, int64_t Kcols, int64_t Kp,
+                                      cudaStream_t s) {
+  if (kind == TC_BF16) return fiber_dispatch<float, 1>(f, Mat, in, nullptr, dst, Kcols, Kp, s);
+  return fiber_dispatch<float, 2>(f, Mat, in, nullptr, dst, Kcols, Kp, s);
+}
+
+osmps_status zero_pad_columns(void* dst, int kind, int64_t rows, int64_t Kcols, int64_t Kp,
+                              cudaStream_t s) {
+  if (Kp <= Kcols || rows <= 0) return OSMPS_OK;
+  const int blocks = grid_for(rows * (Kp - Kcols), 256);
+  if (kind == TC_BF16) k_zero_pad<TC_BF16><<<blocks, 256, 0, s>>>(dst, rows, Kcols, Kp);
+  else k_zero_pad<TC_TF32><<<blocks, 256, 0, s>>>(dst, rows, Kcols, Kp);
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+osmps_status w_reorder(const double* W, int64_t dw, int64_t d, int64_t dw2, int order, double* Mat,
+                       cudaStream_t s) {
+  const int64_t total = dw * d * d * dw2;
+  k_w_reorder<<<grid_for(total, 256), 256, 0, s>>>(W, dw, d, dw2, order, Mat);
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+}  // namespace osmps

@@ -1,0 +1,218 @@
+"""GPU parity of the single operations against the FP64 oracle.
+
+Bars (norm-wise relative error of the output): 1e-12 for OSMPS_PREC_FP64,
+1e-5 for the split-precision tensor-core paths (bf16x3, tf32x3). Shapes
+cover a single tile, several tiles with ragged tails in M, N and K, and the
+full chi = 1024 shape the benchmark times."""
+import numpy as np
+import pytest
+
+from oracle import dmrg as od
+from paper_1703_00387_gb300 import binding as B
+from paper_1703_00387_gb300 import hamiltonians, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "bf16x3": 1e-5, "tf32x3": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import os
+    if not os.path.exists(B.LIB_PATH):
+        from paper_1703_00387_gb300 import build
+        build.build()
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+HEFF_SHAPES = [
+    (5, 2, 2, 7, 3, 3, 3),        # single tile, tiny
+    (130, 2, 2, 70, 5, 5, 5),     # ragged M (650 rows), N (280), K (130 -> 192)
+    (64, 2, 2, 64, 1, 5, 5),      # left boundary (wl = 1)
+    (40, 3, 3, 33, 14, 14, 14),   # AKLT-sized MPO (w = 14, d = 3)
+    (48, 5, 5, 40, 4, 4, 4),      # Bose-Hubbard local dimension d = 5
+    (200, 2, 2, 256, 5, 5, 1),    # right boundary (wr = 1), exact N tile
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("shape", HEFF_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_heff_apply_parity(ctx, prec, shape):
+    Lh, W1, W2, Rh, th = inputs.random_heff_operands(*shape, seed=sum(shape))
+    ref = od.heff_apply(Lh, W1, W2, Rh, th)
+    t = [dev(x) for x in (Lh, W1, W2, Rh, th)]
+    y = torch.empty_like(t[4])
+    B.osmps_heff_apply(ctx, *t, y, precision=prec)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "fp64"])
+def test_heff_apply_full_size_chi1024(ctx, prec):
+    """The benchmark's shape: chi_l = chi_r = 1024, d = 2, w = 5 (XXZ)."""
+    Lh, W1, W2, Rh, th = inputs.random_heff_operands(1024, 2, 2, 1024, 5, 5, 5, seed=1024)
+    ref = od.heff_apply(Lh, W1, W2, Rh, th)
+    t = [dev(x) for x in (Lh, W1, W2, Rh, th)]
+    y = torch.empty_like(t[4])
+    B.osmps_heff_apply(ctx, *t, y, precision=prec)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), ref) <= TOL[prec]
+
+
+def test_heff_apply_repeat_is_deterministic(ctx):
+    Lh, W1, W2, Rh, th = inputs.random_heff_operands(96, 2, 2, 96, 5, 5, 5, seed=3)
+    t = [dev(x) for x in (Lh, W1, W2, Rh, th)]
+    ys = []
+    for _ in range(2):
+        y = torch.empty_like(t[4])
+        B.osmps_heff_apply(ctx, *t, y, precision="bf16x3")
+        ys.append(y.cpu().numpy())
+    np.testing.assert_array_equal(ys[0], ys[1])
+
+
+ENV_SHAPES = [(6, 2, 9, 3, 3), (130, 2, 100, 5, 5), (64, 3, 50, 14, 14), (1, 2, 2, 1, 5), (33, 5, 40, 4, 4)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("side", [0, 1])
+@pytest.mark.parametrize("shape", ENV_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_env_update_parity(ctx, prec, side, shape):
+    chi_l, d, chi_r, w_in, w_out = shape
+    env, A, W = inputs.random_env_operands(chi_l, d, chi_r, w_in, w_out, side, seed=sum(shape) + side)
+    if side == 0:
+        ref = od.env_left(env, A, W)
+        out = torch.empty((chi_r, w_out, chi_r), dtype=torch.float64, device="cuda:0")
+    else:
+        ref = od.env_right(env, A, W)
+        out = torch.empty((chi_l, w_out, chi_l), dtype=torch.float64, device="cuda:0")
+    B.osmps_env_update(ctx, side, dev(env), dev(A), dev(W), out, precision=prec)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("shape", [(3, 2, 5, 2, 4), (100, 2, 70, 3, 90), (1024, 2, 1024, 2, 1024)])
+def test_theta_form_parity(ctx, shape):
+    chi_l, d1, chi_m, d2, chi_r = shape
+    rng = np.random.default_rng(5)
+    A1 = rng.standard_normal((chi_l, d1, chi_m))
+    A2 = rng.standard_normal((chi_m, d2, chi_r))
+    ref = np.tensordot(A1, A2, axes=([2], [0]))
+    th = torch.empty(ref.shape, dtype=torch.float64, device="cuda:0")
+    B.osmps_theta_form(ctx, dev(A1), dev(A2), th)
+    torch.cuda.synchronize()
+    assert rel(th.cpu().numpy(), ref) <= 1e-13
+
+
+def _split_case(seed, shape, decay):
+    """theta with a prescribed, decaying Schmidt spectrum (random orthogonal factors)."""
+    chi_l, d1, d2, chi_r = shape
+    rng = np.random.default_rng(seed)
+    m, n = chi_l * d1, d2 * chi_r
+    r = min(m, n)
+    U, _ = np.linalg.qr(rng.standard_normal((m, r)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    s = np.exp(-decay * np.arange(r))
+    M = (U * s) @ V.T
+    return (M / np.linalg.norm(M)).reshape(shape)
+
+
+@pytest.mark.parametrize("move_right", [1, 0])
+@pytest.mark.parametrize("shape,chi_max,eps", [((8, 2, 2, 8), 100, 0.0), ((40, 2, 2, 30), 20, 0.0),
+                                               ((64, 2, 2, 64), 1000, 1e-10), ((20, 5, 5, 16), 50, 1e-12)])
+def test_split_parity(ctx, move_right, shape, chi_max, eps):
+    theta = _split_case(11, shape, 0.35)
+    a_ref, b_ref, info = od.split_svd(theta, chi_max, eps, bool(move_right))
+    chi_l, d1, d2, chi_r = shape
+    cap = min(chi_l * d1, d2 * chi_r)
+    A1 = torch.empty(chi_l * d1 * cap, dtype=torch.float64, device="cuda:0")
+    A2 = torch.empty(cap * d2 * chi_r, dtype=torch.float64, device="cuda:0")
+    chn, disc, ent, lam2 = B.osmps_split(ctx, dev(theta), A1, A2, move_right, chi_max, eps)
+    assert chn == info["keep"]
+    big = info["lam2"] > 1e-6
+    np.testing.assert_allclose(lam2[big], info["lam2"][big], rtol=1e-12)
+    assert abs(disc - info["discarded"]) <= 1e-13
+    assert abs(ent - info["entropy"]) <= 1e-12
+    a = A1[: chi_l * d1 * chn].cpu().numpy().reshape(chi_l, d1, chn)
+    b = A2[: chn * d2 * chi_r].cpu().numpy().reshape(chn, d2, chi_r)
+    # gauge-invariant comparison: the truncated, renormalised two-site tensor
+    np.testing.assert_allclose(np.tensordot(a, b, axes=([2], [0])),
+                               np.tensordot(a_ref, b_ref, axes=([2], [0])), atol=1e-11)
+    if move_right:
+        assert od.left_isometry_defect(a) < 1e-12
+    else:
+        assert od.right_isometry_defect(b) < 1e-12
+
+
+def _xxz_operator(L, k, chi, seed):
+    W = hamiltonians.xxz(L, 1.0, 1.0, 0.0)
+    mps = od.right_canonicalize(inputs.random_mps(L, 2, chi, seed=seed))
+    Renv = od.build_right_envs(W, mps)
+    Lenv = np.ones((1, 1, 1))
+    for j in range(k):  # shift centre to k with QR so that L is built on isometries
+        chl, d, chr_ = mps[j].shape
+        Q, Rm = np.linalg.qr(mps[j].reshape(chl * d, chr_))
+        mps[j] = Q.reshape(chl, d, Q.shape[1])
+        mps[j + 1] = np.tensordot(Rm, mps[j + 1], axes=([1], [0]))
+        Lenv = od.env_left(Lenv, mps[j], W[j])
+    theta = np.tensordot(mps[k], mps[k + 1], axes=([2], [0]))
+    return Lenv, W[k], W[k + 1], Renv[k + 2], theta
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x3"])
+def test_lanczos_parity(ctx, prec):
+    Lenv, W1, W2, Renv, theta = _xxz_operator(12, 5, 32, seed=2)
+    mv = lambda x: od.heff_apply(Lenv, W1, W2, Renv, x)
+    e_ref, x_ref, it_ref, _ = od.lanczos_ground(mv, theta, 100, 1e-12)
+    th = dev(theta)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    e, it, res, ok = B.osmps_lanczos_ground(ctx, dev(Lenv), dev(W1), dev(W2), dev(Renv), th,
+                                            max_iter=100, tol=tol, precision=prec)
+    x = th.cpu().numpy()
+    assert abs(np.linalg.norm(x) - 1.0) < 1e-12
+    if prec == "fp64":
+        assert ok
+        assert abs(e - e_ref) <= 1e-10 * abs(e_ref)
+        assert abs(abs(np.vdot(x, x_ref)) - 1.0) < 1e-9
+    else:
+        # a perturbed operator: the Ritz value carries the matvec error linearly,
+        # the Rayleigh quotient with the exact operator is accurate to second order
+        assert abs(e - e_ref) <= 1e-5 * abs(e_ref)
+        rq = float(np.vdot(x, mv(x)))
+        assert abs(rq - e_ref) <= 1e-8 * abs(e_ref)
+
+
+def test_lanczos_max_iter_reports_noconv(ctx):
+    Lenv, W1, W2, Renv, theta = _xxz_operator(10, 4, 16, seed=3)
+    th = dev(theta)
+    e, it, res, ok = B.osmps_lanczos_ground(ctx, dev(Lenv), dev(W1), dev(W2), dev(Renv), th,
+                                            max_iter=2, tol=1e-14, precision="fp64")
+    assert not ok and it == 2
+    assert abs(torch.linalg.norm(th).item() - 1.0) < 1e-12  # best pair still written
+
+
+def test_invalid_arguments_are_reported(ctx):
+    Lh, W1, W2, Rh, th = (dev(x) for x in inputs.random_heff_operands(4, 2, 2, 4, 3, 3, 3))
+    with pytest.raises(B.OsmpsError) as e:
+        B.osmps_heff_apply(ctx, Lh, W1, W2, Rh, th, th, precision="fp64")
+    assert e.value.status == 1  # y aliases theta
+    with pytest.raises(B.OsmpsError) as e:
+        B.osmps_heff_apply(ctx, Lh, W1, W2, Rh, th, torch.empty_like(th), precision=7)
+    assert e.value.status == 1
+    with pytest.raises(B.OsmpsError) as e:
+        B.osmps_lanczos_ground(ctx, Lh, W1, W2, Rh, th, max_iter=0)
+    assert e.value.status == 1
+    z = torch.zeros_like(th)
+    with pytest.raises(B.OsmpsError) as e:
+        B.osmps_lanczos_ground(ctx, Lh, W1, W2, Rh, z, max_iter=5)
+    assert e.value.status == 1  # zero start vector

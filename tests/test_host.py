@@ -1,0 +1,85 @@
+"""Host-side checks that need no GPU: the library builds and exports every
+symbol declared in include/osmps.h, the binding covers them, and the
+library's MPO builder agrees with the oracle's."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import mpo as ompo
+from paper_1703_00387_gb300 import binding, hamiltonians, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "osmps.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(osmps_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    if not os.path.exists(binding.LIB_PATH):
+        from paper_1703_00387_gb300 import build
+        build.build()
+    return binding.lib()
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(built_lib, name), f"{name} declared in osmps.h but not exported"
+
+
+def test_binding_covers_header():
+    assert sorted(binding.exported_symbols()) == _declared()
+
+
+def test_status_strings(built_lib):
+    for code, name in binding.STATUS.items():
+        assert built_lib.osmps_status_string(code).decode() == name
+
+
+def test_ctx_create_without_gpu_reports_error(built_lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes
+    p = ctypes.c_void_p()
+    st = built_lib.osmps_ctx_create(0, 0, ctypes.byref(p))
+    assert st != 0
+    assert b"device" in built_lib.osmps_last_error().lower() or st == 4
+
+
+@pytest.mark.parametrize("name", ["ising", "xxz", "bh"])
+def test_mpo_builders_agree_with_oracle(name):
+    if name == "ising":
+        a, b = hamiltonians.ising(7, 0.9, 1.3), ompo.ising_mpo(7, 0.9, 1.3)
+    elif name == "xxz":
+        J, h = inputs.random_couplings(7, seed=4)
+        a, b = hamiltonians.xxz(7, J, 0.6, h), ompo.xxz_mpo(7, J, 0.6, h)
+    else:
+        a, b = hamiltonians.bose_hubbard(5, 1.0, 4.0, 4), ompo.bose_hubbard_mpo(5, 1.0, 4.0, 4)
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x.shape, y.shape)
+        np.testing.assert_allclose(x, y, atol=1e-15)
+
+
+def test_aklt_builder_same_operator():
+    np.testing.assert_allclose(ompo.mpo_to_dense(hamiltonians.aklt(4)),
+                               ompo.mpo_to_dense(ompo.aklt_mpo(4)), atol=1e-13)
+
+
+def test_seeded_inputs_are_deterministic():
+    a = inputs.random_mps(10, 2, 16, seed=0)
+    b = inputs.random_mps(10, 2, 16, seed=0)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    assert [t.shape[0] for t in a] == inputs.bond_dims(10, 2, 16)[:10]
+    batch = inputs.chain_batch(64, seed=0)
+    assert len(batch) == 64 and all(16 <= c["L"] <= 128 for c in batch)
