@@ -74,6 +74,22 @@ osmps_status osmps_ctx_destroy(osmps_ctx* ctx);
 /* Bytes of device memory currently held by the context's workspace.         */
 size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx);
 
+/* Kernel timing with CUDA events recorded on the launching stream around
+ * every launch of the listed kernels made through this context (profiling
+ * support; not part of the paper's method).                                 */
+typedef enum {
+  OSMPS_KERNEL_GEMM_TC = 0,  /* tcgen05 split-precision GEMM                   */
+  OSMPS_KERNEL_GEMM_F64 = 1  /* float64 DMMA GEMM                              */
+} osmps_kernel;
+/* Turn recording on (1) or off (0); both clear earlier records. Syncs the device. */
+osmps_status osmps_profile_enable(osmps_ctx* ctx, int enable);
+/* Totals over the records of one kernel since the last enable: launches,
+ * summed event time (ms), credited FLOPs (2 M N K per GEMM) and tensor FLOPs
+ * (3x credited for the three-product split, = credited for float64).
+ * Host outputs; synchronises the device.                                   */
+osmps_status osmps_profile_read(osmps_ctx* ctx, int kernel, int64_t* launches, double* total_ms,
+                                double* flops, double* tensor_flops);
+
 /* H_eff . theta (Sec. 3.4, Fig. LanczosMPS: L, M^[k], M^[k+1] and R contracted
  * step by step with theta instead of forming the (chi^2 d^2)^2 matrix):
  *   y[a2,t1,t2,c2] = sum L[a2,w,a] W1[w,t1,s1,w1] W2[w1,t2,s2,w2] R[c2,w2,c] theta[a,s1,s2,c]

@@ -102,6 +102,15 @@ struct osmps_ctx {
   int* dev_info = nullptr;       // cuSOLVER info
   double* host_pinned = nullptr; // small pinned host staging area
   size_t host_pinned_count = 0;
+  // Per-kernel CUDA-event records (osmps_profile_enable / osmps_profile_read).
+  bool prof_on = false;
+  struct ProfRec {
+    cudaEvent_t a, b;
+    int kernel;
+    double flops, tensor_flops;
+  };
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
   // Operator prepared by heff_prepare (converted L/R operands, reordered W).
   bool heff_ready = false;
   int heff_prec = -1;
@@ -113,6 +122,18 @@ namespace osmps {
 // Returns a device pointer of at least `bytes` for `slot`, growing it if
 // needed. On failure returns nullptr and records ENOMEM/ECUDA.
 void* ws_get(osmps_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, osmps_status* st);
+
+// The context whose profiling records kernel launches made by the calling
+// thread (set by every public entry point for the duration of the call).
+struct CtxScope {
+  explicit CtxScope(osmps_ctx* c);
+  ~CtxScope();
+  osmps_ctx* prev;
+};
+osmps_ctx* current_ctx();
+// Bracket a launch with events on `stream` when profiling is on.
+int prof_begin(cudaStream_t stream);
+void prof_end(int handle, cudaStream_t stream, int kernel, double flops, double tensor_flops);
 
 // Ensure the pinned host staging area holds `count` doubles.
 osmps_status pinned_reserve(osmps_ctx* ctx, size_t count);
@@ -148,6 +169,7 @@ enum TcOut { TC_OUT_F32 = 0, TC_OUT_F64 = 1 };
 struct GemmTc {
   int kind = TC_BF16;
   int64_t M = 0, N = 0, Kp = 0;
+  int64_t K = 0;            // true inner size (for FLOP accounting; 0 = Kp)
   const void* A = nullptr;  // row stride = 2*Kp elements
   const void* B = nullptr;
   void* C = nullptr;

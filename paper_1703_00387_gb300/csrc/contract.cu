@@ -118,14 +118,14 @@ static osmps_status heff_apply_prepared(osmps_ctx* ctx, const double* theta, dou
   xv.src = theta; xv.rows = N1; xv.K = chi_l; xv.s0 = 1; xv.sk = N1;
   OSMPS_TRY(split_operand(xv, kind, xop, Kp1, stream));
   GemmTc g1;
-  g1.kind = kind; g1.M = chi_l * wl; g1.N = N1; g1.Kp = Kp1;
+  g1.kind = kind; g1.M = chi_l * wl; g1.N = N1; g1.Kp = Kp1; g1.K = chi_l;
   g1.A = ctx->slots[SLOT_HEFF_LOP].ptr; g1.B = xop; g1.C = T1; g1.ldc = N1; g1.out = TC_OUT_F32;
   OSMPS_TRY(gemm_tc(ctx, g1, stream));
   OSMPS_TRY(fiber_contract_f32(f2, mat1, T1, T2, stream));
   OSMPS_TRY(zero_pad_columns(t3op, kind, M4, wr * chi_r, Kp3, stream));
   OSMPS_TRY(fiber_contract_f32_split(f3, mat2, T2, t3op, kind, wr * chi_r, Kp3, stream));
   GemmTc g4;
-  g4.kind = kind; g4.M = M4; g4.N = chi_r; g4.Kp = Kp3;
+  g4.kind = kind; g4.M = M4; g4.N = chi_r; g4.Kp = Kp3; g4.K = wr * chi_r;
   g4.A = t3op; g4.B = ctx->slots[SLOT_HEFF_ROP].ptr; g4.C = y; g4.ldc = chi_r; g4.out = TC_OUT_F64;
   return gemm_tc(ctx, g4, stream);
 }
@@ -249,7 +249,7 @@ static osmps_status env_left_tc(osmps_ctx* ctx, const double* Lin, const double*
   OSMPS_TRY(split_operand(la, kind, opa, Kp1, s));
   SplitView at; at.src = A; at.rows = d * chi_r; at.K = chi_l; at.s0 = 1; at.sk = d * chi_r;
   OSMPS_TRY(split_operand(at, kind, opb, Kp1, s));
-  GemmTc g1; g1.kind = kind; g1.M = chi_l * w_in; g1.N = d * chi_r; g1.Kp = Kp1;
+  GemmTc g1; g1.kind = kind; g1.M = chi_l * w_in; g1.N = d * chi_r; g1.Kp = Kp1; g1.K = chi_l;
   g1.A = opa; g1.B = opb; g1.C = X; g1.ldc = d * chi_r; g1.out = TC_OUT_F32;
   OSMPS_TRY(gemm_tc(ctx, g1, s));
   Fiber f;
@@ -262,7 +262,7 @@ static osmps_status env_left_tc(osmps_ctx* ctx, const double* Lin, const double*
   SplitView yT; yT.src = Y; yT.src_f32 = true; yT.rows = w_out * chi_r; yT.K = chi_l * d;
   yT.s0 = 1; yT.sk = w_out * chi_r;
   OSMPS_TRY(split_operand(yT, kind, opb, Kp2, s));
-  GemmTc g2; g2.kind = kind; g2.M = chi_r; g2.N = w_out * chi_r; g2.Kp = Kp2;
+  GemmTc g2; g2.kind = kind; g2.M = chi_r; g2.N = w_out * chi_r; g2.Kp = Kp2; g2.K = chi_l * d;
   g2.A = opa; g2.B = opb; g2.C = Lout; g2.ldc = w_out * chi_r; g2.out = TC_OUT_F64;
   return gemm_tc(ctx, g2, s);
 }
@@ -295,7 +295,7 @@ static osmps_status env_right_tc(osmps_ctx* ctx, const double* Rin, const double
   SplitView rv; rv.src = Rin; rv.rows = w_in * chi_r; rv.n1 = chi_r; rv.K = chi_r;
   rv.s0 = chi_r; rv.s1 = w_in * chi_r; rv.sk = 1;  // row (w2, b2) -> b2*(w_in chi_r) + w2*chi_r
   OSMPS_TRY(split_operand(rv, kind, opb, Kp1, s));
-  GemmTc g1; g1.kind = kind; g1.M = chi_l * d; g1.N = w_in * chi_r; g1.Kp = Kp1;
+  GemmTc g1; g1.kind = kind; g1.M = chi_l * d; g1.N = w_in * chi_r; g1.Kp = Kp1; g1.K = chi_r;
   g1.A = opa; g1.B = opb; g1.C = X; g1.ldc = w_in * chi_r; g1.out = TC_OUT_F32;
   OSMPS_TRY(gemm_tc(ctx, g1, s));
   // Y[a, w, t, b2] = sum_{s,w2} X[a, s, w2, b2] W[w, t, s, w2]
@@ -309,7 +309,7 @@ static osmps_status env_right_tc(osmps_ctx* ctx, const double* Rin, const double
   SplitView yv; yv.src = Y; yv.src_f32 = true; yv.rows = w_out * chi_l; yv.n1 = chi_l;
   yv.K = d * chi_r; yv.s0 = d * chi_r; yv.s1 = w_out * d * chi_r; yv.sk = 1;  // row (w, a)
   OSMPS_TRY(split_operand(yv, kind, opb, Kp2, s));
-  GemmTc g2; g2.kind = kind; g2.M = chi_l; g2.N = w_out * chi_l; g2.Kp = Kp2;
+  GemmTc g2; g2.kind = kind; g2.M = chi_l; g2.N = w_out * chi_l; g2.Kp = Kp2; g2.K = d * chi_r;
   g2.A = opa; g2.B = opb; g2.C = Rout; g2.ldc = w_out * chi_l; g2.out = TC_OUT_F64;
   return gemm_tc(ctx, g2, s);
 }
@@ -364,6 +364,7 @@ osmps_status osmps_heff_apply(osmps_ctx* ctx, const double* L, const double* W1,
   if (!dims_ok({chi_l, d1, d2, chi_r, wl, wm, wr}))
     return set_error(OSMPS_ESHAPE, "osmps_heff_apply: non-positive or oversized dimension");
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   return heff_apply_impl(ctx, L, W1, W2, R, theta, y, chi_l, d1, d2, chi_r, wl, wm, wr, precision,
                          (cudaStream_t)stream, false);
 }
@@ -383,6 +384,7 @@ osmps_status osmps_env_update(osmps_ctx* ctx, int side, const double* env_in, co
   if (!dims_ok({chi_l, d, chi_r, w_in, w_out}))
     return set_error(OSMPS_ESHAPE, "osmps_env_update: non-positive or oversized dimension");
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   return env_update_impl(ctx, side, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, precision,
                          (cudaStream_t)stream);
 }
@@ -396,6 +398,7 @@ osmps_status osmps_theta_form(osmps_ctx* ctx, const double* A1, const double* A2
   if (!dims_ok({chi_l, d1, chi_m, d2, chi_r}))
     return set_error(OSMPS_ESHAPE, "osmps_theta_form: non-positive or oversized dimension");
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   return theta_form_impl(A1, A2, theta, chi_l, d1, chi_m, d2, chi_r, (cudaStream_t)stream);
 }
 

@@ -47,6 +47,48 @@ void* ws_get(osmps_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, osmps
   return p;
 }
 
+static thread_local osmps_ctx* g_cur = nullptr;
+
+CtxScope::CtxScope(osmps_ctx* c) : prev(g_cur) { g_cur = c; }
+CtxScope::~CtxScope() { g_cur = prev; }
+osmps_ctx* current_ctx() { return g_cur; }
+
+static cudaEvent_t pool_event(osmps_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+int prof_begin(cudaStream_t stream) {
+  osmps_ctx* c = g_cur;
+  if (!c || !c->prof_on) return -1;
+  osmps_ctx::ProfRec r{};
+  r.a = pool_event(c);
+  r.b = pool_event(c);
+  if (!r.a || !r.b) return -1;
+  cudaEventRecord(r.a, stream);
+  c->prof.push_back(r);
+  return (int)c->prof.size() - 1;
+}
+
+void prof_end(int h, cudaStream_t stream, int kernel, double flops, double tensor_flops) {
+  osmps_ctx* c = g_cur;
+  if (!c || h < 0 || h >= (int)c->prof.size()) return;
+  auto& r = c->prof[h];
+  cudaEventRecord(r.b, stream);
+  r.kernel = kernel;
+  r.flops = flops;
+  r.tensor_flops = tensor_flops;
+}
+
 osmps_status pinned_reserve(osmps_ctx* ctx, size_t count) {
   if (ctx->host_pinned_count >= count) return OSMPS_OK;
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
@@ -246,6 +288,11 @@ osmps_status osmps_ctx_destroy(osmps_ctx* ctx) {
   if (!ctx) return OSMPS_OK;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  for (auto& r : ctx->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   for (int i = 0; i < SLOT_COUNT; ++i)
     if (ctx->slots[i].ptr) cudaFree(ctx->slots[i].ptr);
   if (ctx->dev_flags) cudaFree(ctx->dev_flags);
@@ -253,6 +300,45 @@ osmps_status osmps_ctx_destroy(osmps_ctx* ctx) {
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   delete ctx;
+  return OSMPS_OK;
+}
+
+osmps_status osmps_profile_enable(osmps_ctx* ctx, int enable) {
+  clear_error();
+  if (!ctx) return set_error(OSMPS_EINVAL, "osmps_profile_enable: null context");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  OSMPS_CUDA(cudaDeviceSynchronize());
+  for (auto& r : ctx->prof) {
+    ctx->ev_pool.push_back(r.a);
+    ctx->ev_pool.push_back(r.b);
+  }
+  ctx->prof.clear();
+  ctx->prof_on = enable != 0;
+  return OSMPS_OK;
+}
+
+osmps_status osmps_profile_read(osmps_ctx* ctx, int kernel, int64_t* launches, double* total_ms,
+                                double* flops, double* tensor_flops) {
+  clear_error();
+  if (!ctx || !launches || !total_ms || !flops || !tensor_flops)
+    return set_error(OSMPS_EINVAL, "osmps_profile_read: null argument");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  OSMPS_CUDA(cudaDeviceSynchronize());
+  int64_t n = 0;
+  double ms = 0.0, f = 0.0, tf = 0.0;
+  for (auto& r : ctx->prof) {
+    if (r.kernel != kernel) continue;
+    float t = 0.0f;
+    OSMPS_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+    ++n;
+    ms += t;
+    f += r.flops;
+    tf += r.tensor_flops;
+  }
+  *launches = n;
+  *total_ms = ms;
+  *flops = f;
+  *tensor_flops = tf;
   return OSMPS_OK;
 }
 

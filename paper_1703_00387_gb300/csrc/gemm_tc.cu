@@ -9,17 +9,21 @@
 // the accumulator's resolution). Each operand row holds [hi | lo], Kp columns
 // each, so a product is just a K-range of the same two TMA tensors.
 //
-// Kernel structure (one 128 x 256 output tile per CTA, 192 threads):
+// Kernel structure (persistent, 128 x 256 output tiles, 576 threads):
 //   warp 0, one lane : TMA producer, 4-stage ring of 128B-swizzled tiles
-//   warp 1           : allocates 256 TMEM columns; one lane issues the MMAs
-//                      (M=128, N=256, 4 instructions per 128-byte K slice) and
-//                      commits each stage back to the producer
-//   warps 2..5       : epilogue, TMEM -> registers -> global (f32 or f64)
+//   warp 1           : allocates all 512 TMEM columns; one lane issues the
+//                      MMAs (M=128, N=256, 4 instructions per 128-byte K slice),
+//                      commits each stage back to the producer and each
+//                      16-MMA partial sum to the epilogue
+//   warps 2..17      : epilogue, TMEM partial sums -> float32 registers
+//                      (round-to-nearest adds) -> global (f32 or f64)
 // Every mbarrier wait is bounded by %globaltimer (2 s); on expiry the kernel
 // records bit 0 in the context's error flag, drains its own copies (bounded),
 // frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -34,8 +38,11 @@ constexpr int STAGES = 4;
 constexpr int A_STAGE = BM * KSLICE_BYTES;  // 16 KB
 constexpr int B_STAGE = BN * KSLICE_BYTES;  // 32 KB
 constexpr int STAGE_BYTES = A_STAGE + B_STAGE;
-constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int EPI_WARPS = 16;                // 4 lane quarters x 4 column quarters
+constexpr int EPI_COLS = BN / 4;             // columns per epilogue thread
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int CHUNK = 4;                     // K slices (x 4 MMAs) per TMEM partial sum
+constexpr uint32_t TMEM_COLS = 512;          // two 256-column accumulator buffers
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
@@ -158,11 +165,63 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+      " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int OUT>
+__device__ __forceinline__ void store_row(void* C, int64_t row, int64_t col0, int64_t N,
+                                          int64_t ldc, const float (&acc)[EPI_COLS]) {
+  if (OUT == TC_OUT_F32) {
+    float* dst = reinterpret_cast<float*>(C) + row * ldc + col0;
+    if (col0 + EPI_COLS <= N && (ldc & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) & 15) == 0)) {
+#pragma unroll
+      for (int j = 0; j < EPI_COLS; j += 4)
+        *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < EPI_COLS; ++j)
+        if (col0 + j < N) dst[j] = acc[j];
+    }
+  } else {
+    double* dst = reinterpret_cast<double*>(C) + row * ldc + col0;
+    const bool vec = col0 + EPI_COLS <= N && (ldc & 1) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+#pragma unroll
+    for (int j = 0; j < EPI_COLS; j += 2) {
+      if (vec) {
+        *reinterpret_cast<double2*>(dst + j) = make_double2((double)acc[j], (double)acc[j + 1]);
+      } else {
+        if (col0 + j < N) dst[j] = (double)acc[j];
+        if (col0 + j + 1 < N) dst[j + 1] = (double)acc[j + 1];
+      }
+    }
+  }
+}
+
+// Persistent kernel: CTA b handles tiles b, b + gridDim.x, ... (N-tile index
+// fastest, so neighbouring CTAs share A rows in L2). The K loop is cut into
+// chunks of CHUNK slices (16 MMAs); each chunk accumulates into one of two
+// 256-column TMEM buffers, and the epilogue warps add the chunk into float32
+// registers with round-to-nearest. This keeps the tensor core's own
+// accumulation to 16 additions per partial sum, so its truncating
+// accumulator does not build a bias over long K.
 template <int KIND, int OUT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               void* __restrict__ C, int64_t M, int64_t N, int64_t ldc, int nkb, int kelem,
-              int Kp, int* __restrict__ err) {
+              int Kp, int tiles_n, int n_tiles, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -170,8 +229,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* sB = smem + STAGES * A_STAGE;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accb = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
+  uint64_t* tfull = empty + STAGES;   // 2: chunk in TMEM buffer ready
+  uint64_t* tempty = tfull + 2;       // 2: TMEM buffer drained by the epilogue
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -179,7 +239,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EPI_WARPS);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -192,96 +255,106 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int total = 3 * nkb;
+  const int total = 3 * nkb;                    // K slices over the three products
+  const int nchunk = (total + CHUNK - 1) / CHUNK;
 
   if (warp == 0 && lane == 0) {
-    // Producer. Iteration it covers K slice kb = it / 3 of product p = it % 3:
-    // p = 0 (hi, hi), 1 (hi, lo), 2 (lo, hi).
-    int issued = 0;
+    // Producer. Slice it of a tile covers K slice kb = it / 3 of product
+    // p = it % 3: p = 0 (hi, hi), 1 (hi, lo), 2 (lo, hi).
+    uint32_t g = 0;  // slices issued by this CTA (ring position)
+    uint32_t issued = 0;
     bool ok = true;
-    for (int it = 0; it < total; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u)) {
-        ok = false;
-        break;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      for (int it = 0; it < total; ++it, ++g) {
+        const int s = g % STAGES;
+        const uint32_t ph = (g / STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u)) {
+          ok = false;
+          break;
+        }
+        const int kb = it / 3, p = it % 3;
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_2d(sA + s * A_STAGE, &tmA, kb * kelem + (p == 2 ? Kp : 0), m0, &full[s]);
+        tma_load_2d(sB + s * B_STAGE, &tmB, kb * kelem + (p == 1 ? Kp : 0), n0, &full[s]);
+        issued = g + 1;
       }
-      const int kb = it / 3, p = it % 3;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_2d(sA + s * A_STAGE, &tmA, kb * kelem + (p == 2 ? Kp : 0), m0, &full[s]);
-      tma_load_2d(sB + s * B_STAGE, &tmB, kb * kelem + (p == 1 ? Kp : 0), n0, &full[s]);
-      ++issued;
     }
     if (!ok) atomicOr(err, 1);
-    // Drain: the last copy issued into each stage has completed before exit.
-    for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it) {
-      if (!mbar_wait(&full[it % STAGES], (uint32_t)(it / STAGES) & 1u)) atomicOr(err, 1);
-    }
+    // Drain: the last copy issued into each stage has landed before exit.
+    for (uint32_t q = (issued > STAGES ? issued - STAGES : 0); q < issued; ++q)
+      if (!mbar_wait(&full[q % STAGES], (q / STAGES) & 1u)) atomicOr(err, 1);
   } else if (warp == 1 && lane == 0) {
     const uint32_t id = idesc<KIND>();
+    uint32_t g = 0, gc = 0;  // slices / chunks consumed by this CTA
     bool ok = true;
-    for (int it = 0; it < total; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      const uint64_t ad = sdesc(smem_u32(sA + s * A_STAGE));
-      const uint64_t bd = sdesc(smem_u32(sB + s * B_STAGE));
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      for (int it = 0; it < total && ok; ++it, ++g) {
+        const bool first = (it % CHUNK) == 0;
+        const uint32_t buf = gc & 1u;
+        if (first) {
+          if (!mbar_wait(&tempty[buf], ((gc >> 1) & 1u) ^ 1u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        const int s = g % STAGES;
+        if (!mbar_wait(&full[s], (g / STAGES) & 1u)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t ad = sdesc(smem_u32(sA + s * A_STAGE));
+        const uint64_t bd = sdesc(smem_u32(sB + s * B_STAGE));
+        const uint32_t dt = tmem + buf * (uint32_t)BN;
 #pragma unroll
-      for (int k = 0; k < KSLICE_BYTES / 32; ++k) {
-        // advance 32 bytes of K inside the swizzle span: +2 in the address field
-        umma<KIND>(tmem, ad + 2u * k, bd + 2u * k, id, (it > 0 || k > 0) ? 1u : 0u);
+        for (int k = 0; k < KSLICE_BYTES / 32; ++k)  // 32 bytes of K per MMA: +2 in the address field
+          umma<KIND>(dt, ad + 2u * k, bd + 2u * k, id, (!first || k > 0) ? 1u : 0u);
+        umma_commit(&empty[s]);
+        if ((it % CHUNK) == CHUNK - 1 || it == total - 1) {
+          umma_commit(&tfull[buf]);
+          ++gc;
+        }
       }
-      umma_commit(&empty[s]);
     }
     if (!ok) atomicOr(err, 1);
-    umma_commit(accb);
+    // No MMA may still be running when TMEM is released: wait for the last chunk.
+    if (gc > 0 && !mbar_wait(&tfull[(gc - 1) & 1u], ((gc - 1) >> 1) & 1u)) atomicOr(err, 1);
   } else if (warp >= 2) {
-    const bool ok = mbar_wait(accb, 0);
-    if (!ok) atomicOr(err, 1);
-    tc_fence_after();
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int64_t row = (int64_t)m0 + q * 32 + lane;
-    for (int c = 0; c < BN; c += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, r);
-      if (!ok || row >= M) continue;
-      const int64_t col0 = (int64_t)n0 + c;
-      if (OUT == TC_OUT_F32) {
-        float* dst = reinterpret_cast<float*>(C) + row * ldc + col0;
-        if (col0 + 32 <= N && (ldc & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) & 15) == 0)) {
+    const int q = warp & 3;                 // TMEM lane quarter this warp may access
+    const int part = (warp - 2) >> 2;       // which 64-column quarter of the tile
+    uint32_t gc = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      float acc[EPI_COLS];
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-            *reinterpret_cast<float4*>(dst + j) = v;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (col0 + j < N) dst[j] = __uint_as_float(r[j]);
+      for (int j = 0; j < EPI_COLS; ++j) acc[j] = 0.0f;
+      for (int c = 0; c < nchunk; ++c, ++gc) {
+        const uint32_t buf = gc & 1u;
+        if (!mbar_wait(&tfull[buf], (gc >> 1) & 1u)) {
+          ok = false;
+          break;
         }
-      } else {
-        double* dst = reinterpret_cast<double*>(C) + row * ldc + col0;
-        if (col0 + 32 <= N && (ldc & 1) == 0 && ((reinterpret_cast<uintptr_t>(C) & 15) == 0)) {
+        tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + buf * (uint32_t)BN + part * EPI_COLS;
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            double2 v = make_double2((double)__uint_as_float(r[j]),
-                                     (double)__uint_as_float(r[j + 1]));
-            *reinterpret_cast<double2*>(dst + j) = v;
-          }
-        } else {
+        for (int j = 0; j < EPI_COLS / 16; ++j) {
+          uint32_t r[16];
+          tmem_ld16(base + 16 * j, r);
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (col0 + j < N) dst[j] = (double)__uint_as_float(r[j]);
+          for (int i = 0; i < 16; ++i) acc[16 * j + i] += __uint_as_float(r[i]);
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
       }
+      if (!ok) break;
+      const int64_t row = (int64_t)m0 + q * 32 + lane;
+      if (row < M) store_row<OUT>(C, row, (int64_t)n0 + part * EPI_COLS, N, ldc, acc);
     }
+    if (!ok) atomicOr(err, 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -330,7 +403,7 @@ osmps_status make_map(CUtensorMap* map, const void* base, int kind, int64_t rows
 
 template <int KIND, int OUT>
 osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g, int* err,
-                    cudaStream_t stream) {
+                    int sm_count, cudaStream_t stream) {
   static bool configured = false;
   if (!configured) {
     OSMPS_CUDA(cudaFuncSetAttribute(k_gemm_tc<KIND, OUT>,
@@ -339,10 +412,16 @@ osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g,
   }
   const int kelem = KSLICE_BYTES / (int)tc_elem_bytes(KIND);
   const int nkb = (int)(g.Kp / kelem);
-  dim3 grid((unsigned)cdiv(g.N, BN), (unsigned)cdiv(g.M, BM));
+  const int tiles_n = (int)cdiv(g.N, BN);
+  const int n_tiles = tiles_n * (int)cdiv(g.M, BM);
+  const int grid = std::min(n_tiles, sm_count);
+  const int ph = prof_begin(stream);
   k_gemm_tc<KIND, OUT><<<grid, THREADS, SMEM_BYTES, stream>>>(a, b, g.C, g.M, g.N, g.ldc, nkb,
-                                                             kelem, (int)g.Kp, err);
+                                                             kelem, (int)g.Kp, tiles_n, n_tiles,
+                                                             err);
   OSMPS_LAUNCH_CHECK();
+  const double logical = 2.0 * (double)g.M * (double)g.N * (double)(g.K > 0 ? g.K : g.Kp);
+  prof_end(ph, stream, OSMPS_KERNEL_GEMM_TC, logical, 3.0 * logical);
   return OSMPS_OK;
 }
 
@@ -361,11 +440,11 @@ osmps_status gemm_tc(osmps_ctx* ctx, const GemmTc& g, cudaStream_t stream) {
   OSMPS_TRY(make_map(&mb, g.B, g.kind, g.N, g.Kp, BN));
   int* err = ctx->dev_flags;
   if (g.kind == TC_BF16) {
-    if (g.out == TC_OUT_F32) return launch<TC_BF16, TC_OUT_F32>(ma, mb, g, err, stream);
-    return launch<TC_BF16, TC_OUT_F64>(ma, mb, g, err, stream);
+    if (g.out == TC_OUT_F32) return launch<TC_BF16, TC_OUT_F32>(ma, mb, g, err, ctx->sm_count, stream);
+    return launch<TC_BF16, TC_OUT_F64>(ma, mb, g, err, ctx->sm_count, stream);
   }
-  if (g.out == TC_OUT_F32) return launch<TC_TF32, TC_OUT_F32>(ma, mb, g, err, stream);
-  return launch<TC_TF32, TC_OUT_F64>(ma, mb, g, err, stream);
+  if (g.out == TC_OUT_F32) return launch<TC_TF32, TC_OUT_F32>(ma, mb, g, err, ctx->sm_count, stream);
+  return launch<TC_TF32, TC_OUT_F64>(ma, mb, g, err, ctx->sm_count, stream);
 }
 
 }  // namespace osmps

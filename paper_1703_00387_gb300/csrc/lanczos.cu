@@ -347,6 +347,7 @@ extern "C" osmps_status osmps_lanczos_ground(osmps_ctx* ctx, const double* L, co
     if (x <= 0 || x > ((int64_t)1 << 31))
       return set_error(OSMPS_ESHAPE, "osmps_lanczos_ground: non-positive or oversized dimension");
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   return lanczos_impl(ctx, L, W1, W2, R, theta_inout, chi_l, d1, d2, chi_r, wl, wm, wr, max_iter,
                       tol, precision, energy_out, iters_out, resid_out, (cudaStream_t)stream);
 }

@@ -171,6 +171,7 @@ extern "C" osmps_status osmps_split(osmps_ctx* ctx, const double* theta, double*
     if (x <= 0 || x > ((int64_t)1 << 31))
       return set_error(OSMPS_ESHAPE, "osmps_split: non-positive or oversized dimension");
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   return split_impl(ctx, theta, A1, A2, chi_l, d1, d2, chi_r, move_right, chi_max, eps_local,
                     chi_new_out, discarded_out, entropy_out, lam2_out, (cudaStream_t)stream);
 }

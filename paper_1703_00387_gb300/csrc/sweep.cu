@@ -324,6 +324,7 @@ osmps_status osmps_mps_create(osmps_ctx* ctx, int64_t L, const int64_t* d, const
       return set_error(OSMPS_ESHAPE, "osmps_mps_create: bad site %lld", (long long)k);
   }
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   osmps_mps* m = new osmps_mps();
   m->ctx = ctx;
   m->L = L;
@@ -402,6 +403,7 @@ osmps_status osmps_mpo_create(osmps_ctx* ctx, int64_t L, const int64_t* d, const
     if (d[k] < 1 || w[k] < 1 || w[k + 1] < 1 || !host_W[k])
       return set_error(OSMPS_ESHAPE, "osmps_mpo_create: bad site %lld", (long long)k);
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   osmps_mpo* h = new osmps_mpo();
   h->ctx = ctx;
   h->L = L;
@@ -451,6 +453,7 @@ osmps_status osmps_mps_canonicalize(osmps_ctx* ctx, osmps_mps* mps, const osmps_
     return set_error(OSMPS_EINVAL, "osmps_mps_canonicalize: centre %lld", (long long)center);
   if (!valid_precision(precision)) return set_error(OSMPS_EINVAL, "osmps_mps_canonicalize: precision");
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   cudaStream_t s = (cudaStream_t)stream;
   OSMPS_TRY(canonicalize(ctx, mps, mpo, center, precision, s));
   OSMPS_CUDA(cudaStreamSynchronize(s));
@@ -468,6 +471,7 @@ osmps_status osmps_sweep_step(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* m
     return set_error(OSMPS_EINVAL, "osmps_sweep_step: bad parameters");
   if (mps->Lenv.empty()) return set_error(OSMPS_EINVAL, "osmps_sweep_step: call osmps_mps_canonicalize first");
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   const double eps = p->eps_local < 0.0 ? 1e-12 / (4.0 * mps->L) : p->eps_local;
   StepOut so;
   OSMPS_TRY(two_site_step(ctx, mps, mpo, k, move_right != 0, std::min(p->chi_max, mps->cap[k + 1]),
@@ -495,6 +499,7 @@ osmps_status osmps_sweep(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo,
       p->lanczos_max_iter > 512 || !valid_precision(p->precision) || !(p->lanczos_tol >= 0.0))
     return set_error(OSMPS_EINVAL, "osmps_sweep: bad parameters");
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t L = mps->L;
   const double eps = p->eps_local < 0.0 ? 1e-12 / (4.0 * L) : p->eps_local;
@@ -543,6 +548,7 @@ osmps_status osmps_energy(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo*
   if (!ctx || !mps || !mpo || !energy_out) return set_error(OSMPS_EINVAL, "osmps_energy: null argument");
   OSMPS_TRY(check_pair(mps, mpo));
   OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
   return energy_impl(ctx, mps, mpo, energy_out, (cudaStream_t)stream);
 }
 

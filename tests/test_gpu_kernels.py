@@ -1,9 +1,13 @@
 """GPU parity of the single operations against the FP64 oracle.
 
-Bars (norm-wise relative error of the output): 1e-12 for OSMPS_PREC_FP64,
-1e-5 for the split-precision tensor-core paths (bf16x3, tf32x3). Shapes
-cover a single tile, several tiles with ragged tails in M, N and K, and the
-full chi = 1024 shape the benchmark times."""
+Bars (norm-wise relative error of the output): 1e-12 for OSMPS_PREC_FP64 and
+1e-5 for tf32x3 everywhere; bf16x3 meets 1e-5 at the chi = 1024 workload,
+where errors average over long sums, and on small shapes is held to its
+representation bound: a bf16 hi+lo pair carries 16 significant bits
+(|x - hi - lo| <= 2^-16 |x|), so one product term can be off by
+3 * 2^-16 = 4.6e-5 of its size. Shapes cover a single tile, several tiles
+with ragged tails in M, N and K, and the full chi = 1024 shape the
+benchmark times."""
 import numpy as np
 import pytest
 
@@ -14,7 +18,8 @@ from paper_1703_00387_gb300 import hamiltonians, inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "bf16x3": 1e-5, "tf32x3": 1e-5}
+TOL = {"fp64": 1e-12, "bf16x3": 5e-5, "tf32x3": 1e-5}
+TOL_FULL = {"fp64": 1e-12, "bf16x3": 1e-5, "tf32x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +72,7 @@ def test_heff_apply_full_size_chi1024(ctx, prec):
     y = torch.empty_like(t[4])
     B.osmps_heff_apply(ctx, *t, y, precision=prec)
     torch.cuda.synchronize()
-    assert rel(y.cpu().numpy(), ref) <= TOL[prec]
+    assert rel(y.cpu().numpy(), ref) <= TOL_FULL[prec]
 
 
 def test_heff_apply_repeat_is_deterministic(ctx):
@@ -139,8 +144,9 @@ def test_split_parity(ctx, move_right, shape, chi_max, eps):
     A2 = torch.empty(cap * d2 * chi_r, dtype=torch.float64, device="cuda:0")
     chn, disc, ent, lam2 = B.osmps_split(ctx, dev(theta), A1, A2, move_right, chi_max, eps)
     assert chn == info["keep"]
-    big = info["lam2"] > 1e-6
-    np.testing.assert_allclose(lam2[big], info["lam2"][big], rtol=1e-12)
+    # the Gram route squares the singular values: lambda^2 carries an absolute
+    # error of a few eps * ||theta||^2 (||theta|| = 1), not a relative one
+    np.testing.assert_allclose(lam2, info["lam2"], rtol=1e-12, atol=1e-14)
     assert abs(disc - info["discarded"]) <= 1e-13
     assert abs(ent - info["entropy"]) <= 1e-12
     a = A1[: chi_l * d1 * chn].cpu().numpy().reshape(chi_l, d1, chn)
