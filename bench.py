@@ -1,0 +1,456 @@
+"""Benchmark: two-site DMRG steps at chi = 1024 (XXZ chain, L = 128, d = 2, w = 5).
+
+A step is one pass of the whole hot path at a saturated bulk bond: theta
+formation, Lanczos on H_eff (each iteration one H_eff.theta product plus
+float64 reorthogonalisation), the float64 Gram/eigendecomposition split with
+truncation, and the environment update. Steps walk the orthogonality centre
+to the right from bond 40, so every timed step is a genuine step of a sweep.
+
+Reported value: credited H_eff.theta FLOPs executed in the timed steps
+divided by the timed wall time (logical TFLOP/s; identity environment
+channels are not credited). Also reported: ms per step, a full left-right-
+left sweep at chi_max = 1024 (seconds), the plain float64 GPU path on the same
+steps, the roofline of the dominant kernel (tcgen05 GEMM, timed per launch
+with CUDA events on its stream), an end-to-end number through the C ABI with
+host buffers, and the CPU oracle on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_SITES, D, W_MPO, CHI = 128, 2, 5, 1024
+CENTER0 = 40
+LANCZOS_CAP, LANCZOS_TOL = 20, 1e-10
+WORKLOAD = ("XXZ chain J=1 Delta=1, L=128, d=2, MPO w=5, chi_max=1024: two-site DMRG steps "
+            "at saturated bulk bonds (theta, Lanczos on H_eff.theta, Gram/eig split, env update)")
+METRIC = "H_eff.theta TFLOP/s at chi=1024 within DMRG steps (XXZ L=128); sweep seconds reported alongside"
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense tensor ratio
+
+
+def heff_credited_flops(chi_l, chi_r, d1=D, d2=D, wl=W_MPO, wm=W_MPO, wr=W_MPO):
+    """Algorithmic FLOPs of one H_eff.theta: the two GEMM stages without the
+    identity channel of L (last) and of R (first), plus the two W-steps."""
+    nl, nr = max(wl - 1, 1), max(wr - 1, 1)
+    return (2.0 * d1 * d2 * chi_l * chi_r * (nl * chi_l + nr * chi_r)
+            + 2.0 * chi_l * chi_r * d1 * d2 * (d1 * wl * wm + d2 * wm * wr))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, max, throttle reasons) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier_max(value, ws):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier_sum(value, ws):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and the reference arm only)
+# ---------------------------------------------------------------------------
+def oracle_step_sample(seed=0):
+    """One oracle two-site step at chi=1024 on seeded symmetric environments:
+    theta formation, Lanczos (same cap), eigendecomposition split, env update.
+    Returns (seconds, credited FLOPs, iterations)."""
+    from oracle import dmrg as od
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+    W = hamiltonians.xxz(L_SITES, 1.0, 1.0, 0.0)
+    k = CENTER0
+    Lenv = inputs.random_symmetric_env(CHI, W_MPO, seed=seed)
+    Renv = inputs.random_symmetric_env(CHI, W_MPO, seed=seed + 1)
+    rng = np.random.default_rng(seed + 2)
+    A1 = rng.standard_normal((CHI, D, CHI // 2))
+    A2 = rng.standard_normal((CHI // 2, D, CHI))
+    t0 = time.perf_counter()
+    theta = np.tensordot(A1, A2, axes=([2], [0]))
+    mv = lambda x: od.heff_apply(Lenv, W[k], W[k + 1], Renv, x)
+    e, theta, iters, _ = od.lanczos_ground(mv, theta, LANCZOS_CAP, LANCZOS_TOL)
+    a, b, info = od.split_eig(theta, CHI, 1e-12 / (4 * L_SITES), True)
+    od.env_left(Lenv, a, W[k])
+    dt = time.perf_counter() - t0
+    return dt, iters * heff_credited_flops(CHI, CHI), iters
+
+
+def cpu_threads():
+    return os.cpu_count()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    for i in range(args.warmup):
+        oracle_step_sample(seed=100 + i)
+    total_t, total_f = 0.0, 0.0
+    for i in range(args.steps):
+        dt, f, _ = oracle_step_sample(seed=i)
+        total_t += dt
+        total_f += f
+    value = total_f / total_t / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "chi": CHI, "L": L_SITES, "lanczos_cap": LANCZOS_CAP},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": "per step: one FP64 NumPy two-site step at chi=1024 on seeded "
+                                   "symmetric environments"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1703_00387_gb300 import binding as B
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    B.lib()  # raises if the library is missing: no fallback
+    stream = torch.cuda.current_stream()
+    ctx = B.Context(local)
+    prec = args.precision
+    Wh = hamiltonians.xxz(L_SITES, 1.0, 1.0, 0.0)
+    mpo = B.MPO(ctx, Wh)
+    mps = B.MPS(ctx, inputs.random_mps(L_SITES, D, CHI, seed=rank), chi_cap=CHI)
+    B.osmps_mps_canonicalize(ctx, mps, mpo, CENTER0, prec)
+    params = B.sweep_params(CHI, 1, prec, lanczos_tol=LANCZOS_TOL, lanczos_max_iter=LANCZOS_CAP)
+
+    k = CENTER0
+    for _ in range(args.warmup):
+        B.osmps_sweep_step(ctx, mps, mpo, k, 1, params)
+        k += 1
+    torch.cuda.synchronize()
+    barrier(ws)
+    sampler = ClockSampler(local)
+    sampler.start()
+    B.osmps_profile_enable(ctx, True)
+    launches0 = B.osmps_kernel_launches()
+    torch.cuda.synchronize()
+    barrier(ws)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    flops, iters = 0.0, []
+    for _ in range(args.steps):
+        out = B.osmps_sweep_step(ctx, mps, mpo, k, 1, params)
+        chi = mps.bond_dims()
+        flops += out["iters"] * heff_credited_flops(chi[k], chi[k + 2])
+        iters.append(out["iters"])
+        k += 1
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = B.osmps_kernel_launches() - launches0
+    prof = B.osmps_profile_read(ctx, "gemm_tc")
+    B.osmps_profile_enable(ctx, False)
+    clocks = sampler.stop()
+    t_max = barrier_max(elapsed, ws)
+    flops_all = barrier_sum(flops, ws)
+    value = flops_all / t_max / 1e12
+
+    peaks, peak_src = load_peaks()
+    peak_bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    peak = peak_bf16 * (TF32_OVER_BF16 if prec == "tf32x3" else 1.0)
+    achieved = (prof["tensor_flops"] / (prof["ms"] / 1e3) / 1e12) if prof["ms"] > 0 else None
+    roofline = {"kernel": "k_gemm_tc (tcgen05 split-precision GEMM)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained" + (" x 1.1/2.25 (tf32)" if prec == "tf32x3" else ""),
+                "launches": prof["launches"],
+                "avg_launch_ms": prof["ms"] / max(prof["launches"], 1),
+                "share_of_step_time": prof["ms"] / 1e3 / elapsed if elapsed > 0 else None,
+                "traffic": traffic_per_launch(prof)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (contractions " + prec + ")",
+        "data": "synthetic (seeded random MPS, XXZ MPO)",
+        "config": {"workload": WORKLOAD, "chi": CHI, "L": L_SITES, "d": D, "w": W_MPO,
+                   "precision": prec, "lanczos_cap": LANCZOS_CAP, "lanczos_tol": LANCZOS_TOL,
+                   "lanczos_iters": iters, "l2": "inputs larger than L2 (each step streams ~1 GB: "
+                                                 "20 Krylov vectors of 33.5 MB, 42 MB environments)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+    }
+
+    if rank == 0 and not args.quick:
+        line["fp64_gpu"] = fp64_leg(B, ctx, mps, mpo, k, args)
+        k = line["fp64_gpu"].pop("_k")
+        line["e2e"] = e2e_leg(B, ctx, Wh, prec, args)
+        if not args.no_sweep:
+            line["sweep_s"] = sweep_leg(B, ctx, mpo, prec)
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"], line["matvec_rel_err"] = cpu_leg(B, ctx, Wh)
+    mps.close()
+    mpo.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def traffic_per_launch(prof):
+    """DRAM bytes per launch of k_gemm_tc from the committed ncu summary, if the
+    kernel source is unchanged since it was taken (else null)."""
+    p = os.path.join(ROOT, "profiles", "gemm_tc_traffic.json")
+    src = os.path.join(ROOT, "paper_1703_00387_gb300", "csrc", "gemm_tc.cu")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if d.get("gemm_tc_sha256") != h:
+        return None
+    return d.get("bytes_per_launch")
+
+
+def fp64_leg(B, ctx, mps, mpo, k, args):
+    import torch
+    params = B.sweep_params(CHI, 1, "fp64", lanczos_tol=LANCZOS_TOL, lanczos_max_iter=LANCZOS_CAP)
+    B.osmps_sweep_step(ctx, mps, mpo, k, 1, params)  # warm-up
+    k += 1
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    flops, n = 0.0, args.fp64_steps
+    for _ in range(n):
+        out = B.osmps_sweep_step(ctx, mps, mpo, k, 1, params)
+        chi = mps.bond_dims()
+        flops += out["iters"] * heff_credited_flops(chi[k], chi[k + 2])
+        k += 1
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "ms_per_step": 1e3 * dt / n, "steps": n,
+            "_k": k}
+
+
+def e2e_leg(B, ctx, Wh, prec, args):
+    """The same step through the standalone C-ABI calls with inputs in pinned
+    host memory: copies host->device, theta, Lanczos, split, env update, and
+    device->host copies of the new site tensors, environment and energy."""
+    import torch
+    from paper_1703_00387_gb300 import inputs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    k = CENTER0
+    rng = np.random.default_rng(7)
+    host = {
+        "L": torch.from_numpy(inputs.random_symmetric_env(CHI, W_MPO, seed=11)).pin_memory(),
+        "R": torch.from_numpy(inputs.random_symmetric_env(CHI, W_MPO, seed=12)).pin_memory(),
+        "A1": torch.from_numpy(rng.standard_normal((CHI, D, CHI // 2))).pin_memory(),
+        "A2": torch.from_numpy(rng.standard_normal((CHI // 2, D, CHI))).pin_memory(),
+        "W1": torch.from_numpy(np.ascontiguousarray(Wh[k])).pin_memory(),
+        "W2": torch.from_numpy(np.ascontiguousarray(Wh[k + 1])).pin_memory(),
+    }
+    out_host = {"A1": torch.empty(CHI * D * CHI, dtype=torch.float64).pin_memory(),
+                "A2": torch.empty(CHI * D * CHI, dtype=torch.float64).pin_memory(),
+                "Lout": torch.empty(CHI * W_MPO * CHI, dtype=torch.float64).pin_memory()}
+    d = {n: torch.empty_like(t, device=dev) for n, t in host.items()}
+    theta = torch.empty((CHI, D, D, CHI), dtype=torch.float64, device=dev)
+    A1o = torch.empty(CHI * D * CHI, dtype=torch.float64, device=dev)
+    A2o = torch.empty(CHI * D * CHI, dtype=torch.float64, device=dev)
+    Lout = torch.empty(CHI * W_MPO * CHI, dtype=torch.float64, device=dev)
+    h2d = sum(t.numel() * 8 for t in host.values())
+    d2h = sum(t.numel() * 8 for t in out_host.values()) + 8
+
+    def one():
+        for n in host:
+            d[n].copy_(host[n], non_blocking=True)
+        B.osmps_theta_form(ctx, d["A1"], d["A2"], theta)
+        e, it, _, _ = B.osmps_lanczos_ground(ctx, d["L"], d["W1"], d["W2"], d["R"], theta,
+                                             max_iter=LANCZOS_CAP, tol=LANCZOS_TOL, precision=prec)
+        chn, _, _, _ = B.osmps_split(ctx, theta, A1o, A2o, 1, CHI, 1e-12 / (4 * L_SITES))
+        A1v = A1o[: CHI * D * chn].view(CHI, D, chn)
+        Lv = Lout[: chn * W_MPO * chn].view(chn, W_MPO, chn)
+        B.osmps_env_update(ctx, 0, d["L"], A1v, d["W1"], Lv, precision=prec)
+        out_host["A1"].copy_(A1o, non_blocking=True)
+        out_host["A2"].copy_(A2o, non_blocking=True)
+        out_host["Lout"].copy_(Lout, non_blocking=True)
+        torch.cuda.synchronize()
+        return it, e
+
+    one()
+    t0 = time.perf_counter()
+    flops = 0.0
+    n = max(1, min(args.steps, 3))
+    for _ in range(n):
+        it, _ = one()
+        flops += it * heff_credited_flops(CHI, CHI)
+    dt = time.perf_counter() - t0
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": n, "ms_per_step": 1e3 * dt / n}
+
+
+def sweep_leg(B, ctx, mpo, prec):
+    """One full left->right->left sweep at chi_max = 1024 from a fresh seeded MPS."""
+    import torch
+    from paper_1703_00387_gb300 import inputs
+    mps = B.MPS(ctx, inputs.random_mps(L_SITES, D, CHI, seed=123), chi_cap=CHI)
+    p = B.sweep_params(CHI, 1, prec, lanczos_tol=LANCZOS_TOL, lanczos_max_iter=LANCZOS_CAP)
+    torch.cuda.synchronize()
+    st = B.osmps_sweep(ctx, mps, mpo, p, record_steps=False)
+    mps.close()
+    return {"seconds": st["seconds"], "steps": st["steps"], "lanczos_iters": st["lanczos_iters"],
+            "precision": prec, "energy_fp64": st["energy"],
+            "note": "includes QR canonicalisation, environment build and the final float64 energy"}
+
+
+def cpu_leg(B, ctx, Wh):
+    import torch
+    from oracle import dmrg as od
+    from paper_1703_00387_gb300 import inputs
+    dt, f, it = oracle_step_sample(seed=0)
+    base = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"one FP64 NumPy two-site step at chi=1024 ({it} Lanczos matvecs), {dt:.1f} s"}
+    # matvec error of the GPU path at this size against the oracle
+    k = CENTER0
+    Lh = inputs.random_symmetric_env(CHI, W_MPO, seed=21)
+    Rh = inputs.random_symmetric_env(CHI, W_MPO, seed=22)
+    th = np.random.default_rng(23).standard_normal((CHI, D, D, CHI))
+    ref = od.heff_apply(Lh, Wh[k], Wh[k + 1], Rh, th)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (Lh, Wh[k], Wh[k + 1], Rh, th)]
+    errs = {}
+    for prec in ("bf16x3", "tf32x3", "fp64"):
+        y = torch.empty_like(t[4])
+        B.osmps_heff_apply(ctx, *t, y, precision=prec)
+        torch.cuda.synchronize()
+        errs[prec] = float(np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref))
+    return base, errs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="timed steps only (for profiler runs)")
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.quick:
+        raise SystemExit("--warmup must be >= 3")
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -89,6 +89,9 @@ osmps_status osmps_profile_enable(osmps_ctx* ctx, int enable);
  * Host outputs; synchronises the device.                                   */
 osmps_status osmps_profile_read(osmps_ctx* ctx, int kernel, int64_t* launches, double* total_ms,
                                 double* flops, double* tensor_flops);
+/* Number of kernels this library has launched since it was loaded (its own
+ * kernels only; cuSOLVER's are not counted).                               */
+int64_t osmps_kernel_launches(void);
 
 /* H_eff . theta (Sec. 3.4, Fig. LanczosMPS: L, M^[k], M^[k+1] and R contracted
  * step by step with theta instead of forming the (chi^2 d^2)^2 matrix):

@@ -26,6 +26,9 @@ def right_canonicalize(mps):
 
     Every site k >= 1 becomes right-canonical: sum_{s,b} A[a,s,b] A[a2,s,b] =
     delta(a, a2). Returns a new list; bond dimensions may shrink to the rank.
+    The state is only defined up to a scalar, so the site receiving R is
+    rescaled to unit norm at each shift; otherwise the norm of a long random
+    chain (about sqrt(d chi^2) per site) overflows float64.
     """
     mps = [np.array(A, dtype=np.float64, copy=True) for A in mps]
     for k in range(len(mps) - 1, 0, -1):
@@ -35,6 +38,7 @@ def right_canonicalize(mps):
         m = Q.shape[1]
         mps[k] = Q.T.reshape(m, d, chr_)
         mps[k - 1] = np.tensordot(mps[k - 1], Rm.T, axes=([2], [0]))
+        mps[k - 1] = mps[k - 1] / np.linalg.norm(mps[k - 1])
     mps[0] = mps[0] / np.linalg.norm(mps[0])
     return mps
 

@@ -59,6 +59,9 @@ _SIGS = {
     "osmps_ctx_create": (_c.c_int, [_c.c_int, _c.c_size_t, _c.POINTER(_vp)]),
     "osmps_ctx_destroy": (_c.c_int, [_vp]),
     "osmps_ctx_workspace_bytes": (_c.c_size_t, [_vp]),
+    "osmps_profile_enable": (_c.c_int, [_vp, _c.c_int]),
+    "osmps_profile_read": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_i64), _dp, _dp, _dp]),
+    "osmps_kernel_launches": (_i64, []),
     "osmps_heff_apply": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 + [_c.c_int, _vp]),
     "osmps_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_c.c_int, _vp]),
     "osmps_lanczos_ground": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 +
@@ -151,6 +154,26 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+KERNEL = {"gemm_tc": 0, "gemm_f64": 1}
+
+
+def osmps_profile_enable(ctx, enable=True):
+    _check(lib().osmps_profile_enable(ctx.ptr, 1 if enable else 0))
+
+
+def osmps_profile_read(ctx, kernel):
+    """Returns dict(launches, ms, flops, tensor_flops) since the last enable."""
+    n = _i64()
+    ms, f, tf = _c.c_double(), _c.c_double(), _c.c_double()
+    _check(lib().osmps_profile_read(ctx.ptr, KERNEL[kernel] if isinstance(kernel, str) else int(kernel),
+                                    _c.byref(n), _c.byref(ms), _c.byref(f), _c.byref(tf)))
+    return dict(launches=n.value, ms=ms.value, flops=f.value, tensor_flops=tf.value)
+
+
+def osmps_kernel_launches():
+    return int(lib().osmps_kernel_launches())
 
 
 def osmps_heff_apply(ctx, L, W1, W2, R, theta, y, precision="bf16x3", stream=None):

@@ -83,6 +83,7 @@ enum Slot {
   SLOT_SWEEP_ENV,
   SLOT_SWEEP_ENV2,
   SLOT_RED,
+  SLOT_NORM,
   SLOT_COUNT
 };
 
@@ -134,6 +135,9 @@ osmps_ctx* current_ctx();
 // Bracket a launch with events on `stream` when profiling is on.
 int prof_begin(cudaStream_t stream);
 void prof_end(int handle, cudaStream_t stream, int kernel, double flops, double tensor_flops);
+
+// Count of kernels this library has launched (all threads, all contexts).
+void note_launch();
 
 // Ensure the pinned host staging area holds `count` doubles.
 osmps_status pinned_reserve(osmps_ctx* ctx, size_t count);

@@ -1,4 +1,5 @@
 // Context, error reporting, workspace and float64 vector primitives.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -48,6 +49,9 @@ void* ws_get(osmps_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, osmps
 }
 
 static thread_local osmps_ctx* g_cur = nullptr;
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 CtxScope::CtxScope(osmps_ctx* c) : prev(g_cur) { g_cur = c; }
 CtxScope::~CtxScope() { g_cur = prev; }
@@ -152,8 +156,8 @@ osmps_status vec_norm2(osmps_ctx* ctx, const double* x, int64_t n, double* dev_o
   double* part = (double*)ws_get(ctx, SLOT_RED, RED_MAX_BLOCKS * sizeof(double), s, &st);
   if (!part) return st;
   int nb = red_blocks(n);
-  k_sumsq_partial<<<nb, RED_THREADS, 0, s>>>(x, n, part);
-  k_sum_final<<<1, RED_THREADS, 0, s>>>(part, nb, dev_out);
+  { k_sumsq_partial<<<nb, RED_THREADS, 0, s>>>(x, n, part); note_launch(); }
+  { k_sum_final<<<1, RED_THREADS, 0, s>>>(part, nb, dev_out); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }
@@ -181,14 +185,14 @@ static int ew_blocks(int64_t n) {
 }
 
 osmps_status vec_scale_by_inv_sqrt(double* x, int64_t n, const double* dev_norm2, cudaStream_t s) {
-  k_scale_inv_sqrt<<<ew_blocks(n), 256, 0, s>>>(x, n, dev_norm2);
+  { k_scale_inv_sqrt<<<ew_blocks(n), 256, 0, s>>>(x, n, dev_norm2); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }
 
 osmps_status vec_scale_by_inv(double* y, const double* x, int64_t n, const double* dev_div,
                               cudaStream_t s) {
-  k_scale_inv<<<ew_blocks(n), 256, 0, s>>>(y, x, n, dev_div);
+  { k_scale_inv<<<ew_blocks(n), 256, 0, s>>>(y, x, n, dev_div); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }
@@ -203,7 +207,7 @@ __global__ void k_nonfinite(const double* __restrict__ x, int64_t n, int* __rest
 
 osmps_status check_finite(osmps_ctx* ctx, const double* x, int64_t n, cudaStream_t s, bool* ok) {
   OSMPS_CUDA(cudaMemsetAsync(ctx->dev_flags + 1, 0, sizeof(int), s));
-  k_nonfinite<<<ew_blocks(n), 256, 0, s>>>(x, n, ctx->dev_flags + 1);
+  { k_nonfinite<<<ew_blocks(n), 256, 0, s>>>(x, n, ctx->dev_flags + 1); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   int h = 0;
   OSMPS_CUDA(cudaMemcpyAsync(&h, ctx->dev_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -341,6 +345,8 @@ osmps_status osmps_profile_read(osmps_ctx* ctx, int kernel, int64_t* launches, d
   *tensor_flops = tf;
   return OSMPS_OK;
 }
+
+int64_t osmps_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx) {
   if (!ctx) return 0;

@@ -141,10 +141,10 @@ osmps_status gemm_f64(const GemmF64& g, cudaStream_t stream) {
   dim3 grid((unsigned)cdiv(g.N, BN), (unsigned)cdiv(g.M, BM), (unsigned)g.batch);
   bool akf = (g.sak == 1), bnf = (g.sbn == 1);
   const int ph = prof_begin(stream);
-  if (akf && bnf) k_gemm_f64<true, true><<<grid, THREADS, 0, stream>>>(a);
-  else if (akf) k_gemm_f64<true, false><<<grid, THREADS, 0, stream>>>(a);
-  else if (bnf) k_gemm_f64<false, true><<<grid, THREADS, 0, stream>>>(a);
-  else k_gemm_f64<false, false><<<grid, THREADS, 0, stream>>>(a);
+  if (akf && bnf) { k_gemm_f64<true, true><<<grid, THREADS, 0, stream>>>(a); note_launch(); }
+  else if (akf) { k_gemm_f64<true, false><<<grid, THREADS, 0, stream>>>(a); note_launch(); }
+  else if (bnf) { k_gemm_f64<false, true><<<grid, THREADS, 0, stream>>>(a); note_launch(); }
+  else { k_gemm_f64<false, false><<<grid, THREADS, 0, stream>>>(a); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   const double f = 2.0 * (double)g.M * (double)g.N * (double)g.K * (double)g.batch;
   prof_end(ph, stream, OSMPS_KERNEL_GEMM_F64, f, f);

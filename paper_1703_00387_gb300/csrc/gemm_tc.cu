@@ -416,9 +416,9 @@ osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g,
   const int n_tiles = tiles_n * (int)cdiv(g.M, BM);
   const int grid = std::min(n_tiles, sm_count);
   const int ph = prof_begin(stream);
-  k_gemm_tc<KIND, OUT><<<grid, THREADS, SMEM_BYTES, stream>>>(a, b, g.C, g.M, g.N, g.ldc, nkb,
+  { k_gemm_tc<KIND, OUT><<<grid, THREADS, SMEM_BYTES, stream>>>(a, b, g.C, g.M, g.N, g.ldc, nkb,
                                                              kelem, (int)g.Kp, tiles_n, n_tiles,
-                                                             err);
+                                                             err); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   const double logical = 2.0 * (double)g.M * (double)g.N * (double)(g.K > 0 ? g.K : g.Kp);
   prof_end(ph, stream, OSMPS_KERNEL_GEMM_TC, logical, 3.0 * logical);

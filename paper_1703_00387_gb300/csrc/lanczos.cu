@@ -237,9 +237,9 @@ int ew_blocks(int64_t n) {
 osmps_status project(osmps_ctx* ctx, const double* V, int64_t n, int nv, double* w, double* part,
                      double* coef, cudaStream_t s) {
   const int nb = dot_blocks(n);
-  k_multidot<<<nb, DOT_THREADS, 0, s>>>(V, n, nv, w, n, part);
-  k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef);
-  k_combine<<<ew_blocks(n), 256, 0, s>>>(V, n, nv, coef, w, n, 0);
+  { k_multidot<<<nb, DOT_THREADS, 0, s>>>(V, n, nv, w, n, part); note_launch(); }
+  { k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef); note_launch(); }
+  { k_combine<<<ew_blocks(n), 256, 0, s>>>(V, n, nv, coef, w, n, 0); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }
@@ -285,7 +285,7 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
     OSMPS_TRY(project(ctx, V, n, j + 1, w, part, sc + OFF_C1, s));
     OSMPS_TRY(project(ctx, V, n, j + 1, w, part, sc + OFF_C2, s));
     OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, s));
-    k_tridiag<<<1, 256, 0, s>>>(sc, j);
+    { k_tridiag<<<1, 256, 0, s>>>(sc, j); note_launch(); }
     OSMPS_LAUNCH_CHECK();
     OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC, 3 * 8, cudaMemcpyDeviceToHost, s));
     OSMPS_CUDA(cudaStreamSynchronize(s));
@@ -303,7 +303,7 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
     OSMPS_TRY(vec_scale_by_inv(V + (int64_t)(j + 1) * n, w, n, sc + OFF_BETA + j, s));
   }
   // Ritz vector theta = sum_i s_i v_i, normalised
-  k_combine<<<ew_blocks(n), 256, 0, s>>>(V, n, m, sc + OFF_S, theta, n, 1);
+  { k_combine<<<ew_blocks(n), 256, 0, s>>>(V, n, m, sc + OFF_S, theta, n, 1); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   OSMPS_TRY(vec_norm2(ctx, theta, n, sc + OFF_MISC + 4, s));
   OSMPS_TRY(vec_scale_by_inv_sqrt(theta, n, sc + OFF_MISC + 4, s));

@@ -143,19 +143,19 @@ osmps_status fiber_dispatch(const Fiber& f, const double* Mat, const T* in, T* o
   if (f.Q <= 8) {
     auto k = k_fiber<T, 8, MODE>;
     if (sm > 48 * 1024) OSMPS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp);
+    { k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp); note_launch(); }
   } else if (f.Q <= 16) {
     auto k = k_fiber<T, 16, MODE>;
     if (sm > 48 * 1024) OSMPS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp);
+    { k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp); note_launch(); }
   } else if (f.Q <= 32) {
     auto k = k_fiber<T, 32, MODE>;
     if (sm > 48 * 1024) OSMPS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp);
+    { k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp); note_launch(); }
   } else if (f.Q <= 64) {
     auto k = k_fiber<T, 64, MODE>;
     if (sm > 48 * 1024) OSMPS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp);
+    { k<<<blocks, threads, sm, s>>>(f, Mat, in, out, sdst, Kcols, Kp); note_launch(); }
   } else {
     return set_error(OSMPS_EUNSUPPORTED, "W-step: output block %lld > 64", (long long)f.Q);
   }
@@ -205,14 +205,14 @@ osmps_status split_operand(const SplitView& v, int kind, void* dst, int64_t Kp, 
   if (Kp < v.K || Kp % 64 != 0) return set_error(OSMPS_ESHAPE, "split_operand: bad Kp");
   if (v.sk == 1 || v.K == 1) {
     const int blocks = grid_for(v.rows * Kp, 256);
-    if (kind == TC_BF16) k_split_direct<TC_BF16><<<blocks, 256, 0, s>>>(v, dst, Kp);
-    else k_split_direct<TC_TF32><<<blocks, 256, 0, s>>>(v, dst, Kp);
+    if (kind == TC_BF16) { k_split_direct<TC_BF16><<<blocks, 256, 0, s>>>(v, dst, Kp); note_launch(); }
+    else { k_split_direct<TC_TF32><<<blocks, 256, 0, s>>>(v, dst, Kp); note_launch(); }
   } else {
     if (cdiv(Kp, 32) > 65535) return set_error(OSMPS_ESHAPE, "split_operand: K too large");
     dim3 grid((unsigned)cdiv(v.rows, 32), (unsigned)cdiv(Kp, 32));
     dim3 block(32, 8);
-    if (kind == TC_BF16) k_split_transpose<TC_BF16><<<grid, block, 0, s>>>(v, dst, Kp);
-    else k_split_transpose<TC_TF32><<<grid, block, 0, s>>>(v, dst, Kp);
+    if (kind == TC_BF16) { k_split_transpose<TC_BF16><<<grid, block, 0, s>>>(v, dst, Kp); note_launch(); }
+    else { k_split_transpose<TC_TF32><<<grid, block, 0, s>>>(v, dst, Kp); note_launch(); }
   }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
@@ -239,8 +239,8 @@ osmps_status zero_pad_columns(void* dst, int kind, int64_t rows, int64_t Kcols, 
                               cudaStream_t s) {
   if (Kp <= Kcols || rows <= 0) return OSMPS_OK;
   const int blocks = grid_for(rows * (Kp - Kcols), 256);
-  if (kind == TC_BF16) k_zero_pad<TC_BF16><<<blocks, 256, 0, s>>>(dst, rows, Kcols, Kp);
-  else k_zero_pad<TC_TF32><<<blocks, 256, 0, s>>>(dst, rows, Kcols, Kp);
+  if (kind == TC_BF16) { k_zero_pad<TC_BF16><<<blocks, 256, 0, s>>>(dst, rows, Kcols, Kp); note_launch(); }
+  else { k_zero_pad<TC_TF32><<<blocks, 256, 0, s>>>(dst, rows, Kcols, Kp); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }
@@ -248,7 +248,7 @@ osmps_status zero_pad_columns(void* dst, int kind, int64_t rows, int64_t Kcols, 
 osmps_status w_reorder(const double* W, int64_t dw, int64_t d, int64_t dw2, int order, double* Mat,
                        cudaStream_t s) {
   const int64_t total = dw * d * d * dw2;
-  k_w_reorder<<<grid_for(total, 256), 256, 0, s>>>(W, dw, d, dw2, order, Mat);
+  { k_w_reorder<<<grid_for(total, 256), 256, 0, s>>>(W, dw, d, dw2, order, Mat); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }

@@ -123,7 +123,7 @@ osmps_status split_impl(osmps_ctx* ctx, const double* theta, double* A1, double*
   if (!nrm) return st;
   if (move_right) {
     // A1[(a,s1), j] = U[:, j];  A2[j, (s2,c)] = sum_r A1[r, j] M[r, (s2,c)]
-    k_gather_cols<<<blocks_for(n * keep), 256, 0, s>>>(G, n, keep, A1);
+    { k_gather_cols<<<blocks_for(n * keep), 256, 0, s>>>(G, n, keep, A1); note_launch(); }
     OSMPS_LAUNCH_CHECK();
     GemmF64 p;
     p.M = keep; p.N = cols; p.K = rows;
@@ -135,7 +135,7 @@ osmps_status split_impl(osmps_ctx* ctx, const double* theta, double* A1, double*
     OSMPS_TRY(vec_scale_by_inv_sqrt(A2, keep * cols, nrm, s));
   } else {
     // A2[j, (s2,c)] = V[:, j]^T;  A1[(a,s1), j] = sum_c M[(a,s1), c] A2[j, c]
-    k_gather_rows<<<blocks_for(n * keep), 256, 0, s>>>(G, n, keep, A2);
+    { k_gather_rows<<<blocks_for(n * keep), 256, 0, s>>>(G, n, keep, A2); note_launch(); }
     OSMPS_LAUNCH_CHECK();
     GemmF64 p;
     p.M = rows; p.N = keep; p.K = cols;

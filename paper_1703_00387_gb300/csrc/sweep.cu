@@ -56,7 +56,7 @@ __global__ void k_transpose(const double* __restrict__ src, int64_t rows, int64_
 osmps_status transpose(const double* src, int64_t rows, int64_t cols, double* dst, cudaStream_t s) {
   dim3 grid((unsigned)cdiv(cols, 32), (unsigned)cdiv(rows, 32));
   if (grid.y > 65535) return set_error(OSMPS_ESHAPE, "transpose: %lld rows", (long long)rows);
-  k_transpose<<<grid, dim3(32, 8), 0, s>>>(src, rows, cols, dst);
+  { k_transpose<<<grid, dim3(32, 8), 0, s>>>(src, rows, cols, dst); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }
@@ -103,7 +103,7 @@ osmps_status qr_inplace(osmps_ctx* ctx, double* X, int64_t nr, int64_t nc, doubl
   double* work = (double*)ws_get(ctx, SLOT_QR_WORK, (size_t)lw * 8, s, &st);
   if (!work) return st;
   OSMPS_SOLVER(cusolverDnDgeqrf(ctx->solver, (int)nr, (int)nc, X, (int)nr, tau, work, lw, ctx->dev_info));
-  k_extract_r<<<nblk(r * nc), 256, 0, s>>>(X, nr, nc, r, Rout);
+  { k_extract_r<<<nblk(r * nc), 256, 0, s>>>(X, nr, nc, r, Rout); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   OSMPS_SOLVER(cusolverDnDorgqr(ctx->solver, (int)nr, (int)r, (int)r, X, (int)nr, tau, work, lw, ctx->dev_info));
   *r_out = r;
@@ -134,7 +134,12 @@ osmps_status shift_right(osmps_ctx* ctx, osmps_mps* m, int64_t k, cudaStream_t s
   OSMPS_TRY(gemm_f64(g, s));
   OSMPS_CUDA(cudaMemcpyAsync(m->A[k + 1], tmp, (size_t)r * d2 * chr2 * 8, cudaMemcpyDeviceToDevice, s));
   m->chi[k + 1] = r;
-  return OSMPS_OK;
+  // The state is defined up to a scalar: keep the receiving tensor at unit
+  // norm so that products of many unnormalised sites cannot overflow.
+  double* nrm = (double*)ws_get(ctx, SLOT_NORM, 64, s, &st);
+  if (!nrm) return st;
+  OSMPS_TRY(vec_norm2(ctx, m->A[k + 1], r * d2 * chr2, nrm, s));
+  return vec_scale_by_inv_sqrt(m->A[k + 1], r * d2 * chr2, nrm, s);
 }
 
 // Make site k right-canonical and push R^T into site k-1.
@@ -157,7 +162,10 @@ osmps_status shift_left(osmps_ctx* ctx, osmps_mps* m, int64_t k, cudaStream_t s)
   OSMPS_TRY(gemm_f64(g, s));
   OSMPS_CUDA(cudaMemcpyAsync(m->A[k - 1], tmp, (size_t)chl0 * d0 * r * 8, cudaMemcpyDeviceToDevice, s));
   m->chi[k] = r;
-  return OSMPS_OK;
+  double* nrm = (double*)ws_get(ctx, SLOT_NORM, 64, s, &st);  // unit norm, as in shift_right
+  if (!nrm) return st;
+  OSMPS_TRY(vec_norm2(ctx, m->A[k - 1], chl0 * d0 * r, nrm, s));
+  return vec_scale_by_inv_sqrt(m->A[k - 1], chl0 * d0 * r, nrm, s);
 }
 
 osmps_status ensure_envs(osmps_ctx* ctx, osmps_mps* m, const osmps_mpo* h, cudaStream_t s) {
@@ -179,8 +187,8 @@ osmps_status ensure_envs(osmps_ctx* ctx, osmps_mps* m, const osmps_mpo* h, cudaS
     }
   }
   m->env_w = h->w;
-  k_fill<<<1, 32, 0, s>>>(m->Lenv[0], 1, 1.0);
-  k_fill<<<1, 32, 0, s>>>(m->Renv[L], 1, 1.0);
+  { k_fill<<<1, 32, 0, s>>>(m->Lenv[0], 1, 1.0); note_launch(); }
+  { k_fill<<<1, 32, 0, s>>>(m->Renv[L], 1, 1.0); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   m->lvalid[0] = 1;
   m->rvalid[L] = 1;
@@ -283,7 +291,7 @@ osmps_status energy_impl(osmps_ctx* ctx, const osmps_mps* m, const osmps_mpo* h,
   if (!e2) return st;
   double vals[2];
   for (int pass = 0; pass < 2; ++pass) {  // pass 0: <psi|H|psi>, pass 1: <psi|psi>
-    k_fill<<<1, 32, 0, s>>>(e1, 1, 1.0);
+    { k_fill<<<1, 32, 0, s>>>(e1, 1, 1.0); note_launch(); }
     OSMPS_LAUNCH_CHECK();
     double* a = e1;
     double* b = e2;
@@ -419,7 +427,7 @@ osmps_status osmps_mpo_create(osmps_ctx* ctx, int64_t L, const int64_t* d, const
       return set_error(OSMPS_ENOMEM, "osmps_mpo_create: cudaMalloc failed");
     }
     OSMPS_CUDA(cudaMemcpy(h->W[k], host_W[k], bytes, cudaMemcpyHostToDevice));
-    k_identity_op<<<1, 64>>>(h->ident[k], d[k]);
+    { k_identity_op<<<1, 64>>>(h->ident[k], d[k]); note_launch(); }
   }
   OSMPS_CUDA(cudaDeviceSynchronize());
   *out = h;

@@ -11,6 +11,8 @@ Recipes (all float64, ``numpy.random.default_rng(seed)``):
   chi_k = min(d^k, d^(L-k), chi_init).
 * ``random_heff_operands``: L, W1, W2, R, theta with N(0, 1) entries, for
   matvec parity tests at arbitrary (ragged) shapes.
+* ``random_symmetric_env``: E[a2, w, a] with N(0, 1) entries, symmetrised in
+  (a2, a).
 * ``random_couplings``: site-dependent XXZ couplings J_i ~ U[0.8, 1.2] for the
   L-1 bonds, then fields h_i ~ U[-0.5, 0.5] for the L sites.
 * ``chain_batch``: a batch of independent chain specifications (model, L,
@@ -52,6 +54,15 @@ def random_env_operands(chi_l, d, chi_r, w_in, w_out, side, seed=0):
         env = rng.standard_normal((chi_r, w_in, chi_r))
         W = rng.standard_normal((w_out, d, d, w_in))
     return env, A, W
+
+
+def random_symmetric_env(chi, w, seed=0):
+    """Environment-shaped tensor E[a2, w, a] with N(0, 1) entries, symmetrised
+    in (a2, a) for every channel so that an effective Hamiltonian built from it
+    is symmetric (timing inputs for a single two-site step)."""
+    rng = np.random.default_rng(seed)
+    E = rng.standard_normal((chi, w, chi))
+    return 0.5 * (E + E.transpose(2, 1, 0))
 
 
 def random_couplings(L, seed=0):

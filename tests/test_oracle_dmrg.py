@@ -220,3 +220,11 @@ def test_dmrg_bose_hubbard_small():
     e_ed = exact.ground_energy(exact.kron_hamiltonian(L, nmax + 1,
                                                       *exact.bose_hubbard_terms(L, 1.0, 4.0, nmax)))
     assert abs(E - e_ed) < 1e-10
+
+
+def test_right_canonicalize_long_random_chain_stays_finite():
+    # a random L=128 chain has norm ~ (d chi^2)^(L/2): the shifts must rescale
+    mps = dmrg.right_canonicalize(inputs.random_mps(128, 2, 32, seed=0))
+    assert all(np.isfinite(A).all() for A in mps)
+    assert abs(dmrg.mps_norm2(mps) - 1.0) < 1e-12
+    assert max(dmrg.right_isometry_defect(A) for A in mps[1:]) < 1e-12
