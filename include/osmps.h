@@ -104,6 +104,31 @@ osmps_status osmps_heff_apply(osmps_ctx* ctx, const double* L, const double* W1,
                               int64_t d1, int64_t d2, int64_t chi_r, int64_t wl, int64_t wm,
                               int64_t wr, int precision, void* stream);
 
+/* H_eff . theta for callers that cannot allocate device memory. (The paper
+ * has no counterpart: this is a deployment variant of osmps_heff_apply.)
+ * Some callers cannot call cudaMalloc: a serving process that reserved its
+ * whole memory budget up front, a real-time loop that must not take the
+ * implicit device synchronisation an allocation may cause, or a plug-in
+ * that is not allowed to own allocations. This call needs no osmps_ctx and
+ * allocates nothing. It computes the same float64 product as
+ * osmps_heff_apply(..., OSMPS_PREC_FP64, ...) with the same arguments and
+ * layouts, on the device current on the calling thread (all pointers must
+ * be on that device); `stream` as everywhere else.
+ * Its scratch is one fixed 32 MiB array compiled into the library: every
+ * GPU that loads the library holds it until the process exits. Dimensions
+ * whose intermediates would not fit are rejected with OSMPS_ESHAPE (the
+ * message gives the bytes needed); use osmps_heff_apply for those.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array and it keeps the previous call's
+ * contents (nothing in it is read before the call writes it), so calls
+ * that can overlap on the GPU (other streams or threads) race: serialise
+ * them.                                                                      */
+osmps_status osmps_heff_apply_noalloc(const double* L, const double* W1, const double* W2,
+                                      const double* R, const double* theta, double* y,
+                                      int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r,
+                                      int64_t wl, int64_t wm, int64_t wr, void* stream);
+
 /* Environment update (Sec. 3.4: the fixed sites are contracted into L and R
  * one site at a time).
  * side 0 (grow L past site k):

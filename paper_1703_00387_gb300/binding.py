@@ -63,6 +63,7 @@ _SIGS = {
     "osmps_profile_read": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_i64), _dp, _dp, _dp]),
     "osmps_kernel_launches": (_i64, []),
     "osmps_heff_apply": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 + [_c.c_int, _vp]),
+    "osmps_heff_apply_noalloc": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 + [_vp]),
     "osmps_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_c.c_int, _vp]),
     "osmps_lanczos_ground": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 +
                              [_c.c_int, _c.c_double, _c.c_int, _dp, _c.POINTER(_c.c_int), _dp, _vp]),
@@ -182,6 +183,17 @@ def osmps_heff_apply(ctx, L, W1, W2, R, theta, y, precision="bf16x3", stream=Non
     _check(lib().osmps_heff_apply(ctx.ptr, _dev(L, "L"), _dev(W1, "W1"), _dev(W2, "W2"),
                                   _dev(R, "R"), _dev(theta, "theta"), _dev(y, "y"), chi_l, d1, d2,
                                   chi_r, wl, wm, wr, _prec(precision), _stream(stream)))
+    return y
+
+
+def osmps_heff_apply_noalloc(L, W1, W2, R, theta, y, stream=None):
+    """Float64 H_eff.theta through the allocation-free entry point (no context;
+    fixed 32 MiB scratch inside the library, shared by all calls)."""
+    chi_l, d1, d2, chi_r = theta.shape
+    wl, wm, wr = W1.shape[0], W1.shape[3], W2.shape[3]
+    _check(lib().osmps_heff_apply_noalloc(_dev(L, "L"), _dev(W1, "W1"), _dev(W2, "W2"),
+                                          _dev(R, "R"), _dev(theta, "theta"), _dev(y, "y"), chi_l,
+                                          d1, d2, chi_r, wl, wm, wr, _stream(stream)))
     return y
 
 
