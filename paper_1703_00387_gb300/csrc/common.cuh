@@ -216,6 +216,13 @@ osmps_status fiber_contract_f32(const Fiber& f, const double* Mat, const float* 
 osmps_status fiber_contract_f32_split(const Fiber& f, const double* Mat, const float* in,
                                       void* dst, int kind, int64_t Kcols, int64_t Kp,
                                       cudaStream_t stream);
+// Both W-steps of H_eff.theta fused (T1 -> split T3) for the d = 2 MPO
+// shapes it is specialised for; *done = false means the caller must fall back
+// to the two fiber contractions.
+osmps_status fused_wsteps_f32_split(const float* T1, const double* Mat1, const double* Mat2,
+                                    void* dst, int kind, int64_t chi_l, int64_t d1, int64_t d2,
+                                    int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int64_t Kp,
+                                    cudaStream_t s, bool* done);
 osmps_status zero_pad_columns(void* dst, int kind, int64_t rows, int64_t Kcols, int64_t Kp,
                               cudaStream_t stream);
 
@@ -255,6 +262,9 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
                           int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int max_iter,
                           double tol, int precision, double* energy, int* iters, double* resid,
                           cudaStream_t stream);
+osmps_status theta_form_tc(osmps_ctx* ctx, const double* A1, const double* A2, double* theta,
+                           int64_t chi_l, int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
+                           int precision, cudaStream_t stream);
 osmps_status theta_form_impl(const double* A1, const double* A2, double* theta, int64_t chi_l,
                              int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
                              cudaStream_t stream);

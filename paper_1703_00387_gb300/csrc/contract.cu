@@ -121,9 +121,14 @@ static osmps_status heff_apply_prepared(osmps_ctx* ctx, const double* theta, dou
   g1.kind = kind; g1.M = chi_l * wl; g1.N = N1; g1.Kp = Kp1; g1.K = chi_l;
   g1.A = ctx->slots[SLOT_HEFF_LOP].ptr; g1.B = xop; g1.C = T1; g1.ldc = N1; g1.out = TC_OUT_F32;
   OSMPS_TRY(gemm_tc(ctx, g1, stream));
-  OSMPS_TRY(fiber_contract_f32(f2, mat1, T1, T2, stream));
   OSMPS_TRY(zero_pad_columns(t3op, kind, M4, wr * chi_r, Kp3, stream));
-  OSMPS_TRY(fiber_contract_f32_split(f3, mat2, T2, t3op, kind, wr * chi_r, Kp3, stream));
+  bool fused = false;
+  OSMPS_TRY(fused_wsteps_f32_split(T1, mat1, mat2, t3op, kind, chi_l, d1, d2, chi_r, wl, wm, wr,
+                                   Kp3, stream, &fused));
+  if (!fused) {
+    OSMPS_TRY(fiber_contract_f32(f2, mat1, T1, T2, stream));
+    OSMPS_TRY(fiber_contract_f32_split(f3, mat2, T2, t3op, kind, wr * chi_r, Kp3, stream));
+  }
   GemmTc g4;
   g4.kind = kind; g4.M = M4; g4.N = chi_r; g4.Kp = Kp3; g4.K = wr * chi_r;
   g4.A = t3op; g4.B = ctx->slots[SLOT_HEFF_ROP].ptr; g4.C = y; g4.ldc = chi_r; g4.out = TC_OUT_F64;
@@ -325,6 +330,28 @@ osmps_status env_update_impl(osmps_ctx* ctx, int side, const double* env_in, con
   if (side == 0)
     return env_left_tc(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, precision, stream);
   return env_right_tc(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, precision, stream);
+}
+
+// theta on the tensor cores (split precision): theta is only the Lanczos
+// start vector, so the sweep forms it in the precision of the contractions.
+osmps_status theta_form_tc(osmps_ctx* ctx, const double* A1, const double* A2, double* theta,
+                           int64_t chi_l, int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
+                           int precision, cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  const int kind = tc_kind(precision);
+  const size_t es = tc_elem_bytes(kind);
+  const int64_t Kp = round_up(chi_m, 64);
+  void* opa = ws_get(ctx, SLOT_ENV_OPA, (size_t)chi_l * d1 * 2 * Kp * es, s, &st);
+  if (!opa) return st;
+  void* opb = ws_get(ctx, SLOT_ENV_OPB, (size_t)d2 * chi_r * 2 * Kp * es, s, &st);
+  if (!opb) return st;
+  SplitView a; a.src = A1; a.rows = chi_l * d1; a.K = chi_m; a.s0 = chi_m; a.sk = 1;
+  OSMPS_TRY(split_operand(a, kind, opa, Kp, s));
+  SplitView b; b.src = A2; b.rows = d2 * chi_r; b.K = chi_m; b.s0 = 1; b.sk = d2 * chi_r;
+  OSMPS_TRY(split_operand(b, kind, opb, Kp, s));
+  GemmTc g; g.kind = kind; g.M = chi_l * d1; g.N = d2 * chi_r; g.Kp = Kp; g.K = chi_m;
+  g.A = opa; g.B = opb; g.C = theta; g.ldc = d2 * chi_r; g.out = TC_OUT_F64;
+  return gemm_tc(ctx, g, s);
 }
 
 osmps_status theta_form_impl(const double* A1, const double* A2, double* theta, int64_t chi_l,

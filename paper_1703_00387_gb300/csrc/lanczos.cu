@@ -6,7 +6,7 @@
 // the result against every stored Krylov vector twice (classical
 // Gram-Schmidt, two passes: full reorthogonalisation), normalises, and
 // solves the small tridiagonal problem for the lowest Ritz pair:
-//   * the eigenvalue by Sturm-count multisection (256 points per round),
+//   * the eigenvalue by Sturm-count multisection (32 points per round, one warp),
 //   * its eigenvector by inverse iteration with a partially pivoted
 //     tridiagonal LU (Gaussian elimination with row interchanges).
 // The host reads three numbers per step (energy, residual estimate, beta)
@@ -21,8 +21,8 @@ namespace {
 
 constexpr int MAXIT = 512;
 constexpr int DOT_THREADS = 256;
-constexpr int DOT_GROUP = 8;
-constexpr int DOT_MAX_BLOCKS = 512;
+constexpr int DOT_GROUP = 16;
+constexpr int DOT_MAX_BLOCKS = 1024;
 
 // scalar layout in SLOT_LZ_SCAL (doubles)
 constexpr int OFF_ALPHA = 0;
@@ -39,33 +39,43 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // part[i * nb + b] = sum over block b's elements of V[i][e] * w[e], i < nv.
+// Each thread takes two consecutive elements (16-byte loads) and 16 rows at a time.
 __global__ void __launch_bounds__(DOT_THREADS) k_multidot(const double* __restrict__ V, int64_t ld,
                                                           int nv, const double* __restrict__ w,
                                                           int64_t n, double* __restrict__ part) {
   __shared__ double sh[DOT_THREADS / 32][DOT_GROUP];
   const int nb = gridDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n2 = n >> 1;  // pairs (n is even for every H_eff vector with d1 d2 >= 2; tail below)
   for (int g0 = 0; g0 < nv; g0 += DOT_GROUP) {
     double acc[DOT_GROUP];
 #pragma unroll
     for (int v = 0; v < DOT_GROUP; ++v) acc[v] = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * DOT_THREADS + threadIdx.x; e < n;
+    for (int64_t e = (int64_t)blockIdx.x * DOT_THREADS + threadIdx.x; e < n2;
          e += (int64_t)nb * DOT_THREADS) {
-      const double wv = w[e];
+      const double2 wv = reinterpret_cast<const double2*>(w)[e];
 #pragma unroll
       for (int v = 0; v < DOT_GROUP; ++v)
-        if (g0 + v < nv) acc[v] = fma(V[(int64_t)(g0 + v) * ld + e], wv, acc[v]);
+        if (g0 + v < nv) {
+          const double2 x = reinterpret_cast<const double2*>(V + (int64_t)(g0 + v) * ld)[e];
+          acc[v] = fma(x.x, wv.x, fma(x.y, wv.y, acc[v]));
+        }
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+      for (int v = 0; v < DOT_GROUP; ++v)
+        if (g0 + v < nv) acc[v] = fma(V[(int64_t)(g0 + v) * ld + n - 1], w[n - 1], acc[v]);
     }
 #pragma unroll
     for (int v = 0; v < DOT_GROUP; ++v) {
-      double s = warp_sum(acc[v]);
-      if (lane == 0) sh[warp][v] = s;
+      double t = warp_sum(acc[v]);
+      if (lane == 0) sh[warp][v] = t;
     }
     __syncthreads();
     if (threadIdx.x < DOT_GROUP && g0 + (int)threadIdx.x < nv) {
-      double s = 0.0;
-      for (int k = 0; k < DOT_THREADS / 32; ++k) s += sh[k][threadIdx.x];
-      part[(int64_t)(g0 + threadIdx.x) * nb + blockIdx.x] = s;
+      double t = 0.0;
+      for (int k = 0; k < DOT_THREADS / 32; ++k) t += sh[k][threadIdx.x];
+      part[(int64_t)(g0 + threadIdx.x) * nb + blockIdx.x] = t;
     }
     __syncthreads();
   }
@@ -87,17 +97,49 @@ __global__ void k_multidot_final(const double* __restrict__ part, int nb, double
 }
 
 // mode 0: w[e] -= sum_i c[i] V[i][e];  mode 1: w[e] = sum_i c[i] V[i][e]
+// (two consecutive elements per thread, 16-byte loads; the vectors are
+// 256-byte aligned with an even stride).
 __global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
                           const double* __restrict__ c, double* __restrict__ w, int64_t n,
                           int mode) {
   __shared__ double cs[MAXIT];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = c[i];
   __syncthreads();
+  const int64_t n2 = n >> 1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double ax = 0.0, ay = 0.0;
+    for (int i = 0; i < nv; ++i) {
+      const double2 x = reinterpret_cast<const double2*>(V + (int64_t)i * ld)[e];
+      ax = fma(cs[i], x.x, ax);
+      ay = fma(cs[i], x.y, ay);
+    }
+    double2* wp = reinterpret_cast<double2*>(w) + e;
+    if (mode == 0) {
+      const double2 o = *wp;
+      *wp = make_double2(o.x - ax, o.y - ay);
+    } else {
+      *wp = make_double2(ax, ay);
+    }
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    double a = 0.0;
+    for (int i = 0; i < nv; ++i) a = fma(cs[i], V[(int64_t)i * ld + n - 1], a);
+    w[n - 1] = (mode == 0) ? (w[n - 1] - a) : a;
+  }
+}
+
+// x[e] = sum_i c[i] V[i][e] into an arbitrary (8-byte aligned) caller buffer.
+__global__ void k_combine_scalar(const double* __restrict__ V, int64_t ld, int nv,
+                                 const double* __restrict__ c, double* __restrict__ x, int64_t n) {
+  __shared__ double cs[MAXIT];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = c[i];
+  __syncthreads();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int i = 0; i < nv; ++i) acc = fma(cs[i], V[(int64_t)i * ld + e], acc);
-    w[e] = (mode == 0) ? (w[e] - acc) : acc;
+    double a = 0.0;
+    for (int i = 0; i < nv; ++i) a = fma(cs[i], V[(int64_t)i * ld + e], a);
+    x[e] = a;
   }
 }
 
@@ -114,54 +156,47 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x) {
   return cnt;
 }
 
-// Record alpha_j, beta_j, then the lowest eigenpair of T_{j+1}.
-__global__ void __launch_bounds__(256) k_tridiag(double* __restrict__ sc, int j) {
+// Record alpha_j, beta_j, then the lowest eigenpair of T_{j+1}; one warp.
+// Eigenvalue: Sturm-count multisection, 32 points per round (5 bits).
+// Eigenvector: inverse iteration (3 solves) with a partially pivoted
+// tridiagonal LU, run by lane 0.
+__global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int j) {
   __shared__ double a[MAXIT], b[MAXIT], x[MAXIT], dl[MAXIT], dd[MAXIT], du[MAXIT];
-  __shared__ double lo, hi;
-  __shared__ int best;
   const int m = j + 1;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
+  const int lane = threadIdx.x;
+  if (lane == 0) {
     sc[OFF_ALPHA + j] = sc[OFF_C1 + j] + sc[OFF_C2 + j];
     sc[OFF_BETA + j] = sqrt(sc[OFF_MISC + 3]);
   }
-  __syncthreads();
-  for (int i = tid; i < m; i += blockDim.x) {
+  __syncwarp();
+  for (int i = lane; i < m; i += 32) {
     a[i] = sc[OFF_ALPHA + i];
     b[i] = sc[OFF_BETA + i];  // b[i] couples i and i+1 (b[j] is the residual norm)
   }
-  __syncthreads();
-  if (tid == 0) {
-    double l = 1e300, h = -1e300;
-    for (int i = 0; i < m; ++i) {
-      double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
-      l = fmin(l, a[i] - r);
-      h = fmax(h, a[i] + r);
-    }
-    double pad = 1e-12 * fmax(fabs(l), fabs(h)) + 1e-300;
-    lo = l - pad;
-    hi = h + pad;
+  __syncwarp();
+  double l = 1e300, h = -1e300;
+  for (int i = lane; i < m; i += 32) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+    l = fmin(l, a[i] - r);
+    h = fmax(h, a[i] + r);
   }
-  __syncthreads();
-  const int P = blockDim.x;
-  for (int round = 0; round < 12; ++round) {
-    const double L0 = lo, H0 = hi;
-    if (!(H0 - L0 > 4e-16 * fmax(fabs(L0), fabs(H0)))) break;
-    if (tid == 0) best = P;
-    __syncthreads();
-    const double xt = L0 + (H0 - L0) * (double)(tid + 1) / (double)(P + 1);
-    if (sturm_count(a, b, m, xt) >= 1) atomicMin(&best, tid);
-    __syncthreads();
-    if (tid == 0) {
-      const int t = best;
-      const double xh = (t < P) ? L0 + (H0 - L0) * (double)(t + 1) / (double)(P + 1) : H0;
-      const double xl = L0 + (H0 - L0) * (double)t / (double)(P + 1);
-      lo = xl;
-      hi = xh;
-    }
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
+    h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
   }
-  if (tid == 0) {
+  const double pad = 1e-12 * fmax(fabs(l), fabs(h)) + 1e-300;
+  double lo = l - pad, hi = h + pad;
+  for (int round = 0; round < 16; ++round) {
+    if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
+    const double xt = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const unsigned hit = __ballot_sync(0xffffffffu, sturm_count(a, b, m, xt) >= 1);
+    const int t = hit ? (__ffs(hit) - 1) : 32;
+    const double nlo = lo + (hi - lo) * (double)t / 33.0;
+    const double nhi = (t < 32) ? lo + (hi - lo) * (double)(t + 1) / 33.0 : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) {
     const double e = 0.5 * (lo + hi);
     double tnorm = 0.0;
     for (int i = 0; i < m; ++i) tnorm = fmax(tnorm, fabs(a[i]) + 2.0 * fabs(b[i]));
@@ -221,7 +256,7 @@ __global__ void __launch_bounds__(256) k_tridiag(double* __restrict__ sc, int j)
 }
 
 int dot_blocks(int64_t n) {
-  int64_t b = cdiv(n, DOT_THREADS * 4);
+  int64_t b = cdiv(n, DOT_THREADS * 8);
   if (b < 1) b = 1;
   if (b > DOT_MAX_BLOCKS) b = DOT_MAX_BLOCKS;
   return (int)b;
@@ -234,12 +269,14 @@ int ew_blocks(int64_t n) {
   return (int)b;
 }
 
-osmps_status project(osmps_ctx* ctx, const double* V, int64_t n, int nv, double* w, double* part,
-                     double* coef, cudaStream_t s) {
+// w -= V^T-projection of w onto the nv stored Krylov vectors (rows of V with
+// an even stride ld, 16-byte aligned like w), coefficients to coef.
+osmps_status project(osmps_ctx* ctx, const double* V, int64_t ld, int64_t n, int nv, double* w,
+                     double* part, double* coef, cudaStream_t s) {
   const int nb = dot_blocks(n);
-  { k_multidot<<<nb, DOT_THREADS, 0, s>>>(V, n, nv, w, n, part); note_launch(); }
+  { k_multidot<<<nb, DOT_THREADS, 0, s>>>(V, ld, nv, w, n, part); note_launch(); }
   { k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef); note_launch(); }
-  { k_combine<<<ew_blocks(n), 256, 0, s>>>(V, n, nv, coef, w, n, 0); note_launch(); }
+  { k_combine<<<ew_blocks(n), 256, 0, s>>>(V, ld, nv, coef, w, n, 0); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }
@@ -253,8 +290,9 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
                           cudaStream_t s) {
   osmps_status st = OSMPS_OK;
   const int64_t n = chi_l * d1 * d2 * chi_r;
+  const int64_t ld = (n + 1) & ~(int64_t)1;  // even row stride: 16-byte aligned rows
   if (max_iter > n) max_iter = (int)n;
-  double* V = (double*)ws_get(ctx, SLOT_LZ_BASIS, (size_t)max_iter * n * 8, s, &st);
+  double* V = (double*)ws_get(ctx, SLOT_LZ_BASIS, (size_t)max_iter * ld * 8, s, &st);
   if (!V) return st;
   double* w = (double*)ws_get(ctx, SLOT_LZ_W, (size_t)n * 8, s, &st);
   if (!w) return st;
@@ -279,13 +317,13 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
   double e = 0.0, res = 0.0;
   bool converged = false;
   for (int j = 0; j < max_iter; ++j) {
-    double* vj = V + (int64_t)j * n;
+    double* vj = V + (int64_t)j * ld;
     OSMPS_TRY(heff_apply_impl(ctx, nullptr, nullptr, nullptr, nullptr, vj, w, chi_l, d1, d2,
                               chi_r, wl, wm, wr, precision, s, true));
-    OSMPS_TRY(project(ctx, V, n, j + 1, w, part, sc + OFF_C1, s));
-    OSMPS_TRY(project(ctx, V, n, j + 1, w, part, sc + OFF_C2, s));
+    OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C1, s));
+    OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C2, s));
     OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, s));
-    { k_tridiag<<<1, 256, 0, s>>>(sc, j); note_launch(); }
+    { k_tridiag<<<1, 32, 0, s>>>(sc, j); note_launch(); }
     OSMPS_LAUNCH_CHECK();
     OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC, 3 * 8, cudaMemcpyDeviceToHost, s));
     OSMPS_CUDA(cudaStreamSynchronize(s));
@@ -300,10 +338,10 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
       break;
     }
     if (j + 1 == max_iter) break;
-    OSMPS_TRY(vec_scale_by_inv(V + (int64_t)(j + 1) * n, w, n, sc + OFF_BETA + j, s));
+    OSMPS_TRY(vec_scale_by_inv(V + (int64_t)(j + 1) * ld, w, n, sc + OFF_BETA + j, s));
   }
   // Ritz vector theta = sum_i s_i v_i, normalised
-  { k_combine<<<ew_blocks(n), 256, 0, s>>>(V, n, m, sc + OFF_S, theta, n, 1); note_launch(); }
+  { k_combine_scalar<<<ew_blocks(n), 256, 0, s>>>(V, ld, m, sc + OFF_S, theta, n); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   OSMPS_TRY(vec_norm2(ctx, theta, n, sc + OFF_MISC + 4, s));
   OSMPS_TRY(vec_scale_by_inv_sqrt(theta, n, sc + OFF_MISC + 4, s));

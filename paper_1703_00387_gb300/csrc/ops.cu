@@ -198,6 +198,85 @@ __global__ void k_w_reorder(const double* __restrict__ W, int64_t dw, int64_t d,
   }
 }
 
+// Both W-steps of H_eff.theta in one pass, for the spin-1/2 chains (d = 2)
+// whose MPO bond dimensions are fixed at compile time: for every fiber
+// (a2, c) the wl*d*d values T1[a2, w, s1, s2, c] are contracted with W1 and
+// then W2 in registers and written straight into the split operand
+// T3[(a2, t1, t2), (w2, c)]; the intermediate T2 never touches memory.
+template <int D, int WL, int WM, int WR, int KIND>
+__global__ void __launch_bounds__(256) k_fused_wsteps(const float* __restrict__ T1,
+                                                      const double* __restrict__ Mat1,
+                                                      const double* __restrict__ Mat2,
+                                                      void* __restrict__ dst, int64_t chi_l,
+                                                      int64_t chi_r, int64_t Kp) {
+  constexpr int P1 = WL * D, Q1 = D * WM, P2 = WM * D, Q2 = D * WR;
+  __shared__ float m1[P1 * Q1], m2[P2 * Q2];
+  for (int i = threadIdx.x; i < P1 * Q1; i += blockDim.x) m1[i] = (float)Mat1[i];
+  for (int i = threadIdx.x; i < P2 * Q2; i += blockDim.x) m2[i] = (float)Mat2[i];
+  __syncthreads();
+  const int64_t total = chi_l * chi_r;
+  const int64_t Kcols = (int64_t)WR * chi_r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a2 = e / chi_r, c = e - a2 * chi_r;
+    const float* src = T1 + a2 * (WL * D * D) * chi_r + c;
+    float x[WL][D][D];
+#pragma unroll
+    for (int w = 0; w < WL; ++w)
+#pragma unroll
+      for (int s1 = 0; s1 < D; ++s1)
+#pragma unroll
+        for (int s2 = 0; s2 < D; ++s2) x[w][s1][s2] = src[((w * D + s1) * D + s2) * chi_r];
+    float mid[D][WM][D];  // T2[t1, w1, s2]
+#pragma unroll
+    for (int t1 = 0; t1 < D; ++t1)
+#pragma unroll
+      for (int w1 = 0; w1 < WM; ++w1)
+#pragma unroll
+        for (int s2 = 0; s2 < D; ++s2) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int w = 0; w < WL; ++w)
+#pragma unroll
+            for (int s1 = 0; s1 < D; ++s1)
+              acc = fmaf(m1[(w * D + s1) * Q1 + t1 * WM + w1], x[w][s1][s2], acc);
+          mid[t1][w1][s2] = acc;
+        }
+#pragma unroll
+    for (int t1 = 0; t1 < D; ++t1)
+#pragma unroll
+      for (int t2 = 0; t2 < D; ++t2) {
+        const int64_t row = (a2 * D + t1) * D + t2;
+#pragma unroll
+        for (int w2 = 0; w2 < WR; ++w2) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int w1 = 0; w1 < WM; ++w1)
+#pragma unroll
+            for (int s2 = 0; s2 < D; ++s2)
+              acc = fmaf(m2[(w1 * D + s2) * Q2 + t2 * WR + w2], mid[t1][w1][s2], acc);
+          split_store<KIND>(dst, row * 2 * Kp + (int64_t)w2 * chi_r + c, Kp, (double)acc);
+        }
+      }
+  }
+  (void)Kcols;
+}
+
+template <int D, int WL, int WM, int WR>
+bool try_fused(int64_t d, int64_t wl, int64_t wm, int64_t wr, int kind, const float* T1,
+               const double* m1, const double* m2, void* dst, int64_t chi_l, int64_t chi_r,
+               int64_t Kp, cudaStream_t s) {
+  if (d != D || wl != WL || wm != WM || wr != WR) return false;
+  const int blocks = grid_for(chi_l * chi_r, 256);
+  if (kind == TC_BF16) {
+    k_fused_wsteps<D, WL, WM, WR, TC_BF16><<<blocks, 256, 0, s>>>(T1, m1, m2, dst, chi_l, chi_r, Kp);
+  } else {
+    k_fused_wsteps<D, WL, WM, WR, TC_TF32><<<blocks, 256, 0, s>>>(T1, m1, m2, dst, chi_l, chi_r, Kp);
+  }
+  note_launch();
+  return true;
+}
+
 }  // namespace
 
 osmps_status split_operand(const SplitView& v, int kind, void* dst, int64_t Kp, cudaStream_t s) {
@@ -233,6 +312,25 @@ osmps_status fiber_contract_f32_split(const Fiber& f, const double* Mat, const f
                                       cudaStream_t s) {
   if (kind == TC_BF16) return fiber_dispatch<float, 1>(f, Mat, in, nullptr, dst, Kcols, Kp, s);
   return fiber_dispatch<float, 2>(f, Mat, in, nullptr, dst, Kcols, Kp, s);
+}
+
+osmps_status fused_wsteps_f32_split(const float* T1, const double* Mat1, const double* Mat2,
+                                    void* dst, int kind, int64_t chi_l, int64_t d1, int64_t d2,
+                                    int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int64_t Kp,
+                                    cudaStream_t s, bool* done) {
+  *done = false;
+  if (d1 != d2) return OSMPS_OK;
+  const int64_t d = d1;
+  bool ok = try_fused<2, 5, 5, 5>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
+            try_fused<2, 1, 5, 5>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
+            try_fused<2, 5, 5, 1>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
+            try_fused<2, 3, 3, 3>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
+            try_fused<2, 1, 3, 3>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
+            try_fused<2, 3, 3, 1>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s);
+  if (!ok) return OSMPS_OK;
+  OSMPS_LAUNCH_CHECK();
+  *done = true;
+  return OSMPS_OK;
 }
 
 osmps_status zero_pad_columns(void* dst, int kind, int64_t rows, int64_t Kcols, int64_t Kp,

@@ -245,7 +245,10 @@ osmps_status two_site_step(osmps_ctx* ctx, osmps_mps* m, const osmps_mpo* h, int
   const int64_t d1 = m->d[k], d2 = m->d[k + 1];
   double* theta = (double*)ws_get(ctx, SLOT_SWEEP_THETA, (size_t)chl * d1 * d2 * chr * 8, s, &st);
   if (!theta) return st;
-  OSMPS_TRY(theta_form_impl(m->A[k], m->A[k + 1], theta, chl, d1, chm, d2, chr, s));
+  if (precision == OSMPS_PREC_FP64)
+    OSMPS_TRY(theta_form_impl(m->A[k], m->A[k + 1], theta, chl, d1, chm, d2, chr, s));
+  else
+    OSMPS_TRY(theta_form_tc(ctx, m->A[k], m->A[k + 1], theta, chl, d1, chm, d2, chr, precision, s));
   double e = 0.0, res = 0.0;
   int it = 0;
   osmps_status ls = lanczos_impl(ctx, m->Lenv[k], h->W[k], h->W[k + 1], m->Renv[k + 2], theta, chl,
