@@ -58,7 +58,10 @@ typedef enum {
 typedef enum {
   OSMPS_PREC_FP64 = 0,   /* plain float64 on CUDA cores / DMMA                       */
   OSMPS_PREC_BF16X3 = 1, /* tcgen05 bf16 tensor cores, hi+lo split, 3 products, f32 acc */
-  OSMPS_PREC_TF32X3 = 2  /* tcgen05 tf32 tensor cores, hi+lo split, 3 products, f32 acc */
+  OSMPS_PREC_TF32X3 = 2, /* tcgen05 tf32 tensor cores, hi+lo split, 3 products, f32 acc */
+  OSMPS_PREC_FP64_EMU = 3 /* float64-accurate products emulated on the bf16 tensor cores:
+                             8 exact 7-bit slices per operand, 36 slice pairs, exact
+                             float32 partial sums added in float64                     */
 } osmps_precision;
 
 typedef struct osmps_ctx osmps_ctx;
@@ -79,7 +82,8 @@ size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx);
  * support; not part of the paper's method).                                 */
 typedef enum {
   OSMPS_KERNEL_GEMM_TC = 0,  /* tcgen05 split-precision GEMM                   */
-  OSMPS_KERNEL_GEMM_F64 = 1  /* float64 DMMA GEMM                              */
+  OSMPS_KERNEL_GEMM_F64 = 1, /* float64 DMMA GEMM                             */
+  OSMPS_KERNEL_GEMM_EMU = 2  /* float64-accurate GEMM on bf16 tensor cores       */
 } osmps_kernel;
 /* Turn recording on (1) or off (0); both clear earlier records. Syncs the device. */
 osmps_status osmps_profile_enable(osmps_ctx* ctx, int enable);
@@ -129,6 +133,17 @@ osmps_status osmps_heff_apply_noalloc(const double* L, const double* W1, const d
                                       int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r,
                                       int64_t wl, int64_t wm, int64_t wr, void* stream);
 
+/* Float64-accurate matrix product on the tensor cores, C = A B with A
+ * (M, K), B (K, N), C (M, N) row-major float64 device arrays. A support
+ * routine of the float64 split (Sec. 2, Eq. AAD_ULLUD: the Gram matrix and
+ * the projection are such products): every row of A and column of B is
+ * scaled by a power of two and cut into 8 exact 7-bit bf16 slices; the 36
+ * slice pairs whose weight is above 2^-56 are multiplied on tcgen05 with
+ * exact float32 partial sums of 256 products, accumulated in float64.
+ * C must not alias A or B. Scratch from the context.                       */
+osmps_status osmps_dgemm_emu(osmps_ctx* ctx, const double* A, const double* B, double* C,
+                             int64_t M, int64_t N, int64_t K, void* stream);
+
 /* Environment update (Sec. 3.4: the fixed sites are contracted into L and R
  * one site at a time).
  * side 0 (grow L past site k):
@@ -166,6 +181,12 @@ osmps_status osmps_theta_form(osmps_ctx* ctx, const double* A1, const double* A2
 
 /* Split theta with truncation by the eigendecomposition route (Sec. 2,
  * Eq. AAD_ULLUD and Eq. ThetaAL), Gram matrix and eigensolver in float64.
+ * The eigenpairs are float64 (cuSOLVER dsyevdx for the largest
+ * min(chi_max, rank) only). The Gram matrix and the projection run on the
+ * float64 DMMA GEMM for precision OSMPS_PREC_FP64 and on the float64-accurate
+ * emulated tensor-core GEMM for every other precision. The discarded weight
+ * is 1 - (kept sum of lambda^2) / ||theta||^2 (the Gram route cannot resolve
+ * the tail below ~n eps ||theta||^2).
  * move_right = 1: G = M M^T with M = theta as (chi_l d1) x (d2 chi_r);
  *   A1 = kept eigenvectors (left-canonical), A2 = U^T M renormalised.
  * move_right = 0: G = M^T M; A2 = V^T (right-canonical), A1 = M V renormalised.
@@ -173,15 +194,16 @@ osmps_status osmps_theta_form(osmps_ctx* ctx, const double* A1, const double* A2
  * <= eps_local), lambda^2 normalised to sum 1 (Eq. elocal; Sec. 3.4).
  * A1 must hold chi_l*d1*min(chi_max, chi_l*d1, d2*chi_r) doubles and A2
  * min(...)*d2*chi_r; they are written with the actual chi'.
- * Host outputs: chi_new_out, discarded_out (sum of dropped lambda^2),
+ * Host outputs: chi_new_out, discarded_out (weight of the dropped lambda^2),
  * entropy_out (-sum lambda'^2 log lambda'^2 over kept, renormalised values),
  * lam2_out (optional host array of min(chi_l d1, d2 chi_r) values,
- * descending). Synchronises `stream`.                                       */
+ * descending; only the first min(chi_max, rank) are computed, the rest are
+ * written as 0). Synchronises `stream`.                                     */
 osmps_status osmps_split(osmps_ctx* ctx, const double* theta, double* A1, double* A2,
                          int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r, int move_right,
                          int64_t chi_max, double eps_local, int64_t* chi_new_out,
                          double* discarded_out, double* entropy_out, double* lam2_out,
-                         void* stream);
+                         int precision, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Whole-chain handles and sweeps (Sec. 3.4).
@@ -217,7 +239,8 @@ typedef struct {
   int lanczos_max_iter;   /* Lanczos cap per step (paper default 100)              */
   int n_sweeps;           /* number of full L->R->L sweeps                          */
   int precision;          /* osmps_precision of the contractions                   */
-  int refine_sweeps;      /* extra float64 sweeps after n_sweeps                    */
+  int refine_sweeps;      /* extra float64-accurate sweeps after n_sweeps (OSMPS_PREC_FP64_EMU
+                             after tensor-core sweeps, OSMPS_PREC_FP64 otherwise)      */
 } osmps_sweep_params;
 
 typedef struct {
@@ -230,6 +253,9 @@ typedef struct {
   int64_t lanczos_iters;     /* total matrix-vector products                           */
   int64_t nonconverged;      /* steps whose Lanczos stopped at max_iter above tol      */
   double seconds;            /* wall time of the call                                  */
+  double setup_seconds;      /* canonicalisation and environment build                 */
+  double sweep_seconds;      /* the sweeps themselves                                  */
+  double energy_seconds;     /* the final float64 energy                               */
   double* step_energies;     /* optional HOST array (caller-owned) of length
                                 2 (L-1) (n_sweeps + refine_sweeps), or NULL          */
   int64_t* step_iters;       /* optional HOST array, same length, or NULL              */
@@ -270,13 +296,15 @@ osmps_status osmps_sweep_step(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* m
  * Sec. 2), build the right environments, then for every sweep optimise the
  * pairs (0,1)...(L-2,L-1) left to right and back (2 (L-1) steps per sweep):
  * theta formation, Lanczos, split with truncation, environment update.
- * Finally the energy is evaluated in float64 by contracting <psi|H|psi>.
+ * Finally the energy is evaluated to float64 accuracy by contracting
+ * <psi|H|psi> and <psi|psi> (float64-accurate emulated tensor-core GEMMs).
  * stats is a host pointer (may be NULL). Synchronises `stream`.            */
 osmps_status osmps_sweep(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo,
                          const osmps_sweep_params* params, osmps_sweep_stats* stats,
                          void* stream);
 
-/* <psi|H|psi> / <psi|psi> in float64 for the MPS as it stands (host result). */
+/* <psi|H|psi> / <psi|psi> to float64 accuracy for the MPS as it stands (host
+ * result; contractions on the float64-accurate emulated GEMM).            */
 osmps_status osmps_energy(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo* mpo,
                           double* energy_out, void* stream);
 

@@ -14,7 +14,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libosmps.so")
 
-PRECISION = {"fp64": 0, "bf16x3": 1, "tf32x3": 2}
+PRECISION = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "fp64emu": 3}
 STATUS = {0: "OSMPS_OK", 1: "OSMPS_EINVAL", 2: "OSMPS_ESHAPE", 3: "OSMPS_ENOMEM", 4: "OSMPS_ECUDA",
           5: "OSMPS_ENOCONV", 6: "OSMPS_ETIMEOUT", 7: "OSMPS_ENAN", 8: "OSMPS_EUNSUPPORTED"}
 ENOCONV = 5
@@ -41,7 +41,8 @@ class SweepStats(_c.Structure):
     _fields_ = [("energy", _c.c_double), ("last_step_energy", _c.c_double),
                 ("max_discarded", _c.c_double), ("entropy_center", _c.c_double),
                 ("max_chi", _i64), ("steps", _i64), ("lanczos_iters", _i64),
-                ("nonconverged", _i64), ("seconds", _c.c_double),
+                ("nonconverged", _i64), ("seconds", _c.c_double), ("setup_seconds", _c.c_double),
+                ("sweep_seconds", _c.c_double), ("energy_seconds", _c.c_double),
                 ("step_energies", _dp), ("step_iters", _c.POINTER(_i64))]
 
 
@@ -64,12 +65,13 @@ _SIGS = {
     "osmps_kernel_launches": (_i64, []),
     "osmps_heff_apply": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 + [_c.c_int, _vp]),
     "osmps_heff_apply_noalloc": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 + [_vp]),
+    "osmps_dgemm_emu": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _vp]),
     "osmps_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_c.c_int, _vp]),
     "osmps_lanczos_ground": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 +
                              [_c.c_int, _c.c_double, _c.c_int, _dp, _c.POINTER(_c.c_int), _dp, _vp]),
     "osmps_theta_form": (_c.c_int, [_vp, _vp, _vp, _vp] + [_i64] * 5 + [_vp]),
     "osmps_split": (_c.c_int, [_vp, _vp, _vp, _vp] + [_i64] * 4 +
-                    [_c.c_int, _i64, _c.c_double, _c.POINTER(_i64), _dp, _dp, _dp, _vp]),
+                    [_c.c_int, _i64, _c.c_double, _c.POINTER(_i64), _dp, _dp, _dp, _c.c_int, _vp]),
     "osmps_mps_create": (_c.c_int, [_vp, _i64, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_dp),
                                     _i64, _c.POINTER(_vp)]),
     "osmps_mps_destroy": (_c.c_int, [_vp]),
@@ -157,7 +159,7 @@ class Context:
             pass
 
 
-KERNEL = {"gemm_tc": 0, "gemm_f64": 1}
+KERNEL = {"gemm_tc": 0, "gemm_f64": 1, "gemm_emu": 2}
 
 
 def osmps_profile_enable(ctx, enable=True):
@@ -197,6 +199,16 @@ def osmps_heff_apply_noalloc(L, W1, W2, R, theta, y, stream=None):
     return y
 
 
+def osmps_dgemm_emu(ctx, A, B, C, stream=None):
+    """C = A @ B in float64 accuracy on the bf16 tensor cores (error-free slices)."""
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2 and tuple(C.shape) == (M, N)
+    _check(lib().osmps_dgemm_emu(ctx.ptr, _dev(A, "A"), _dev(B, "B"), _dev(C, "C"), M, N, K,
+                                 _stream(stream)))
+    return C
+
+
 def osmps_env_update(ctx, side, env_in, A, W, env_out, precision="bf16x3", stream=None):
     chi_l, d, chi_r = A.shape
     if side == 0:
@@ -233,7 +245,7 @@ def osmps_theta_form(ctx, A1, A2, theta, stream=None):
     return theta
 
 
-def osmps_split(ctx, theta, A1, A2, move_right, chi_max, eps_local, stream=None):
+def osmps_split(ctx, theta, A1, A2, move_right, chi_max, eps_local, precision="fp64", stream=None):
     """Returns (chi_new, discarded, entropy, lam2 numpy array). A1/A2 are flat
     buffers large enough for the largest possible chi_new; reshape them to
     (chi_l, d1, chi_new) / (chi_new, d2, chi_r)."""
@@ -246,7 +258,7 @@ def osmps_split(ctx, theta, A1, A2, move_right, chi_max, eps_local, stream=None)
     _check(lib().osmps_split(ctx.ptr, _dev(theta, "theta"), _dev(A1, "A1"), _dev(A2, "A2"), chi_l,
                              d1, d2, chi_r, int(move_right), int(chi_max), float(eps_local),
                              _c.byref(chn), _c.byref(disc), _c.byref(ent),
-                             lam2.ctypes.data_as(_dp), _stream(stream)))
+                             lam2.ctypes.data_as(_dp), _prec(precision), _stream(stream)))
     return chn.value, disc.value, ent.value, lam2
 
 

@@ -84,6 +84,16 @@ enum Slot {
   SLOT_SWEEP_ENV2,
   SLOT_RED,
   SLOT_NORM,
+  SLOT_EMU_A,
+  SLOT_EMU_B,
+  SLOT_EMU_EXP,
+  SLOT_EIG_X,
+  SLOT_EIG_F32,
+  SLOT_EIG_R,
+  SLOT_EIG_S,
+  SLOT_EIG_P,
+  SLOT_EIG_E,
+  SLOT_EIG_SCAL,
   SLOT_COUNT
 };
 
@@ -196,6 +206,13 @@ struct SplitView {
 osmps_status split_operand(const SplitView& v, int kind, void* dst, int64_t Kp, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
+// Float64-accurate GEMM on the bf16 tensor cores (error-free slicing):
+// C[M,N] = sum_k a(m,k) b(n,k), with a and b given as views (SplitView: row
+// m / n, column k; float64 sources). C is float64, row-major, ldc.
+osmps_status gemm_emu(osmps_ctx* ctx, const SplitView& a, const SplitView& b, int64_t M,
+                      int64_t N, int64_t K, double* C, int64_t ldc, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // Small contractions with an MPO tensor ("W-steps"): for every fiber
 // (o1, o2, c): out[o1*os1 + o2*os2 + o*ostride + c] = sum_i Mat[i][o] in[o1*is1 + o2*is2 + i*istride + c]
 // Mat is P x Q (row-major, float64, on the device).
@@ -271,10 +288,11 @@ osmps_status theta_form_impl(const double* A1, const double* A2, double* theta, 
 osmps_status split_impl(osmps_ctx* ctx, const double* theta, double* A1, double* A2,
                         int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r, int move_right,
                         int64_t chi_max, double eps_local, int64_t* chi_new, double* discarded,
-                        double* entropy, double* lam2_out, cudaStream_t stream);
+                        double* entropy, double* lam2_out, int precision, cudaStream_t stream);
 
 inline bool valid_precision(int p) {
-  return p == OSMPS_PREC_FP64 || p == OSMPS_PREC_BF16X3 || p == OSMPS_PREC_TF32X3;
+  return p == OSMPS_PREC_FP64 || p == OSMPS_PREC_BF16X3 || p == OSMPS_PREC_TF32X3 ||
+         p == OSMPS_PREC_FP64_EMU;
 }
 
 }  // namespace osmps

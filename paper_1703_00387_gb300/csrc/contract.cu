@@ -31,7 +31,7 @@ osmps_status heff_prepare(osmps_ctx* ctx, const double* L, const double* W1, con
   if (!small) return st;
   OSMPS_TRY(w_reorder(W1, wl, d1, wm, WORD_IN_W_S__OUT_T_W2, small, stream));
   OSMPS_TRY(w_reorder(W2, wm, d2, wr, WORD_IN_W_S__OUT_T_W2, small + P1 * Q1, stream));
-  if (precision == OSMPS_PREC_FP64) {
+  if (precision == OSMPS_PREC_FP64 || precision == OSMPS_PREC_FP64_EMU) {
     OSMPS_TRY(prepare_f64_copies(ctx, L, R, chi_l, chi_r, wl, wr, stream));
   } else {
     const int kind = tc_kind(precision);
@@ -76,6 +76,26 @@ static osmps_status heff_apply_prepared(osmps_ctx* ctx, const double* theta, dou
   f3.P = P2; f3.Q = Q2; f3.n_o1 = chi_l * d1; f3.n_o2 = 1; f3.nc = chi_r;
   f3.is1 = wm * d2 * chi_r; f3.is2 = 0; f3.istride = chi_r;
   f3.os1 = d2 * wr * chi_r; f3.os2 = 0; f3.ostride = chi_r;
+
+  if (precision == OSMPS_PREC_FP64_EMU) {
+    double* T1 = (double*)ws_get(ctx, SLOT_HEFF_T1, (size_t)(chi_l * wl) * N1 * 8, stream, &st);
+    if (!T1) return st;
+    double* T2 = (double*)ws_get(ctx, SLOT_HEFF_T2, (size_t)(chi_l * d1 * wm) * d2 * chi_r * 8, stream, &st);
+    if (!T2) return st;
+    double* T3 = (double*)ws_get(ctx, SLOT_HEFF_T3, (size_t)(chi_l * d1 * d2) * wr * chi_r * 8, stream, &st);
+    if (!T3) return st;
+    SplitView la;  // L as (a2 w) x a
+    la.src = ctx->slots[SLOT_HEFF_LOP].ptr; la.rows = chi_l * wl; la.K = chi_l; la.s0 = chi_l; la.sk = 1;
+    SplitView tt;  // theta^T: row n = (s1 s2 c), column a
+    tt.src = theta; tt.rows = N1; tt.K = chi_l; tt.s0 = 1; tt.sk = N1;
+    OSMPS_TRY(gemm_emu(ctx, la, tt, chi_l * wl, N1, chi_l, T1, N1, stream));
+    OSMPS_TRY(fiber_contract_f64(f2, mat1, T1, T2, stream));
+    OSMPS_TRY(fiber_contract_f64(f3, mat2, T2, T3, stream));
+    const int64_t M4 = chi_l * d1 * d2, K4 = wr * chi_r;
+    SplitView t3; t3.src = T3; t3.rows = M4; t3.K = K4; t3.s0 = K4; t3.sk = 1;
+    SplitView rr; rr.src = ctx->slots[SLOT_HEFF_ROP].ptr; rr.rows = chi_r; rr.K = K4; rr.s0 = K4; rr.sk = 1;
+    return gemm_emu(ctx, t3, rr, M4, chi_r, K4, y, chi_r, stream);
+  }
 
   if (precision == OSMPS_PREC_FP64) {
     double* T1 = (double*)ws_get(ctx, SLOT_HEFF_T1, (size_t)(chi_l * wl) * N1 * 8, stream, &st);
@@ -319,10 +339,63 @@ static osmps_status env_right_tc(osmps_ctx* ctx, const double* Rin, const double
   return gemm_tc(ctx, g2, s);
 }
 
+// Float64-accurate updates with the emulated GEMM (same views as env_*_tc).
+static osmps_status env_left_emu(osmps_ctx* ctx, const double* Lin, const double* A, const double* W,
+                                 double* Lout, int64_t chi_l, int64_t d, int64_t chi_r,
+                                 int64_t w_in, int64_t w_out, cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  double* X = (double*)ws_get(ctx, SLOT_ENV_X, (size_t)chi_l * w_in * d * chi_r * 8, s, &st);
+  if (!X) return st;
+  double* Y = (double*)ws_get(ctx, SLOT_ENV_Y, (size_t)chi_l * d * w_out * chi_r * 8, s, &st);
+  if (!Y) return st;
+  double* Mt = (double*)ws_get(ctx, SLOT_ENV_MAT, (size_t)w_in * d * d * w_out * 8, s, &st);
+  if (!Mt) return st;
+  OSMPS_TRY(w_reorder(W, w_in, d, w_out, WORD_IN_W_S__OUT_T_W2, Mt, s));
+  SplitView la; la.src = Lin; la.rows = chi_l * w_in; la.K = chi_l; la.s0 = chi_l; la.sk = 1;
+  SplitView at; at.src = A; at.rows = d * chi_r; at.K = chi_l; at.s0 = 1; at.sk = d * chi_r;
+  OSMPS_TRY(gemm_emu(ctx, la, at, chi_l * w_in, d * chi_r, chi_l, X, d * chi_r, s));
+  Fiber f;
+  f.P = w_in * d; f.Q = d * w_out; f.n_o1 = chi_l; f.n_o2 = 1; f.nc = chi_r;
+  f.is1 = w_in * d * chi_r; f.istride = chi_r; f.os1 = d * w_out * chi_r; f.ostride = chi_r;
+  OSMPS_TRY(fiber_contract_f64(f, Mt, X, Y, s));
+  SplitView aT; aT.src = A; aT.rows = chi_r; aT.K = chi_l * d; aT.s0 = 1; aT.sk = chi_r;
+  SplitView yT; yT.src = Y; yT.rows = w_out * chi_r; yT.K = chi_l * d; yT.s0 = 1; yT.sk = w_out * chi_r;
+  return gemm_emu(ctx, aT, yT, chi_r, w_out * chi_r, chi_l * d, Lout, w_out * chi_r, s);
+}
+
+static osmps_status env_right_emu(osmps_ctx* ctx, const double* Rin, const double* A,
+                                  const double* W, double* Rout, int64_t chi_l, int64_t d,
+                                  int64_t chi_r, int64_t w_in, int64_t w_out, cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  double* X = (double*)ws_get(ctx, SLOT_ENV_X, (size_t)chi_l * d * w_in * chi_r * 8, s, &st);
+  if (!X) return st;
+  double* Y = (double*)ws_get(ctx, SLOT_ENV_Y, (size_t)chi_l * w_out * d * chi_r * 8, s, &st);
+  if (!Y) return st;
+  double* Mt = (double*)ws_get(ctx, SLOT_ENV_MAT, (size_t)w_out * d * d * w_in * 8, s, &st);
+  if (!Mt) return st;
+  OSMPS_TRY(w_reorder(W, w_out, d, w_in, WORD_IN_S_W2__OUT_W_T, Mt, s));
+  SplitView av; av.src = A; av.rows = chi_l * d; av.K = chi_r; av.s0 = chi_r; av.sk = 1;
+  SplitView rv; rv.src = Rin; rv.rows = w_in * chi_r; rv.n1 = chi_r; rv.K = chi_r;
+  rv.s0 = chi_r; rv.s1 = w_in * chi_r; rv.sk = 1;
+  OSMPS_TRY(gemm_emu(ctx, av, rv, chi_l * d, w_in * chi_r, chi_r, X, w_in * chi_r, s));
+  Fiber f;
+  f.P = d * w_in; f.Q = w_out * d; f.n_o1 = chi_l; f.n_o2 = 1; f.nc = chi_r;
+  f.is1 = d * w_in * chi_r; f.istride = chi_r; f.os1 = w_out * d * chi_r; f.ostride = chi_r;
+  OSMPS_TRY(fiber_contract_f64(f, Mt, X, Y, s));
+  SplitView a2; a2.src = A; a2.rows = chi_l; a2.K = d * chi_r; a2.s0 = d * chi_r; a2.sk = 1;
+  SplitView yv; yv.src = Y; yv.rows = w_out * chi_l; yv.n1 = chi_l; yv.K = d * chi_r;
+  yv.s0 = d * chi_r; yv.s1 = w_out * d * chi_r; yv.sk = 1;
+  return gemm_emu(ctx, a2, yv, chi_l, w_out * chi_l, d * chi_r, Rout, w_out * chi_l, s);
+}
+
 osmps_status env_update_impl(osmps_ctx* ctx, int side, const double* env_in, const double* A,
                              const double* W, double* env_out, int64_t chi_l, int64_t d,
                              int64_t chi_r, int64_t w_in, int64_t w_out, int precision,
                              cudaStream_t stream) {
+  if (precision == OSMPS_PREC_FP64_EMU) {
+    if (side == 0) return env_left_emu(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
+    return env_right_emu(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
+  }
   if (precision == OSMPS_PREC_FP64) {
     if (side == 0) return env_left_f64(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
     return env_right_f64(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
@@ -338,6 +411,11 @@ osmps_status theta_form_tc(osmps_ctx* ctx, const double* A1, const double* A2, d
                            int64_t chi_l, int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
                            int precision, cudaStream_t s) {
   osmps_status st = OSMPS_OK;
+  if (precision == OSMPS_PREC_FP64_EMU) {
+    SplitView a; a.src = A1; a.rows = chi_l * d1; a.K = chi_m; a.s0 = chi_m; a.sk = 1;
+    SplitView b; b.src = A2; b.rows = d2 * chi_r; b.K = chi_m; b.s0 = 1; b.sk = d2 * chi_r;
+    return gemm_emu(ctx, a, b, chi_l * d1, d2 * chi_r, chi_m, theta, d2 * chi_r, s);
+  }
   const int kind = tc_kind(precision);
   const size_t es = tc_elem_bytes(kind);
   const int64_t Kp = round_up(chi_m, 64);

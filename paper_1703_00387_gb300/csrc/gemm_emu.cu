@@ -1,0 +1,383 @@
+// Float64-accurate GEMM on the bf16 tensor cores (error-free slicing).
+//
+// GB300's float64 units are slow; its bf16 tensor cores are about a
+// thousand times faster. A float64 GEMM is emulated on them exactly in the
+// manner of Ozaki's error-free transformation of matrix products:
+//   * every row of A (and of B, both K-major) is scaled by a power of two
+//     2^-e so that its entries lie in (-1, 1), and cut into S = 8 slices
+//     x = sum_p q_p 2^(-7(p+1)), q_p an integer with |q_p| <= 128, so every
+//     slice is exact in bf16;
+//   * for a slice pair (i, j) all products q_i q_j share the unit
+//     2^(-7(i+j+2)) and are at most 2^14 units, so a run of 256 of them sums
+//     to less than 2^22 units: exact in the float32 TMEM accumulator;
+//   * those exact partial sums are added in float64 registers, over the 36
+//     pairs with i + j <= 7 (the dropped pairs are below 2^-56 of the row
+//     scales), and the tile is scaled back by 2^(e_A[row] + e_B[col]).
+// The kernel reuses the persistent, warp-specialised structure of gemm_tc:
+// 128 x 128 tiles, a 6-stage TMA ring, two 128-column TMEM buffers, 16
+// epilogue warps each holding 32 float64 accumulators per row.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "tcgen05.cuh"
+
+namespace osmps {
+
+namespace {
+
+using namespace tc;
+
+constexpr int SLICES = 8;
+constexpr int SLICE_BITS = 7;
+constexpr int EBM = 128, EBN = 128;
+constexpr int ESTAGES = 6;
+constexpr int E_A_STAGE = EBM * 128, E_B_STAGE = EBN * 128;
+constexpr int E_STAGE = E_A_STAGE + E_B_STAGE;
+constexpr int E_EPI_WARPS = 16;
+constexpr int E_EPI_COLS = EBN / 4;
+constexpr int E_THREADS = 64 + 32 * E_EPI_WARPS;
+constexpr int E_CHUNK = 4;  // 64-element K slices per exact partial sum (256 products)
+constexpr uint32_t E_TMEM_COLS = 256;
+constexpr size_t E_SMEM = (size_t)ESTAGES * E_STAGE + 1024 + 256;
+
+struct PairList {
+  int n;
+  unsigned char a[64], b[64];
+};
+
+__global__ void __launch_bounds__(E_THREADS, 1)
+    k_gemm_emu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               double* __restrict__ C, int64_t M, int64_t N, int64_t ldc, int nkb, int Kp,
+               int tiles_n, int n_tiles, const int* __restrict__ eA, const int* __restrict__ eB,
+               const __grid_constant__ PairList pl, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + ESTAGES * E_A_STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + ESTAGES * E_STAGE);
+  uint64_t* empty = full + ESTAGES;
+  uint64_t* tfull = empty + ESTAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ESTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], E_EPI_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(E_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int npairs = pl.n;
+  const int cpp = (nkb + E_CHUNK - 1) / E_CHUNK;  // chunks per pair
+
+  if (warp == 0 && lane == 0) {
+    uint32_t g = 0, issued = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int m0 = (tile / tiles_n) * EBM, n0 = (tile % tiles_n) * EBN;
+      for (int q = 0; q < npairs && ok; ++q) {
+        const int xa = pl.a[q] * Kp, xb = pl.b[q] * Kp;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % ESTAGES;
+          if (!mbar_wait(&empty[s], ((g / ESTAGES) & 1u) ^ 1u)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], E_STAGE);
+          tma_load_2d(sA + s * E_A_STAGE, &tmA, xa + kb * 64, m0, &full[s]);
+          tma_load_2d(sB + s * E_B_STAGE, &tmB, xb + kb * 64, n0, &full[s]);
+          issued = g + 1;
+        }
+      }
+    }
+    if (!ok) atomicOr(err, 1);
+    for (uint32_t q = (issued > ESTAGES ? issued - ESTAGES : 0); q < issued; ++q)
+      if (!mbar_wait(&full[q % ESTAGES], (q / ESTAGES) & 1u)) atomicOr(err, 1);
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t id = idesc<TC_BF16, EBM, EBN>();
+    uint32_t g = 0, gc = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      for (int q = 0; q < npairs && ok; ++q) {
+        for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
+          const bool first = (kb % E_CHUNK) == 0;
+          const uint32_t buf = gc & 1u;
+          if (first) {
+            if (!mbar_wait(&tempty[buf], ((gc >> 1) & 1u) ^ 1u)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          const int s = g % ESTAGES;
+          if (!mbar_wait(&full[s], (g / ESTAGES) & 1u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = sdesc(smem_u32(sA + s * E_A_STAGE));
+          const uint64_t bd = sdesc(smem_u32(sB + s * E_B_STAGE));
+          const uint32_t dt = tmem + buf * (uint32_t)EBN;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            umma<TC_BF16>(dt, ad + 2u * k, bd + 2u * k, id, (!first || k > 0) ? 1u : 0u);
+          umma_commit(&empty[s]);
+          if ((kb % E_CHUNK) == E_CHUNK - 1 || kb == nkb - 1) {
+            umma_commit(&tfull[buf]);
+            ++gc;
+          }
+        }
+      }
+    }
+    if (!ok) atomicOr(err, 1);
+    if (gc > 0 && !mbar_wait(&tfull[(gc - 1) & 1u], ((gc - 1) >> 1) & 1u)) atomicOr(err, 1);
+  } else if (warp >= 2) {
+    const int qd = warp & 3;
+    const int part = (warp - 2) >> 2;
+    uint32_t gc = 0;
+    bool ok = true;
+    const int nchunk = npairs * cpp;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int m0 = (tile / tiles_n) * EBM, n0 = (tile % tiles_n) * EBN;
+      double acc[E_EPI_COLS];
+#pragma unroll
+      for (int j = 0; j < E_EPI_COLS; ++j) acc[j] = 0.0;
+      for (int c = 0; c < nchunk; ++c, ++gc) {
+        const uint32_t buf = gc & 1u;
+        if (!mbar_wait(&tfull[buf], (gc >> 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(qd * 32) << 16) + buf * (uint32_t)EBN + part * E_EPI_COLS;
+#pragma unroll
+        for (int j = 0; j < E_EPI_COLS / 16; ++j) {
+          uint32_t r[16];
+          tmem_ld16(base + 16 * j, r);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[16 * j + i] += (double)__uint_as_float(r[i]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+      }
+      if (!ok) break;
+      const int64_t row = (int64_t)m0 + qd * 32 + lane;
+      const int64_t col0 = (int64_t)n0 + part * E_EPI_COLS;
+      if (row < M) {
+        const int ea = eA[row];
+        double* dst = C + row * ldc + col0;
+#pragma unroll
+        for (int j = 0; j < E_EPI_COLS; ++j)
+          if (col0 + j < N) dst[j] = scalbn(acc[j], ea + eB[col0 + j]);
+      }
+    }
+    if (!ok) atomicOr(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(E_TMEM_COLS));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Slicing
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double load_view(const SplitView& v, int64_t r, int64_t k) {
+  const int64_t r0 = r / v.n1, r1 = r - r0 * v.n1;
+  const int64_t off = r0 * v.s0 + r1 * v.s1 + k * v.sk;
+  return v.src_f32 ? (double)reinterpret_cast<const float*>(v.src)[off]
+                   : reinterpret_cast<const double*>(v.src)[off];
+}
+
+__device__ __forceinline__ int row_exponent(double amax) {
+  return amax > 0.0 ? ilogb(amax) + 1 : 0;  // |x| < 2^e for every x of the row
+}
+
+// e[r] for rows whose K index is contiguous: one block per row.
+__global__ void k_rowexp_contig(SplitView v, int* __restrict__ e) {
+  __shared__ double sh[8];
+  const int64_t r = blockIdx.x;
+  double m = 0.0;
+  for (int64_t k = threadIdx.x; k < v.K; k += blockDim.x) m = fmax(m, fabs(load_view(v, r, k)));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, sh[i]);
+    e[r] = row_exponent(fmax(m, sh[0]));
+  }
+}
+
+// e[r] for rows that are adjacent in memory (K strided): one thread per row.
+__global__ void k_rowexp_strided(SplitView v, int* __restrict__ e) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.rows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double m = 0.0;
+    for (int64_t k = 0; k < v.K; ++k) m = fmax(m, fabs(load_view(v, r, k)));
+    e[r] = row_exponent(m);
+  }
+}
+
+__device__ __forceinline__ void store_slices(__nv_bfloat16* dst, int64_t base, int64_t Kp, double x,
+                                             int e) {
+  double r = scalbn(x, -e);  // |r| < 1
+#pragma unroll
+  for (int p = 0; p < SLICES; ++p) {
+    const double scale = (double)(1ll << (SLICE_BITS * (p + 1)));
+    const double q = rint(r * scale);
+    const double sl = q / scale;
+    dst[base + (int64_t)p * Kp] = __double2bfloat16(sl);
+    r -= sl;
+  }
+}
+
+__global__ void k_slice_direct(SplitView v, const int* __restrict__ e, __nv_bfloat16* __restrict__ dst,
+                               int64_t Kp) {
+  const int64_t total = v.rows * Kp;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / Kp, k = t - r * Kp;
+    const double x = (k < v.K) ? load_view(v, r, k) : 0.0;
+    store_slices(dst, r * SLICES * Kp + k, Kp, x, e[r]);
+  }
+}
+
+__global__ void k_slice_transpose(SplitView v, const int* __restrict__ e,
+                                  __nv_bfloat16* __restrict__ dst, int64_t Kp) {
+  __shared__ double tile[32][33];
+  const int64_t r_base = (int64_t)blockIdx.x * 32, k_base = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t k = k_base + j, r = r_base + tx;
+    tile[j][tx] = (k < v.K && r < v.rows) ? load_view(v, r, k) : 0.0;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t r = r_base + j, k = k_base + tx;
+    if (r < v.rows && k < Kp) store_slices(dst, r * SLICES * Kp + k, Kp, tile[tx][j], e[r]);
+  }
+}
+
+int blocks_1d(int64_t n, int t) {
+  int64_t b = cdiv(n, t);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 65536));
+}
+
+osmps_status slice_operand(const SplitView& v, int64_t Kp, int* e, __nv_bfloat16* dst,
+                           cudaStream_t s) {
+  if (v.rows <= 0) return OSMPS_OK;
+  const bool contig = (v.sk == 1);
+  if (contig) {
+    if (v.rows > 2147483647ll) return set_error(OSMPS_ESHAPE, "emulated GEMM: too many rows");
+    { k_rowexp_contig<<<(unsigned)v.rows, 256, 0, s>>>(v, e); note_launch(); }
+    { k_slice_direct<<<blocks_1d(v.rows * Kp, 256), 256, 0, s>>>(v, e, dst, Kp); note_launch(); }
+  } else {
+    { k_rowexp_strided<<<blocks_1d(v.rows, 256), 256, 0, s>>>(v, e); note_launch(); }
+    if (cdiv(Kp, 32) > 65535) return set_error(OSMPS_ESHAPE, "emulated GEMM: K too large");
+    dim3 grid((unsigned)cdiv(v.rows, 32), (unsigned)cdiv(Kp, 32));
+    { k_slice_transpose<<<grid, dim3(32, 8), 0, s>>>(v, e, dst, Kp); note_launch(); }
+  }
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+PairList make_pairs() {
+  PairList pl{};
+  pl.n = 0;
+  for (int sum = 0; sum < SLICES; ++sum)
+    for (int i = 0; i <= sum; ++i) {
+      pl.a[pl.n] = (unsigned char)i;
+      pl.b[pl.n] = (unsigned char)(sum - i);
+      ++pl.n;
+    }
+  return pl;
+}
+
+}  // namespace
+
+osmps_status gemm_emu(osmps_ctx* ctx, const SplitView& a, const SplitView& b, int64_t M,
+                      int64_t N, int64_t K, double* C, int64_t ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return OSMPS_OK;
+  if (K <= 0 || a.rows != M || b.rows != N || a.K != K || b.K != K)
+    return set_error(OSMPS_ESHAPE, "gemm_emu: inconsistent operand views");
+  const int64_t Kp = round_up(K, 64);
+  if (SLICES * Kp > ((int64_t)1 << 31) || cdiv(M, EBM) * cdiv(N, EBN) > ((int64_t)1 << 31))
+    return set_error(OSMPS_ESHAPE, "gemm_emu: dimensions exceed the supported range");
+  osmps_status st = OSMPS_OK;
+  auto* sa = (__nv_bfloat16*)ws_get(ctx, SLOT_EMU_A, (size_t)M * SLICES * Kp * 2, s, &st);
+  if (!sa) return st;
+  auto* sb = (__nv_bfloat16*)ws_get(ctx, SLOT_EMU_B, (size_t)N * SLICES * Kp * 2, s, &st);
+  if (!sb) return st;
+  int* ex = (int*)ws_get(ctx, SLOT_EMU_EXP, (size_t)(M + N + 64) * sizeof(int), s, &st);
+  if (!ex) return st;
+  int* eA = ex;
+  int* eB = ex + ((M + 63) / 64) * 64;
+  OSMPS_TRY(slice_operand(a, Kp, eA, sa, s));
+  OSMPS_TRY(slice_operand(b, Kp, eB, sb, s));
+  CUtensorMap ma, mb;
+  OSMPS_TRY(tc_make_map(&ma, sa, TC_BF16, M, SLICES * Kp, EBM));
+  OSMPS_TRY(tc_make_map(&mb, sb, TC_BF16, N, SLICES * Kp, EBN));
+  static bool configured = false;
+  if (!configured) {
+    OSMPS_CUDA(cudaFuncSetAttribute(k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)E_SMEM));
+    configured = true;
+  }
+  static const PairList pl = make_pairs();
+  const int tiles_n = (int)cdiv(N, EBN);
+  const int n_tiles = tiles_n * (int)cdiv(M, EBM);
+  const int grid = std::min(n_tiles, ctx->sm_count);
+  const int nkb = (int)(Kp / 64);
+  const int ph = prof_begin(s);
+  {
+    k_gemm_emu<<<grid, E_THREADS, E_SMEM, s>>>(ma, mb, C, M, N, ldc, nkb, (int)Kp, tiles_n,
+                                               n_tiles, eA, eB, pl, ctx->dev_flags);
+    note_launch();
+  }
+  OSMPS_LAUNCH_CHECK();
+  const double logical = 2.0 * (double)M * (double)N * (double)K;
+  prof_end(ph, s, OSMPS_KERNEL_GEMM_EMU, logical, (double)pl.n * logical);
+  return OSMPS_OK;
+}
+
+}  // namespace osmps
+
+using namespace osmps;
+
+extern "C" osmps_status osmps_dgemm_emu(osmps_ctx* ctx, const double* A, const double* B, double* C,
+                                        int64_t M, int64_t N, int64_t K, void* stream) {
+  clear_error();
+  if (!ctx || !A || !B || !C) return set_error(OSMPS_EINVAL, "osmps_dgemm_emu: null argument");
+  if (C == A || C == B) return set_error(OSMPS_EINVAL, "osmps_dgemm_emu: C aliases an input");
+  if (M <= 0 || N <= 0 || K <= 0) return set_error(OSMPS_ESHAPE, "osmps_dgemm_emu: dimensions");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
+  SplitView a;
+  a.src = A; a.rows = M; a.K = K; a.s0 = K; a.sk = 1;
+  SplitView b;  // row n of the B operand = column n of B
+  b.src = B; b.rows = N; b.K = K; b.s0 = 1; b.sk = N;
+  return gemm_emu(ctx, a, b, M, N, K, C, N, (cudaStream_t)stream);
+}

@@ -26,10 +26,13 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace osmps {
 
 namespace {
+
+using namespace tc;
 
 constexpr int BM = 128;
 constexpr int BN = 256;
@@ -44,141 +47,6 @@ constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int CHUNK = 4;                     // K slices (x 4 MMAs) per TMEM partial sum
 constexpr uint32_t TMEM_COLS = 512;          // two 256-column accumulator buffers
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint64_t t0 = 0;
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if ((i & 255u) == 0) {
-      uint64_t t = globaltimer();
-      if (i == 0) t0 = t;
-      else if (t - t0 > WAIT_LIMIT_NS) return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of
-// 128 bytes, 8-row core groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: D f32, A/B bf16 (kind::f16) or tf32 (kind::tf32),
-// both K-major, M = 128, N = 256.
-template <int KIND>
-__device__ __forceinline__ uint32_t idesc() {
-  const uint32_t ab = (KIND == TC_BF16) ? 1u : 2u;
-  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
-}
-
-template <int KIND>
-__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id,
-                                     uint32_t accumulate) {
-  if (KIND == TC_BF16) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(id), "r"(accumulate));
-  } else {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(id), "r"(accumulate));
-  }
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32"
-      " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
-      " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 template <int OUT>
 __device__ __forceinline__ void store_row(void* C, int64_t row, int64_t col0, int64_t N,
@@ -285,7 +153,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (uint32_t q = (issued > STAGES ? issued - STAGES : 0); q < issued; ++q)
       if (!mbar_wait(&full[q % STAGES], (q / STAGES) & 1u)) atomicOr(err, 1);
   } else if (warp == 1 && lane == 0) {
-    const uint32_t id = idesc<KIND>();
+    const uint32_t id = idesc<KIND, BM, BN>();
     uint32_t g = 0, gc = 0;  // slices / chunks consumed by this CTA
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -380,15 +248,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-osmps_status make_map(CUtensorMap* map, const void* base, int kind, int64_t rows, int64_t Kp,
-                      int box_rows) {
+}  // namespace
+
+osmps_status tc_make_map(CUtensorMap* map, const void* base, int kind, int64_t rows, int64_t cols,
+                         int box_rows) {
   auto fn = encode_fn();
   if (!fn) return set_error(OSMPS_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
   const size_t es = tc_elem_bytes(kind);
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0)
     return set_error(OSMPS_EINVAL, "tensor-core operand base not 16-byte aligned");
-  cuuint64_t dims[2] = {(cuuint64_t)(2 * Kp), (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(2 * Kp * es)};
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * es)};
   cuuint32_t box[2] = {(cuuint32_t)(KSLICE_BYTES / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, kind == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -396,10 +266,12 @@ osmps_status make_map(CUtensorMap* map, const void* base, int kind, int64_t rows
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
-    return set_error(OSMPS_ECUDA, "cuTensorMapEncodeTiled failed (%d): rows=%lld Kp=%lld", (int)r,
-                     (long long)rows, (long long)Kp);
+    return set_error(OSMPS_ECUDA, "cuTensorMapEncodeTiled failed (%d): rows=%lld cols=%lld", (int)r,
+                     (long long)rows, (long long)cols);
   return OSMPS_OK;
 }
+
+namespace {
 
 template <int KIND, int OUT>
 osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g, int* err,
@@ -436,8 +308,8 @@ osmps_status gemm_tc(osmps_ctx* ctx, const GemmTc& g, cudaStream_t stream) {
       g.N > ((int64_t)1 << 31))
     return set_error(OSMPS_ESHAPE, "gemm_tc: dimensions exceed the supported range");
   CUtensorMap ma, mb;
-  OSMPS_TRY(make_map(&ma, g.A, g.kind, g.M, g.Kp, BM));
-  OSMPS_TRY(make_map(&mb, g.B, g.kind, g.N, g.Kp, BN));
+  OSMPS_TRY(tc_make_map(&ma, g.A, g.kind, g.M, 2 * g.Kp, BM));
+  OSMPS_TRY(tc_make_map(&mb, g.B, g.kind, g.N, 2 * g.Kp, BN));
   int* err = ctx->dev_flags;
   if (g.kind == TC_BF16) {
     if (g.out == TC_OUT_F32) return launch<TC_BF16, TC_OUT_F32>(ma, mb, g, err, ctx->sm_count, stream);

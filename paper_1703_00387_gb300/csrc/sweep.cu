@@ -258,7 +258,7 @@ osmps_status two_site_step(osmps_ctx* ctx, osmps_mps* m, const osmps_mpo* h, int
   int64_t chn = 0;
   double disc = 0.0, ent = 0.0;
   OSMPS_TRY(split_impl(ctx, theta, m->A[k], m->A[k + 1], chl, d1, d2, chr, move_right ? 1 : 0,
-                       chi_max, eps_local, &chn, &disc, &ent, nullptr, s));
+                       chi_max, eps_local, &chn, &disc, &ent, nullptr, precision, s));
   m->chi[k + 1] = chn;
   if (move_right) {
     OSMPS_TRY(env_update_impl(ctx, 0, m->Lenv[k], m->A[k], h->W[k], m->Lenv[k + 1], chl, d1, chn,
@@ -302,7 +302,7 @@ osmps_status energy_impl(osmps_ctx* ctx, const osmps_mps* m, const osmps_mpo* h,
       const double* W = pass == 0 ? h->W[k] : h->ident[k];
       const int64_t wi = pass == 0 ? h->w[k] : 1, wo = pass == 0 ? h->w[k + 1] : 1;
       OSMPS_TRY(env_update_impl(ctx, 0, a, m->A[k], W, b, m->chi[k], m->d[k], m->chi[k + 1], wi, wo,
-                                OSMPS_PREC_FP64, s));
+                                OSMPS_PREC_FP64_EMU, s));
       std::swap(a, b);
     }
     OSMPS_CUDA(cudaMemcpyAsync(&vals[pass], a, 8, cudaMemcpyDeviceToHost, s));
@@ -516,17 +516,22 @@ osmps_status osmps_sweep(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo,
   const double eps = p->eps_local < 0.0 ? 1e-12 / (4.0 * L) : p->eps_local;
   const int total_sweeps = p->n_sweeps + p->refine_sweeps;
   OSMPS_TRY(canonicalize(ctx, mps, mpo, 0, total_sweeps > 0 && p->n_sweeps > 0 ? p->precision : OSMPS_PREC_FP64, s));
+  OSMPS_CUDA(cudaStreamSynchronize(s));
+  auto t_sweeps = std::chrono::steady_clock::now();
   osmps_sweep_stats st{};
   if (stats) {
     st.step_energies = stats->step_energies;
     st.step_iters = stats->step_iters;
   }
   int64_t idx = 0;
+  // Refinement sweeps run float64-accurate contractions: emulated on the
+  // tensor cores after tensor-core sweeps, plain float64 otherwise.
+  const int refine_prec = p->precision == OSMPS_PREC_FP64 ? OSMPS_PREC_FP64 : OSMPS_PREC_FP64_EMU;
   for (int sw = 0; sw < total_sweeps; ++sw) {
-    const int prec = sw < p->n_sweeps ? p->precision : OSMPS_PREC_FP64;
+    const int prec = sw < p->n_sweeps ? p->precision : refine_prec;
     if (sw == p->n_sweeps && sw > 0 && prec != p->precision) {
-      // refinement: rebuild the right environments in float64
-      OSMPS_TRY(canonicalize(ctx, mps, mpo, 0, OSMPS_PREC_FP64, s));
+      // refinement: rebuild the right environments in the refinement precision
+      OSMPS_TRY(canonicalize(ctx, mps, mpo, 0, refine_prec, s));
     }
     for (int dir = 0; dir < 2; ++dir) {
       for (int64_t i = 0; i < L - 1; ++i) {
@@ -547,8 +552,14 @@ osmps_status osmps_sweep(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo,
       }
     }
   }
+  OSMPS_CUDA(cudaStreamSynchronize(s));
+  auto t_energy = std::chrono::steady_clock::now();
   OSMPS_TRY(energy_impl(ctx, mps, mpo, &st.energy, s));
-  st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  auto t_end = std::chrono::steady_clock::now();
+  st.seconds = std::chrono::duration<double>(t_end - t0).count();
+  st.sweep_seconds = std::chrono::duration<double>(t_energy - t_sweeps).count();
+  st.setup_seconds = std::chrono::duration<double>(t_sweeps - t0).count();
+  st.energy_seconds = std::chrono::duration<double>(t_end - t_energy).count();
   if (stats) *stats = st;
   return OSMPS_OK;
 }

@@ -50,7 +50,7 @@ def main():
         B.osmps_lanczos_ground(ctx, L, Wt, Wt, R, x, max_iter=20, tol=1e-10, precision=args.prec)
         a1 = torch.empty(chi * d * chi, dtype=torch.float64, device=dev)
         a2 = torch.empty(chi * d * chi, dtype=torch.float64, device=dev)
-        chn, _, _, _ = B.osmps_split(ctx, x, a1, a2, 1, chi, 1e-14)
+        chn, _, _, _ = B.osmps_split(ctx, x, a1, a2, 1, chi, 1e-14, precision=args.prec)
         Lo = torch.empty(chn * w * chn, dtype=torch.float64, device=dev)
         B.osmps_env_update(ctx, 0, L, a1[: chi * d * chn].view(chi, d, chn), Wt,
                            Lo.view(chn, w, chn), precision=args.prec)
