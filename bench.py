@@ -289,6 +289,10 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.quick:
         line["fp64_gpu"] = fp64_leg(B, ctx, mps, mpo, k, args)
         k = line["fp64_gpu"].pop("_k")
+        line["fp64emu_gpu"] = fp64_leg(B, ctx, mps, mpo, k, args, prec="fp64emu")
+        k = line["fp64emu_gpu"].pop("_k")
+        line["fp64emu_gpu"]["note"] = ("float64-accurate contractions emulated on the bf16 tensor "
+                                       "cores (the refinement-sweep precision)")
         line["e2e"] = e2e_leg(B, ctx, Wh, prec, args)
         if not args.no_sweep:
             line["sweep_s"] = sweep_leg(B, ctx, mpo, prec)
@@ -315,9 +319,9 @@ def traffic_per_launch(prof):
     return d.get("bytes_per_launch")
 
 
-def fp64_leg(B, ctx, mps, mpo, k, args):
+def fp64_leg(B, ctx, mps, mpo, k, args, prec="fp64"):
     import torch
-    params = B.sweep_params(CHI, 1, "fp64", lanczos_tol=LANCZOS_TOL, lanczos_max_iter=LANCZOS_CAP)
+    params = B.sweep_params(CHI, 1, prec, lanczos_tol=LANCZOS_TOL, lanczos_max_iter=LANCZOS_CAP)
     B.osmps_sweep_step(ctx, mps, mpo, k, 1, params)  # warm-up
     k += 1
     torch.cuda.synchronize()

@@ -4,15 +4,19 @@
 // thousand times faster. A float64 GEMM is emulated on them exactly in the
 // manner of Ozaki's error-free transformation of matrix products:
 //   * every row of A (and of B, both K-major) is scaled by a power of two
-//     2^-e so that its entries lie in (-1, 1), and cut into S = 8 slices
-//     x = sum_p q_p 2^(-7(p+1)), q_p an integer with |q_p| <= 128, so every
-//     slice is exact in bf16;
-//   * for a slice pair (i, j) all products q_i q_j share the unit
-//     2^(-7(i+j+2)) and are at most 2^14 units, so a run of 256 of them sums
-//     to less than 2^22 units: exact in the float32 TMEM accumulator;
-//   * those exact partial sums are added in float64 registers, over the 36
-//     pairs with i + j <= 7 (the dropped pairs are below 2^-56 of the row
-//     scales), and the tile is scaled back by 2^(e_A[row] + e_B[col]).
+//     2^-e so that its entries lie in (-1, 1), rounded to 56 fractional bits
+//     and cut into S = 8 balanced base-128 digits q_p (|q_p| <= 128), so
+//     x = 2^e sum_p q_p 2^(-7(p+1)); the slices hold the integers q_p, exact
+//     in bf16 (all of this with integer arithmetic on the IEEE bits);
+//   * a slice pair (i, j) gives integer products q_i q_j of at most 2^14, so
+//     a run of 256 of them sums to less than 2^22: exact in the float32 TMEM
+//     accumulator;
+//   * the epilogue adds those exact integers in int32 per slice diagonal
+//     i + j (same unit 2^(-7(i+j+2))) and moves each diagonal into float64
+//     once, over the 36 pairs with i + j <= 7 (the dropped pairs are below
+//     2^-56 of the row scales); the tile is scaled back by 2^(e_A + e_B).
+// GB300's float64 pipe is what limits this kind of kernel, so the float64
+// work is kept to ~10 operations per output element per tile.
 // The kernel reuses the persistent, warp-specialised structure of gemm_tc:
 // 128 x 128 tiles, a 6-stage TMA ring, two 128-column TMEM buffers, 16
 // epilogue warps each holding 32 float64 accumulators per row.
@@ -41,6 +45,7 @@ constexpr int E_EPI_COLS = EBN / 4;
 constexpr int E_THREADS = 64 + 32 * E_EPI_WARPS;
 constexpr int E_CHUNK = 4;  // 64-element K slices per exact partial sum (256 products)
 constexpr uint32_t E_TMEM_COLS = 256;
+constexpr int FLUSH_EVERY = 64;  // chunks per int32 run: 64 * 2^22 < 2^31
 constexpr size_t E_SMEM = (size_t)ESTAGES * E_STAGE + 1024 + 256;
 
 struct PairList {
@@ -155,32 +160,62 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     const int part = (warp - 2) >> 2;
     uint32_t gc = 0;
     bool ok = true;
-    const int nchunk = npairs * cpp;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const int m0 = (tile / tiles_n) * EBM, n0 = (tile % tiles_n) * EBN;
-      double acc[E_EPI_COLS];
+      double acc[E_EPI_COLS];  // float64 sum of the flushed diagonals
+      int iacc[E_EPI_COLS];    // exact integer sum of the current diagonal
 #pragma unroll
-      for (int j = 0; j < E_EPI_COLS; ++j) acc[j] = 0.0;
-      for (int c = 0; c < nchunk; ++c, ++gc) {
-        const uint32_t buf = gc & 1u;
-        if (!mbar_wait(&tfull[buf], (gc >> 1) & 1u)) {
-          ok = false;
-          break;
+      for (int j = 0; j < E_EPI_COLS; ++j) {
+        acc[j] = 0.0;
+        iacc[j] = 0;
+      }
+      int cur = pl.a[0] + pl.b[0];
+      int run = 0;
+      for (int q = 0; q < npairs && ok; ++q) {
+        const int diag = pl.a[q] + pl.b[q];
+        for (int c = 0; c < cpp; ++c, ++gc) {
+          if (diag != cur || run == FLUSH_EVERY) {
+            // flush: sum(int) x 2^(-7 (cur + 2)) into float64, once per diagonal
+            const double unit = ldexp(1.0, -SLICE_BITS * (cur + 2));
+#pragma unroll
+            for (int j = 0; j < E_EPI_COLS; ++j) {
+              acc[j] = fma((double)iacc[j], unit, acc[j]);
+              iacc[j] = 0;
+            }
+            cur = diag;
+            run = 0;
+          }
+          const uint32_t buf = gc & 1u;
+          if (!mbar_wait(&tfull[buf], (gc >> 1) & 1u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t base =
+              tmem + ((uint32_t)(qd * 32) << 16) + buf * (uint32_t)EBN + part * E_EPI_COLS;
+#pragma unroll
+          for (int j = 0; j < E_EPI_COLS / 16; ++j) {
+            uint32_t r[16];
+            tmem_ld16(base + 16 * j, r);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              // exact integer (|v| < 2^22): v + 1.5*2^23 has v in its low mantissa bits
+              const float v = __uint_as_float(r[i]) + 12582912.0f;
+              iacc[16 * j + i] += (int)(__float_as_uint(v) - 0x4B400000u);
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
+          ++run;
         }
-        tc_fence_after();
-        const uint32_t base = tmem + ((uint32_t)(qd * 32) << 16) + buf * (uint32_t)EBN + part * E_EPI_COLS;
-#pragma unroll
-        for (int j = 0; j < E_EPI_COLS / 16; ++j) {
-          uint32_t r[16];
-          tmem_ld16(base + 16 * j, r);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) acc[16 * j + i] += (double)__uint_as_float(r[i]);
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[buf]);
       }
       if (!ok) break;
+      {
+        const double unit = ldexp(1.0, -SLICE_BITS * (cur + 2));
+#pragma unroll
+        for (int j = 0; j < E_EPI_COLS; ++j) acc[j] = fma((double)iacc[j], unit, acc[j]);
+      }
       const int64_t row = (int64_t)m0 + qd * 32 + lane;
       const int64_t col0 = (int64_t)n0 + part * E_EPI_COLS;
       if (row < M) {
@@ -212,22 +247,29 @@ __device__ __forceinline__ double load_view(const SplitView& v, int64_t r, int64
                    : reinterpret_cast<const double*>(v.src)[off];
 }
 
-__device__ __forceinline__ int row_exponent(double amax) {
-  return amax > 0.0 ? ilogb(amax) + 1 : 0;  // |x| < 2^e for every x of the row
+// Biased exponent field of |x| (0 for zero and subnormals): comparing the
+// magnitude bits as integers orders doubles by size.
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+__device__ __forceinline__ int exponent_of_max(unsigned long long mbits) {
+  const int E = (int)(mbits >> 52);
+  return E == 0 ? 0 : E - 1022;  // |x| < 2^(E - 1022) for every x of the row
 }
 
 // e[r] for rows whose K index is contiguous: one block per row.
 __global__ void k_rowexp_contig(SplitView v, int* __restrict__ e) {
-  __shared__ double sh[8];
+  __shared__ unsigned long long sh[8];
   const int64_t r = blockIdx.x;
-  double m = 0.0;
-  for (int64_t k = threadIdx.x; k < v.K; k += blockDim.x) m = fmax(m, fabs(load_view(v, r, k)));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  unsigned long long m = 0;
+  for (int64_t k = threadIdx.x; k < v.K; k += blockDim.x) m = max(m, mag_bits(load_view(v, r, k)));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, sh[i]);
-    e[r] = row_exponent(fmax(m, sh[0]));
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = max(m, sh[i]);
+    e[r] = exponent_of_max(max(m, sh[0]));
   }
 }
 
@@ -235,23 +277,43 @@ __global__ void k_rowexp_contig(SplitView v, int* __restrict__ e) {
 __global__ void k_rowexp_strided(SplitView v, int* __restrict__ e) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.rows;
        r += (int64_t)gridDim.x * blockDim.x) {
-    double m = 0.0;
-    for (int64_t k = 0; k < v.K; ++k) m = fmax(m, fabs(load_view(v, r, k)));
-    e[r] = row_exponent(m);
+    unsigned long long m = 0;
+    for (int64_t k = 0; k < v.K; ++k) m = max(m, mag_bits(load_view(v, r, k)));
+    e[r] = exponent_of_max(m);
   }
 }
 
+// x * 2^(56 - e) rounded to the nearest integer, from the IEEE bits (integer
+// arithmetic only). |x| < 2^e, so |X| <= 2^56. Subnormal inputs count as 0.
+__device__ __forceinline__ long long fixed56(double x, int e) {
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  if (E == 0) return 0;
+  const long long mant = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+  const int sh = E - 1075 + 56 - e;  // value = mant * 2^(E - 1075)
+  long long X;
+  if (sh >= 0) X = mant << sh;  // sh <= 3 since |x| < 2^e
+  else if (sh < -62) X = 0;
+  else X = (mant + (1ll << (-sh - 1))) >> (-sh);
+  return bits < 0 ? -X : X;
+}
+
+// Balanced base-128 digits of X: X = sum_p d_p 128^(7 - p); d_1..d_7 in
+// [-64, 63], d_0 in [-128, 128]; slice p of the operand is the integer d_p
+// (exact in bf16) and stands for d_p 2^(-7 (p + 1)) 2^e.
 __device__ __forceinline__ void store_slices(__nv_bfloat16* dst, int64_t base, int64_t Kp, double x,
                                              int e) {
-  double r = scalbn(x, -e);  // |r| < 1
+  long long X = fixed56(x, e);
+  int d[SLICES];
 #pragma unroll
-  for (int p = 0; p < SLICES; ++p) {
-    const double scale = (double)(1ll << (SLICE_BITS * (p + 1)));
-    const double q = rint(r * scale);
-    const double sl = q / scale;
-    dst[base + (int64_t)p * Kp] = __double2bfloat16(sl);
-    r -= sl;
+  for (int p = SLICES - 1; p > 0; --p) {
+    const int dig = (int)(((X + 64) & 127) - 64);
+    d[p] = dig;
+    X = (X - dig) >> SLICE_BITS;
   }
+  d[0] = (int)X;
+#pragma unroll
+  for (int p = 0; p < SLICES; ++p) dst[base + (int64_t)p * Kp] = __float2bfloat16_rn((float)d[p]);
 }
 
 __global__ void k_slice_direct(SplitView v, const int* __restrict__ e, __nv_bfloat16* __restrict__ dst,
