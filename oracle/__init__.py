@@ -19,6 +19,9 @@ following the paper's steps in order:
                 Hamiltonian application, environment updates, Lanczos,
                 eigendecomposition/SVD split with truncation (Sec. 2,
                 Eq. AAD_ULLUD, Eq. elocal), sweeps and the MPO energy.
+* ``grad``   -- gradients for the differentiation workload: the vector-Jacobian
+                product of H_eff.theta and dE/dW_k of the MPO energy at a
+                fixed state, with the chain rule to XXZ couplings.
 
 Parity status: every function is pinned by a test in ``tests/test_oracle_*.py``
 against exact diagonalisation, a closed form, the paper's worked example, or a
