@@ -231,6 +231,9 @@ const double* osmps_mps_device_tensor(const osmps_mps* mps, int64_t k);
 osmps_status osmps_mpo_create(osmps_ctx* ctx, int64_t L, const int64_t* d, const int64_t* w,
                               const double* const* host_W, osmps_mpo** out);
 osmps_status osmps_mpo_destroy(osmps_mpo* mpo);
+/* Overwrite every site tensor of an existing MPO with new values of the same
+ * shapes (HOST arrays as for osmps_mpo_create). Synchronises the device.  */
+osmps_status osmps_mpo_set(osmps_mpo* mpo, const double* const* host_W);
 
 typedef struct {
   int64_t chi_max;        /* maximal bond dimension                                  */
@@ -307,6 +310,60 @@ osmps_status osmps_sweep(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo,
  * result; contractions on the float64-accurate emulated GEMM).            */
 osmps_status osmps_energy(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo* mpo,
                           double* energy_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Gradients (differentiation of the Sec. 3.4 operators; the paper has no
+ * backward pass). Every quantity below is linear in the tensor it is
+ * differentiated by, so each gradient is a full contraction of the incoming
+ * cotangent with all other factors.
+ * ---------------------------------------------------------------------- */
+
+/* Vector-Jacobian product of y = H_eff(L, W1, W2, R) theta (osmps_heff_apply)
+ * for an output cotangent gy (chi_l, d1, d2, chi_r):
+ *   gtheta = H_eff^T gy   (the same four-stage contraction with bra and ket
+ *            swapped in L, W1, W2 and R; computed in `precision`),
+ *   gW1[w,t1,s1,w1] = sum gy[a2,t1,t2,c2] L[a2,w,a] theta[a,s1,s2,c] W2[w1,t2,s2,w2] R[c2,w2,c],
+ *   gW2[w1,t2,s2,w2] = sum gy[a2,t1,t2,c2] L[a2,w,a] theta[a,s1,s2,c] W1[w,t1,s1,w1] R[c2,w2,c].
+ * gtheta, gW1, gW2 are device outputs with the shapes of theta, W1 and W2;
+ * any of them may be NULL (not computed). theta may be NULL when gW1 and gW2
+ * are. gW1 and gW2 are float64-accurate in every precision (DMMA for
+ * OSMPS_PREC_FP64, the emulated GEMM otherwise). gtheta must not alias gy or
+ * theta (EINVAL). wl*d1, d1*wm, wm*d2, d2*wr above 64 give EUNSUPPORTED when
+ * a weight gradient is requested.                                          */
+osmps_status osmps_heff_backward(osmps_ctx* ctx, const double* L, const double* W1,
+                                 const double* W2, const double* R, const double* theta,
+                                 const double* gy, double* gtheta, double* gW1, double* gW2,
+                                 int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r, int64_t wl,
+                                 int64_t wm, int64_t wr, int precision, void* stream);
+
+/* E = <psi|H|psi> / <psi|psi> of the MPS as it stands (Eq. mpo) and its
+ * gradient with respect to every MPO site tensor:
+ *   dE/dW_k[w,t,s,w2] = sum L_k[a2,w,a] A_k[a2,t,b2] A_k[a,s,b] R_{k+1}[b2,w2,b] / <psi|psi>
+ * with L_k, R_{k+1} the environments of the MPS (no canonical form assumed).
+ * gW: device output, the gradients of sites 0..L-1 concatenated, each
+ * (w[k], d[k], d[k], w[k+1]) row-major; gW_count must equal the total.
+ * checkpoint_every: 0 or 1 keeps all L right environments; s > 1 keeps only
+ * every s-th one and rebuilds the others block by block (about L/s + s
+ * environments alive, one extra right pass of work).
+ * precision: OSMPS_PREC_FP64 (DMMA) or OSMPS_PREC_FP64_EMU (emulated GEMM);
+ * others give EINVAL. energy_out, norm_out: host pointers, may be NULL.
+ * MPO blocks w*d above 64 give EUNSUPPORTED. Synchronises `stream`.        */
+osmps_status osmps_energy_grad(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo* mpo,
+                               double* gW, int64_t gW_count, int64_t checkpoint_every,
+                               int precision, double* energy_out, double* norm_out, void* stream);
+
+/* Chain rule from an MPO-tensor gradient to Hamiltonian couplings for an MPO
+ * that is affine in them, W = W_0 + sum_p c_p B_p:
+ *   g_par[p] = sum_{j = row_ptr[p]}^{row_ptr[p+1]-1} val[j] * gW[col[j]]
+ * (B in compressed sparse rows: row p lists the nonzero entries of B_p by
+ * their index into the concatenated MPO, as in osmps_energy_grad).
+ * row_ptr (n_par + 1 entries), col and val (nnz entries), gW (n_w entries)
+ * and g_par (n_par entries) are device arrays. A column outside [0, n_w) or
+ * a bad row pointer contributes nothing and gives EINVAL. Sums run in a
+ * fixed order. Synchronises `stream`.                                      */
+osmps_status osmps_coupling_grad(osmps_ctx* ctx, int64_t n_par, const int64_t* row_ptr,
+                                 const int64_t* col, const double* val, int64_t nnz,
+                                 const double* gW, int64_t n_w, double* g_par, void* stream);
 
 #ifdef __cplusplus
 }

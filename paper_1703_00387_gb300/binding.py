@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libosmps.so")
 PRECISION = {"fp64": 0, "bf16x3": 1, "tf32x3": 2, "fp64emu": 3}
 STATUS = {0: "OSMPS_OK", 1: "OSMPS_EINVAL", 2: "OSMPS_ESHAPE", 3: "OSMPS_ENOMEM", 4: "OSMPS_ECUDA",
           5: "OSMPS_ENOCONV", 6: "OSMPS_ETIMEOUT", 7: "OSMPS_ENAN", 8: "OSMPS_EUNSUPPORTED"}
-ENOCONV = 5
+EINVAL, ESHAPE, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENAN, EUNSUPPORTED = range(1, 9)
 
 _c = ctypes
 _i64 = _c.c_int64
@@ -86,6 +86,10 @@ _SIGS = {
                                     _c.POINTER(StepStats), _vp]),
     "osmps_sweep": (_c.c_int, [_vp, _vp, _vp, _c.POINTER(SweepParams), _c.POINTER(SweepStats), _vp]),
     "osmps_energy": (_c.c_int, [_vp, _vp, _vp, _dp, _vp]),
+    "osmps_mpo_set": (_c.c_int, [_vp, _c.POINTER(_dp)]),
+    "osmps_heff_backward": (_c.c_int, [_vp] + [_vp] * 9 + [_i64] * 7 + [_c.c_int, _vp]),
+    "osmps_energy_grad": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _c.c_int, _dp, _dp, _vp]),
+    "osmps_coupling_grad": (_c.c_int, [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
 }
 
 
@@ -316,6 +320,20 @@ class MPO:
         ptrs = (_dp * self.L)(*[x.ctypes.data_as(_dp) for x in W])
         self.ptr = _vp()
         _check(lib().osmps_mpo_create(ctx.ptr, self.L, d, w, ptrs, _c.byref(self.ptr)))
+        self.shapes = [x.shape for x in W]
+
+    def set(self, W):
+        """Overwrite the site tensors with new values of the same shapes."""
+        W = [np.ascontiguousarray(x, dtype=np.float64) for x in W]
+        if [x.shape for x in W] != self.shapes:
+            raise ValueError("MPO.set: shapes differ from the handle's")
+        ptrs = (_dp * self.L)(*[x.ctypes.data_as(_dp) for x in W])
+        _check(lib().osmps_mpo_set(self.ptr, ptrs))
+
+    @property
+    def n_params(self):
+        """Number of values in the concatenated site tensors."""
+        return int(sum(np.prod(sh) for sh in self.shapes))
 
     def close(self):
         if self.ptr:
@@ -368,3 +386,45 @@ def osmps_energy(ctx, mps, mpo, stream=None):
     e = _c.c_double()
     _check(lib().osmps_energy(ctx.ptr, mps.ptr, mpo.ptr, _c.byref(e), _stream(stream)))
     return e.value
+
+
+def _opt(t, name):
+    return _vp(0) if t is None else _dev(t, name)
+
+
+def osmps_heff_backward(ctx, L, W1, W2, R, theta, gy, gtheta=None, gW1=None, gW2=None,
+                        precision="fp64", stream=None):
+    """Vector-Jacobian product of H_eff.theta: fills whichever of gtheta, gW1,
+    gW2 are given (shapes of theta, W1, W2)."""
+    chi_l, d1, d2, chi_r = gy.shape
+    wl, wm, wr = W1.shape[0], W1.shape[3], W2.shape[3]
+    _check(lib().osmps_heff_backward(ctx.ptr, _dev(L, "L"), _dev(W1, "W1"), _dev(W2, "W2"),
+                                     _dev(R, "R"), _opt(theta, "theta"), _dev(gy, "gy"),
+                                     _opt(gtheta, "gtheta"), _opt(gW1, "gW1"), _opt(gW2, "gW2"),
+                                     chi_l, d1, d2, chi_r, wl, wm, wr, _prec(precision),
+                                     _stream(stream)))
+
+
+def osmps_energy_grad(ctx, mps, mpo, gW, checkpoint_every=0, precision="fp64emu", stream=None):
+    """E and dE/dW (written into the flat device tensor gW, sites concatenated).
+    Returns (energy, <psi|psi>)."""
+    e = _c.c_double()
+    n = _c.c_double()
+    _check(lib().osmps_energy_grad(ctx.ptr, mps.ptr, mpo.ptr, _dev(gW, "gW"), gW.numel(),
+                                   int(checkpoint_every), _prec(precision), _c.byref(e),
+                                   _c.byref(n), _stream(stream)))
+    return e.value, n.value
+
+
+def osmps_coupling_grad(ctx, row_ptr, col, val, gW, g_par, stream=None):
+    """g_par[p] = sum over row p of the CSR basis of val * gW[col] (int64 row_ptr
+    and col, float64 val, all CUDA tensors)."""
+    import torch
+    for t, nm in ((row_ptr, "row_ptr"), (col, "col")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int64 and t.is_contiguous()):
+            raise TypeError(f"{nm} must be a contiguous int64 CUDA tensor")
+    _check(lib().osmps_coupling_grad(ctx.ptr, g_par.numel(), _vp(row_ptr.data_ptr()),
+                                     _vp(col.data_ptr()), _dev(val, "val"), col.numel(),
+                                     _dev(gW, "gW"), gW.numel(), _dev(g_par, "g_par"),
+                                     _stream(stream)))
+    return g_par

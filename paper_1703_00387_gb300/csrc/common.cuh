@@ -94,6 +94,13 @@ enum Slot {
   SLOT_EIG_P,
   SLOT_EIG_E,
   SLOT_EIG_SCAL,
+  SLOT_GRAD_A,
+  SLOT_GRAD_B,
+  SLOT_GRAD_C,
+  SLOT_GRAD_M,
+  SLOT_GRAD_T,
+  SLOT_GRAD_PART,
+  SLOT_GRAD_ENVS,
   SLOT_COUNT
 };
 
@@ -248,7 +255,8 @@ osmps_status zero_pad_columns(void* dst, int kind, int64_t rows, int64_t Kcols, 
 // code selects one of the fixed orders used by the contractions.
 enum WOrder {
   WORD_IN_W_S__OUT_T_W2 = 0,   // i = (w, s),  o = (t, w2)   [left side]
-  WORD_IN_S_W2__OUT_W_T = 1    // i = (s, w2), o = (w, t)    [right side]
+  WORD_IN_S_W2__OUT_W_T = 1,   // i = (s, w2), o = (w, t)    [right side]
+  WORD_IN_T_W2__OUT_W_S = 2    // i = (t, w2), o = (w, s)    [left side, transposed]
 };
 osmps_status w_reorder(const double* W, int64_t dw, int64_t d, int64_t dw2, int order, double* Mat,
                        cudaStream_t stream);
@@ -289,6 +297,18 @@ osmps_status split_impl(osmps_ctx* ctx, const double* theta, double* A1, double*
                         int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r, int move_right,
                         int64_t chi_max, double eps_local, int64_t* chi_new, double* discarded,
                         double* entropy, double* lam2_out, int precision, cudaStream_t stream);
+
+// Gradients. fiber_weight_grad: dMat[i][o] = sum over the fibers of f of
+// X[fiber, i] Y[fiber, o] (X in the input layout of f, Y in its output
+// layout); P, Q <= 64. site_energy_grad: the MPO-energy gradient of one
+// site, scale * sum L[a2,w,a] A[a2,t,b2] A[a,s,b] R[b2,w2,b], written as
+// gW[w,t,s,w2]; precision FP64 (DMMA) or anything else (emulated float64).
+osmps_status fiber_weight_grad(osmps_ctx* ctx, const Fiber& f, const double* X, const double* Y,
+                               double* dMat, cudaStream_t s);
+osmps_status site_energy_grad(osmps_ctx* ctx, const double* Lenv, const double* A,
+                              const double* Renv, double* gW, int64_t chi_l, int64_t d,
+                              int64_t chi_r, int64_t wl, int64_t wr, double scale, int precision,
+                              cudaStream_t s);
 
 inline bool valid_precision(int p) {
   return p == OSMPS_PREC_FP64 || p == OSMPS_PREC_BF16X3 || p == OSMPS_PREC_TF32X3 ||

@@ -189,6 +189,10 @@ __global__ void k_w_reorder(const double* __restrict__ W, int64_t dw, int64_t d,
       i = w * d + s;
       o = t * dw2 + w2;
       Q = d * dw2;
+    } else if (order == WORD_IN_T_W2__OUT_W_S) {
+      i = t * dw2 + w2;
+      o = w * d + s;
+      Q = dw * d;
     } else {
       i = s * dw2 + w2;
       o = w * d + t;

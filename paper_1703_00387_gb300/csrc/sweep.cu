@@ -313,6 +313,98 @@ osmps_status energy_impl(osmps_ctx* ctx, const osmps_mps* m, const osmps_mpo* h,
   return OSMPS_OK;
 }
 
+// dE/dW_k for every site at a fixed state (Eq. mpo: H is linear in each W_k,
+// so dE/dW_k = G_k / <psi|psi> with G_k the contraction of everything else).
+// Right environments R_1..R_L come from one pass from the right; with
+// `every` > 1 only R_L and the R_k with k a multiple of `every` are kept and
+// the others are rebuilt block by block from the checkpoint above them, so
+// about L/every + every environments are alive instead of L. The left
+// environment is carried along (one alive at a time).
+osmps_status energy_grad_impl(osmps_ctx* ctx, const osmps_mps* m, const osmps_mpo* h, double* gW,
+                              int64_t every, int prec, double* E, double* norm_out,
+                              cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  const int64_t L = m->L;
+  const int64_t stride = every > 1 ? std::min<int64_t>(every, L) : 1;
+  auto envsz = [&](int64_t k) { return m->chi[k] * h->w[k] * m->chi[k]; };
+  int64_t maxsz = 1;
+  for (int64_t k = 0; k <= L; ++k) maxsz = std::max(maxsz, envsz(k));
+  double* t0 = (double*)ws_get(ctx, SLOT_SWEEP_ENV, (size_t)maxsz * 8, s, &st);
+  if (!t0) return st;
+  double* t1 = (double*)ws_get(ctx, SLOT_SWEEP_ENV2, (size_t)maxsz * 8, s, &st);
+  if (!t1) return st;
+  // <psi|psi>: left pass with identity operators
+  { k_fill<<<1, 32, 0, s>>>(t0, 1, 1.0); note_launch(); }
+  OSMPS_LAUNCH_CHECK();
+  {
+    double* a = t0;
+    double* b = t1;
+    for (int64_t k = 0; k < L; ++k) {
+      OSMPS_TRY(env_update_impl(ctx, 0, a, m->A[k], h->ident[k], b, m->chi[k], m->d[k],
+                                m->chi[k + 1], 1, 1, prec, s));
+      std::swap(a, b);
+    }
+    double nrm = 0.0;
+    OSMPS_CUDA(cudaMemcpyAsync(&nrm, a, 8, cudaMemcpyDeviceToHost, s));
+    OSMPS_CUDA(cudaStreamSynchronize(s));
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) return set_error(OSMPS_ENAN, "energy gradient: state norm %g", nrm);
+    *norm_out = nrm;
+  }
+  const double inv_norm = 1.0 / *norm_out;
+  // storage: checkpoints (k = L and multiples of stride in [1, L)), then a
+  // segment of stride - 1 environments rebuilt per block
+  auto is_ckpt = [&](int64_t k) { return k == L || (k >= 1 && k % stride == 0); };
+  std::vector<int64_t> off(L + 1, -1);
+  int64_t total = 0;
+  for (int64_t k = 1; k <= L; ++k)
+    if (is_ckpt(k)) { off[k] = total; total += envsz(k); }
+  const int64_t seg_off = total;
+  total += (stride - 1) * maxsz;
+  double* store = (double*)ws_get(ctx, SLOT_GRAD_ENVS, (size_t)std::max<int64_t>(total, 1) * 8, s, &st);
+  if (!store) return st;
+  auto renv = [&](int64_t k, int64_t seg_base) -> double* {
+    if (is_ckpt(k)) return store + off[k];
+    return store + seg_off + (k - seg_base - 1) * maxsz;  // seg_base < k < seg_base + stride
+  };
+  // R_L = 1, then R_k = env(R_{k+1}, A_k, W_k) down to k = 1, keeping checkpoints
+  { k_fill<<<1, 32, 0, s>>>(store + off[L], 1, 1.0); note_launch(); }
+  OSMPS_LAUNCH_CHECK();
+  {
+    const double* cur = store + off[L];
+    for (int64_t k = L - 1; k >= 1; --k) {
+      double* out = is_ckpt(k) ? store + off[k] : (cur == t0 ? t1 : t0);
+      OSMPS_TRY(env_update_impl(ctx, 1, cur, m->A[k], h->W[k], out, m->chi[k], m->d[k],
+                                m->chi[k + 1], h->w[k + 1], h->w[k], prec, s));
+      cur = out;
+    }
+  }
+  // left to right: G_k from L_k and R_{k+1}, then L_{k+1}
+  { k_fill<<<1, 32, 0, s>>>(t0, 1, 1.0); note_launch(); }
+  OSMPS_LAUNCH_CHECK();
+  double* a = t0;
+  double* b = t1;
+  int64_t goff = 0;
+  for (int64_t base = 0; base < L; base += stride) {
+    const int64_t top = std::min(base + stride, L);
+    for (int64_t j = top - 1; j > base; --j)  // rebuild R_j for base < j < top
+      OSMPS_TRY(env_update_impl(ctx, 1, renv(j + 1, base), m->A[j], h->W[j], renv(j, base),
+                                m->chi[j], m->d[j], m->chi[j + 1], h->w[j + 1], h->w[j], prec, s));
+    for (int64_t k = base; k < top; ++k) {
+      OSMPS_TRY(site_energy_grad(ctx, a, m->A[k], renv(k + 1, base), gW + goff, m->chi[k], m->d[k],
+                                 m->chi[k + 1], h->w[k], h->w[k + 1], inv_norm, prec, s));
+      goff += h->w[k] * m->d[k] * m->d[k] * h->w[k + 1];
+      OSMPS_TRY(env_update_impl(ctx, 0, a, m->A[k], h->W[k], b, m->chi[k], m->d[k], m->chi[k + 1],
+                                h->w[k], h->w[k + 1], prec, s));
+      std::swap(a, b);
+    }
+  }
+  double num = 0.0;
+  OSMPS_CUDA(cudaMemcpyAsync(&num, a, 8, cudaMemcpyDeviceToHost, s));
+  OSMPS_CUDA(cudaStreamSynchronize(s));
+  *E = num * inv_norm;
+  return OSMPS_OK;
+}
+
 }  // namespace
 
 }  // namespace osmps
@@ -572,6 +664,48 @@ osmps_status osmps_energy(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo*
   OSMPS_CUDA(cudaSetDevice(ctx->device));
   CtxScope scope_(ctx);
   return energy_impl(ctx, mps, mpo, energy_out, (cudaStream_t)stream);
+}
+
+osmps_status osmps_energy_grad(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo* mpo,
+                               double* gW, int64_t gW_count, int64_t checkpoint_every,
+                               int precision, double* energy_out, double* norm_out, void* stream) {
+  clear_error();
+  if (!ctx || !mps || !mpo || !gW) return set_error(OSMPS_EINVAL, "osmps_energy_grad: null argument");
+  OSMPS_TRY(check_pair(mps, mpo));
+  if (precision != OSMPS_PREC_FP64 && precision != OSMPS_PREC_FP64_EMU)
+    return set_error(OSMPS_EINVAL, "osmps_energy_grad: precision %d (FP64 or FP64_EMU)", precision);
+  if (checkpoint_every < 0) return set_error(OSMPS_EINVAL, "osmps_energy_grad: checkpoint_every < 0");
+  int64_t need = 0;
+  for (int64_t k = 0; k < mpo->L; ++k) {
+    if (mpo->w[k] * mpo->d[k] > 64 || mpo->d[k] * mpo->w[k + 1] > 64)
+      return set_error(OSMPS_EUNSUPPORTED, "osmps_energy_grad: site %lld MPO block too large", (long long)k);
+    need += mpo->w[k] * mpo->d[k] * mpo->d[k] * mpo->w[k + 1];
+  }
+  if (gW_count != need)
+    return set_error(OSMPS_ESHAPE, "osmps_energy_grad: gW holds %lld values, the MPO %lld",
+                     (long long)gW_count, (long long)need);
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
+  double E = 0.0, nrm = 0.0;
+  OSMPS_TRY(energy_grad_impl(ctx, mps, mpo, gW, checkpoint_every, precision, &E, &nrm,
+                             (cudaStream_t)stream));
+  if (energy_out) *energy_out = E;
+  if (norm_out) *norm_out = nrm;
+  return OSMPS_OK;
+}
+
+osmps_status osmps_mpo_set(osmps_mpo* mpo, const double* const* host_W) {
+  clear_error();
+  if (!mpo || !host_W) return set_error(OSMPS_EINVAL, "osmps_mpo_set: null argument");
+  for (int64_t k = 0; k < mpo->L; ++k)
+    if (!host_W[k]) return set_error(OSMPS_EINVAL, "osmps_mpo_set: site %lld is NULL", (long long)k);
+  OSMPS_CUDA(cudaSetDevice(mpo->ctx->device));
+  OSMPS_CUDA(cudaDeviceSynchronize());
+  for (int64_t k = 0; k < mpo->L; ++k) {
+    const size_t bytes = (size_t)mpo->w[k] * mpo->d[k] * mpo->d[k] * mpo->w[k + 1] * 8;
+    OSMPS_CUDA(cudaMemcpy(mpo->W[k], host_W[k], bytes, cudaMemcpyHostToDevice));
+  }
+  return OSMPS_OK;
 }
 
 }  // extern "C"

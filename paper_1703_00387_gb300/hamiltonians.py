@@ -128,3 +128,27 @@ def aklt(L):
             for j in range(3):
                 a.add_bond(k, (X[i] @ X[j]) / 3.0, Y[i] @ Y[j])
     return a.tensors()
+
+
+def xxz_coupling_basis(L, delta=1.0):
+    """The XXZ MPO of ``xxz`` as an affine function of its couplings
+    p = (J_0 .. J_{L-2}, h_0 .. h_{L-1}):  W(p) = W_0 + sum_j p_j B_j.
+
+    Returns (W_0, row_ptr, col, val): W_0 the site tensors at p = 0 and the
+    B_j in compressed sparse rows over the concatenated site tensors (row j
+    lists the flat indices and values of the nonzero entries of B_j)."""
+    n_par = 2 * L - 1
+    W0 = xxz(L, np.zeros(L - 1), delta, np.zeros(L))
+    flat0 = np.concatenate([w.ravel() for w in W0])
+    row_ptr = [0]
+    cols, vals = [], []
+    for j in range(n_par):
+        p = np.zeros(n_par)
+        p[j] = 1.0
+        flat = np.concatenate([w.ravel() for w in xxz(L, p[:L - 1], delta, p[L - 1:])]) - flat0
+        nz = np.flatnonzero(flat)
+        cols.append(nz)
+        vals.append(flat[nz])
+        row_ptr.append(row_ptr[-1] + nz.size)
+    return (W0, np.asarray(row_ptr, dtype=np.int64), np.concatenate(cols).astype(np.int64),
+            np.concatenate(vals))

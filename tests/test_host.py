@@ -83,3 +83,23 @@ def test_seeded_inputs_are_deterministic():
     assert [t.shape[0] for t in a] == inputs.bond_dims(10, 2, 16)[:10]
     batch = inputs.chain_batch(64, seed=0)
     assert len(batch) == 64 and all(16 <= c["L"] <= 128 for c in batch)
+
+
+def test_xxz_coupling_basis_rebuilds_oracle_mpo():
+    """W_0 + sum_j p_j B_j equals the oracle's XXZ MPO at random couplings,
+    and every basis row touches only its own site (J_i: site i, h_i: site i)."""
+    L = 9
+    W0, row_ptr, col, val = hamiltonians.xxz_coupling_basis(L, 0.7)
+    rng = np.random.default_rng(3)
+    p = rng.standard_normal(2 * L - 1)
+    flat = np.concatenate([w.ravel() for w in W0])
+    for j in range(2 * L - 1):
+        sl = slice(row_ptr[j], row_ptr[j + 1])
+        np.add.at(flat, col[sl], p[j] * val[sl])
+    ref = np.concatenate([w.ravel() for w in ompo.xxz_mpo(L, p[:L - 1], 0.7, p[L - 1:])])
+    np.testing.assert_array_equal(flat, ref)
+    ends = np.cumsum([w.size for w in W0])
+    site_of = np.searchsorted(ends, col, side="right")
+    for j in range(2 * L - 1):
+        k = j if j < L - 1 else j - (L - 1)
+        assert set(site_of[row_ptr[j]:row_ptr[j + 1]]) == {k}
