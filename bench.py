@@ -240,6 +240,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     barrier(ws)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()  # a profiler started with capture off records the timed steps only
     ev0.record(stream)
     flops, iters = 0.0, []
     for _ in range(args.steps):
@@ -250,6 +251,7 @@ def run_ours(args, ws, rank, local):
         k += 1
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     barrier(ws)
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = B.osmps_kernel_launches() - launches0
