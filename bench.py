@@ -298,6 +298,8 @@ def run_ours(args, ws, rank, local):
         line["e2e"] = e2e_leg(B, ctx, Wh, prec, args)
         if not args.no_sweep:
             line["sweep_s"] = sweep_leg(B, ctx, mpo, prec)
+        if not args.no_batch:
+            line["batch_sweeps"] = batch_leg(B, args)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"], line["matvec_rel_err"] = cpu_leg(B, ctx, Wh)
     mps.close()
@@ -412,6 +414,45 @@ def sweep_leg(B, ctx, mpo, prec):
                     "and the final float64-accurate energy are timed separately"}
 
 
+def batch_leg(B, args):
+    """64 independent TFI / XXZ chains (L in [16, 128], chi_max in {32, 64, 128,
+    256}, g or Delta in [0.5, 1.5], seeded) swept at once by the native batch
+    scheduler: one worker thread, context and stream each, longest chains
+    first. One untimed sweep of every chain first (allocations, workspace
+    growth), then one timed sweep of every chain; aggregate sweeps per second."""
+    import torch
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+    chains = inputs.chain_batch(64, seed=0)
+    ctxs = [B.Context(torch.cuda.current_device()) for _ in range(args.batch_workers)]
+    mps, mpo, par = [], [], []
+    for i, c in enumerate(chains):
+        W = (hamiltonians.ising(c["L"], 1.0, c["param"]) if c["model"] == "tfi"
+             else hamiltonians.xxz(c["L"], 1.0, c["param"], 0.0))
+        mpo.append(B.MPO(ctxs[0], W))
+        mps.append(B.MPS(ctxs[0], inputs.random_mps(c["L"], D, c["chi_max"], seed=1000 + i),
+                         chi_cap=c["chi_max"]))
+        par.append(B.sweep_params(c["chi_max"], 1, args.precision, lanczos_tol=LANCZOS_TOL,
+                                  lanczos_max_iter=LANCZOS_CAP))
+    B.osmps_sweep_batch(ctxs, mps, mpo, par)  # untimed
+    torch.cuda.synchronize()
+    launches0 = B.osmps_kernel_launches()
+    t0 = time.perf_counter()
+    stats, _ = B.osmps_sweep_batch(ctxs, mps, mpo, par)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    launches = B.osmps_kernel_launches() - launches0
+    for x in mps + mpo + ctxs:
+        x.close()
+    steps = sum(s["steps"] for s in stats)
+    return {"value": len(chains) / dt, "unit": "sweeps/s", "chains": len(chains),
+            "sweeps_per_chain": 1, "seconds": dt, "workers": args.batch_workers,
+            "precision": args.precision, "two_site_steps": steps,
+            "lanczos_iters": sum(s["lanczos_iters"] for s in stats), "gpu_launches": launches,
+            "workload": "64 chains from seed 0: TFI or XXZ (p = 1/2), L ~ U{16..128}, "
+                        "chi_max ~ U{32, 64, 128, 256}, g or Delta ~ U[0.5, 1.5]; "
+                        "random seeded MPS at chi_max"}
+
+
 def cpu_leg(B, ctx, Wh):
     import torch
     from oracle import dmrg as od
@@ -445,6 +486,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-workers", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiler runs)")
     args = ap.parse_args()

@@ -311,6 +311,24 @@ osmps_status osmps_sweep(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo,
 osmps_status osmps_energy(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo* mpo,
                           double* energy_out, void* stream);
 
+/* Sweeps of many independent chains at once (the paper's data parallelism
+ * over independent simulations, appendix "Convenient features", MPI item:
+ * jobs are handed to workers one by one, largest systems first).
+ * n_workers host threads each own ctxs[w] (distinct contexts on one device)
+ * and a stream they create; they take chains in decreasing order of
+ * estimated cost (sum over bonds of chi^3 times the sweep count) and run
+ * osmps_sweep(ctxs[w], mps[i], mpo[i], &params[i], &stats[i], stream) on
+ * each. Chains must not share an MPS handle (EINVAL); an MPO may be shared.
+ * stats (n_chains entries, may be NULL) and chain_status (n_chains entries,
+ * may be NULL) are HOST arrays; chain_status[i] is the chain's own status,
+ * or -1 for a chain that was not started because another one failed.
+ * Returns the first failure (message names the chain). Blocks until all
+ * workers are done.                                                        */
+osmps_status osmps_sweep_batch(osmps_ctx* const* ctxs, int n_workers, osmps_mps* const* mps,
+                               const osmps_mpo* const* mpo, const osmps_sweep_params* params,
+                               int64_t n_chains, osmps_sweep_stats* stats,
+                               osmps_status* chain_status);
+
 /* ------------------------------------------------------------------------
  * Gradients (differentiation of the Sec. 3.4 operators; the paper has no
  * backward pass). Every quantity below is linear in the tensor it is

@@ -90,6 +90,9 @@ _SIGS = {
     "osmps_heff_backward": (_c.c_int, [_vp] + [_vp] * 9 + [_i64] * 7 + [_c.c_int, _vp]),
     "osmps_energy_grad": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _c.c_int, _dp, _dp, _vp]),
     "osmps_coupling_grad": (_c.c_int, [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
+    "osmps_sweep_batch": (_c.c_int, [_c.POINTER(_vp), _c.c_int, _c.POINTER(_vp), _c.POINTER(_vp),
+                                     _c.POINTER(SweepParams), _i64, _c.POINTER(SweepStats),
+                                     _c.POINTER(_c.c_int)]),
 }
 
 
@@ -428,3 +431,25 @@ def osmps_coupling_grad(ctx, row_ptr, col, val, gW, g_par, stream=None):
                                      _dev(gW, "gW"), gW.numel(), _dev(g_par, "g_par"),
                                      _stream(stream)))
     return g_par
+
+
+def osmps_sweep_batch(ctxs, mps_list, mpo_list, params_list):
+    """Sweeps of many chains at once: one host thread, context and stream per
+    entry of ctxs. Returns (list of per-chain stats dicts, list of statuses);
+    raises on the first failure."""
+    n = len(mps_list)
+    assert len(mpo_list) == n and len(params_list) == n
+    cs = (_vp * len(ctxs))(*[c.ptr for c in ctxs])
+    ms = (_vp * n)(*[m.ptr for m in mps_list])
+    hs = (_vp * n)(*[h.ptr for h in mpo_list])
+    ps = (SweepParams * n)(*params_list)
+    st = (SweepStats * n)()
+    cst = (_c.c_int * n)()
+    status = lib().osmps_sweep_batch(cs, len(ctxs), ms, hs, ps, n, st, cst)
+    stats = [{f: getattr(x, f) for f, _ in SweepStats._fields_ if not f.startswith("step_")}
+             for x in st]
+    if status != 0:
+        err = OsmpsError(status, lib().osmps_last_error().decode(errors="replace"))
+        err.chain_status = list(cst)
+        raise err
+    return stats, list(cst)

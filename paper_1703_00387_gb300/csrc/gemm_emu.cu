@@ -402,12 +402,10 @@ osmps_status gemm_emu(osmps_ctx* ctx, const SplitView& a, const SplitView& b, in
   CUtensorMap ma, mb;
   OSMPS_TRY(tc_make_map(&ma, sa, TC_BF16, M, SLICES * Kp, EBM));
   OSMPS_TRY(tc_make_map(&mb, sb, TC_BF16, N, SLICES * Kp, EBN));
-  static bool configured = false;
-  if (!configured) {
-    OSMPS_CUDA(cudaFuncSetAttribute(k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)E_SMEM));
-    configured = true;
-  }
+  // thread-safe one-time setup (function-local static initialisation)
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(k_gemm_emu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E_SMEM);
+  OSMPS_CUDA(configured);
   static const PairList pl = make_pairs();
   const int tiles_n = (int)cdiv(N, EBN);
   const int n_tiles = tiles_n * (int)cdiv(M, EBM);

@@ -276,12 +276,10 @@ namespace {
 template <int KIND, int OUT>
 osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g, int* err,
                     int sm_count, cudaStream_t stream) {
-  static bool configured = false;
-  if (!configured) {
-    OSMPS_CUDA(cudaFuncSetAttribute(k_gemm_tc<KIND, OUT>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    configured = true;
-  }
+  // thread-safe one-time setup (function-local static initialisation)
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      k_gemm_tc<KIND, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  OSMPS_CUDA(configured);
   const int kelem = KSLICE_BYTES / (int)tc_elem_bytes(KIND);
   const int nkb = (int)(g.Kp / kelem);
   const int tiles_n = (int)cdiv(g.N, BN);

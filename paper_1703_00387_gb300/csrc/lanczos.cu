@@ -21,7 +21,7 @@ namespace {
 
 constexpr int MAXIT = 512;
 constexpr int DOT_THREADS = 256;
-constexpr int DOT_GROUP = 16;
+constexpr int DOT_GROUP = 8;
 constexpr int DOT_MAX_BLOCKS = 1024;
 
 // scalar layout in SLOT_LZ_SCAL (doubles)
@@ -38,46 +38,69 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// part[i * nb + b] = sum over block b's elements of V[i][e] * w[e], i < nv.
-// Each thread takes two consecutive elements (16-byte loads) and 16 rows at a time.
-__global__ void __launch_bounds__(DOT_THREADS) k_multidot(const double* __restrict__ V, int64_t ld,
+// Block-partial dot products of G consecutive Krylov vectors with w:
+// part[(g0 + v) * nb + b] = sum over block b's elements of V[g0 + v][e] w[e].
+// The float64 pipe is the narrowest unit on this GPU, so exactly one fused
+// multiply-add is issued per (vector, element): the group size is a template
+// parameter (no predicated-off FMAs), and each thread covers many elements so
+// the warp reductions stay a small fraction of the float64 work.
+template <int G>
+__device__ __forceinline__ void multidot_group(const double* __restrict__ V, int64_t ld, int g0,
+                                               const double* __restrict__ w, int64_t n,
+                                               double* __restrict__ part,
+                                               double (*sh)[DOT_GROUP]) {
+  const int nb = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n2 = n >> 1;  // element pairs (16-byte loads); odd tail below
+  const double2* V0 = reinterpret_cast<const double2*>(V + (int64_t)g0 * ld);
+  const int64_t ld2 = ld >> 1;  // ld is even
+  double acc[G];
+#pragma unroll
+  for (int v = 0; v < G; ++v) acc[v] = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * DOT_THREADS + threadIdx.x; e < n2;
+       e += (int64_t)nb * DOT_THREADS) {
+    const double2 wv = reinterpret_cast<const double2*>(w)[e];
+    double2 x[G];
+#pragma unroll
+    for (int v = 0; v < G; ++v) x[v] = V0[v * ld2 + e];
+#pragma unroll
+    for (int v = 0; v < G; ++v) acc[v] = fma(x[v].x, wv.x, fma(x[v].y, wv.y, acc[v]));
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+    for (int v = 0; v < G; ++v) acc[v] = fma(V[(int64_t)(g0 + v) * ld + n - 1], w[n - 1], acc[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < G; ++v) {
+    const double t = warp_sum(acc[v]);
+    if (lane == 0) sh[warp][v] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < G) {
+    double t = 0.0;
+    for (int k = 0; k < DOT_THREADS / 32; ++k) t += sh[k][threadIdx.x];
+    part[(int64_t)(g0 + threadIdx.x) * nb + blockIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// part[i * nb + b] = sum over block b's elements of V[i][e] * w[e], i < nv:
+// groups of DOT_GROUP vectors, then one group of the remainder.
+__global__ void __launch_bounds__(DOT_THREADS, 3) k_multidot(const double* __restrict__ V, int64_t ld,
                                                           int nv, const double* __restrict__ w,
                                                           int64_t n, double* __restrict__ part) {
   __shared__ double sh[DOT_THREADS / 32][DOT_GROUP];
-  const int nb = gridDim.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n2 = n >> 1;  // pairs (n is even for every H_eff vector with d1 d2 >= 2; tail below)
-  for (int g0 = 0; g0 < nv; g0 += DOT_GROUP) {
-    double acc[DOT_GROUP];
-#pragma unroll
-    for (int v = 0; v < DOT_GROUP; ++v) acc[v] = 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * DOT_THREADS + threadIdx.x; e < n2;
-         e += (int64_t)nb * DOT_THREADS) {
-      const double2 wv = reinterpret_cast<const double2*>(w)[e];
-#pragma unroll
-      for (int v = 0; v < DOT_GROUP; ++v)
-        if (g0 + v < nv) {
-          const double2 x = reinterpret_cast<const double2*>(V + (int64_t)(g0 + v) * ld)[e];
-          acc[v] = fma(x.x, wv.x, fma(x.y, wv.y, acc[v]));
-        }
-    }
-    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-#pragma unroll
-      for (int v = 0; v < DOT_GROUP; ++v)
-        if (g0 + v < nv) acc[v] = fma(V[(int64_t)(g0 + v) * ld + n - 1], w[n - 1], acc[v]);
-    }
-#pragma unroll
-    for (int v = 0; v < DOT_GROUP; ++v) {
-      double t = warp_sum(acc[v]);
-      if (lane == 0) sh[warp][v] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < DOT_GROUP && g0 + (int)threadIdx.x < nv) {
-      double t = 0.0;
-      for (int k = 0; k < DOT_THREADS / 32; ++k) t += sh[k][threadIdx.x];
-      part[(int64_t)(g0 + threadIdx.x) * nb + blockIdx.x] = t;
-    }
-    __syncthreads();
+  int g0 = 0;
+  for (; g0 + DOT_GROUP <= nv; g0 += DOT_GROUP) multidot_group<DOT_GROUP>(V, ld, g0, w, n, part, sh);
+  switch (nv - g0) {
+    case 1: multidot_group<1>(V, ld, g0, w, n, part, sh); break;
+    case 2: multidot_group<2>(V, ld, g0, w, n, part, sh); break;
+    case 3: multidot_group<3>(V, ld, g0, w, n, part, sh); break;
+    case 4: multidot_group<4>(V, ld, g0, w, n, part, sh); break;
+    case 5: multidot_group<5>(V, ld, g0, w, n, part, sh); break;
+    case 6: multidot_group<6>(V, ld, g0, w, n, part, sh); break;
+    case 7: multidot_group<7>(V, ld, g0, w, n, part, sh); break;
+    default: break;
   }
 }
 
@@ -255,10 +278,14 @@ __global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int j) 
   }
 }
 
-int dot_blocks(int64_t n) {
-  int64_t b = cdiv(n, DOT_THREADS * 8);
-  if (b < 1) b = 1;
+// Blocks for k_multidot: at least 16 element pairs per thread, and no more
+// blocks than fit on the GPU in one wave (3 per SM at its register use).
+int dot_blocks(int64_t n, int sm_count) {
+  int64_t b = cdiv(n, DOT_THREADS * 32);
+  const int64_t wave = 3 * (int64_t)(sm_count > 0 ? sm_count : 1);
+  if (b > wave) b = wave;
   if (b > DOT_MAX_BLOCKS) b = DOT_MAX_BLOCKS;
+  if (b < 1) b = 1;
   return (int)b;
 }
 
@@ -273,7 +300,7 @@ int ew_blocks(int64_t n) {
 // an even stride ld, 16-byte aligned like w), coefficients to coef.
 osmps_status project(osmps_ctx* ctx, const double* V, int64_t ld, int64_t n, int nv, double* w,
                      double* part, double* coef, cudaStream_t s) {
-  const int nb = dot_blocks(n);
+  const int nb = dot_blocks(n, ctx->sm_count);
   { k_multidot<<<nb, DOT_THREADS, 0, s>>>(V, ld, nv, w, n, part); note_launch(); }
   { k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef); note_launch(); }
   { k_combine<<<ew_blocks(n), 256, 0, s>>>(V, ld, nv, coef, w, n, 0); note_launch(); }

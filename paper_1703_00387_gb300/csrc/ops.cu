@@ -37,6 +37,24 @@ __device__ __forceinline__ void split_store(void* dst, int64_t off_hi, int64_t K
   }
 }
 
+// The same split for a float32 value with float32 arithmetic only (the
+// float64 pipe is narrow on this GPU). x - hi is exact in float32 (hi keeps
+// the leading bits of x), so the result equals split_store's bit for bit.
+template <int KIND>
+__device__ __forceinline__ void split_store_f32(void* dst, int64_t off_hi, int64_t Kp, float x) {
+  if (KIND == TC_BF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    reinterpret_cast<__nv_bfloat16*>(dst)[off_hi] = h;
+    reinterpret_cast<__nv_bfloat16*>(dst)[off_hi + Kp] = l;
+  } else {
+    const uint32_t h = to_tf32(x);
+    const uint32_t l = to_tf32(x - __uint_as_float(h));
+    reinterpret_cast<uint32_t*>(dst)[off_hi] = h;
+    reinterpret_cast<uint32_t*>(dst)[off_hi + Kp] = l;
+  }
+}
+
 __device__ __forceinline__ double load_src(const void* src, bool f32, int64_t off) {
   return f32 ? (double)reinterpret_cast<const float*>(src)[off]
              : reinterpret_cast<const double*>(src)[off];
@@ -122,7 +140,7 @@ __global__ void k_fiber(Fiber f, const double* __restrict__ Mat, const T* __rest
           out[off] = acc[o];
         } else {
           const int64_t row = off / Kcols, col = off - row * Kcols;
-          split_store<MODE == 1 ? TC_BF16 : TC_TF32>(sdst, row * 2 * Kp + col, Kp, (double)acc[o]);
+          split_store_f32<MODE == 1 ? TC_BF16 : TC_TF32>(sdst, row * 2 * Kp + col, Kp, (float)acc[o]);
         }
       }
     }
@@ -170,7 +188,7 @@ __global__ void k_zero_pad(void* dst, int64_t rows, int64_t Kcols, int64_t Kp) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / w, k = Kcols + (e - r * w);
-    split_store<KIND>(dst, r * 2 * Kp + k, Kp, 0.0);
+    split_store_f32<KIND>(dst, r * 2 * Kp + k, Kp, 0.0f);
   }
 }
 
@@ -259,7 +277,7 @@ __global__ void __launch_bounds__(256) k_fused_wsteps(const float* __restrict__ 
 #pragma unroll
             for (int s2 = 0; s2 < D; ++s2)
               acc = fmaf(m2[(w1 * D + s2) * Q2 + t2 * WR + w2], mid[t1][w1][s2], acc);
-          split_store<KIND>(dst, row * 2 * Kp + (int64_t)w2 * chi_r + c, Kp, (double)acc);
+          split_store_f32<KIND>(dst, row * 2 * Kp + (int64_t)w2 * chi_r + c, Kp, acc);
         }
       }
   }
