@@ -300,6 +300,7 @@ def run_ours(args, ws, rank, local):
             line["sweep_s"] = sweep_leg(B, ctx, mpo, prec)
         if not args.no_batch:
             line["batch_sweeps"] = batch_leg(B, args)
+        line["u1_heff"] = u1_leg(B, ctx, args)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"], line["matvec_rel_err"] = cpu_leg(B, ctx, Wh)
     mps.close()
@@ -451,6 +452,55 @@ def batch_leg(B, args):
             "workload": "64 chains from seed 0: TFI or XXZ (p = 1/2), L ~ U{16..128}, "
                         "chi_max ~ U{32, 64, 128, 256}, g or Delta ~ U[0.5, 1.5]; "
                         "random seeded MPS at chi_max"}
+
+
+def u1_leg(B, ctx, args):
+    """Config 3: U(1) block-sparse H_eff.theta of the Bose-Hubbard chain (L=64,
+    N=64, n <= 4, d=5, w=4, chi=512 per bond, sector sizes from the Gaussian
+    profile around N k / L at bonds 31 and 33), each GEMM stage one grouped
+    tcgen05 launch over all sector blocks. Inputs resident; CUDA events over
+    `reps` products after 3 warm-up products."""
+    import torch
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+    from paper_1703_00387_gb300 import u1 as pu1
+    dev = torch.device("cuda", torch.cuda.current_device())
+    W = hamiltonians.bose_hubbard(64, 1.0, 4.0, 4)
+    q = pu1.channel_charges(W)
+    left = inputs.u1_sector_profile(31.0, total=512, width=8.0)
+    right = inputs.u1_sector_profile(33.0, total=512, width=8.0)
+    out = {}
+    for prec in ("tf32x3", "bf16x3"):
+        op = pu1.U1Operator(ctx, left, right, 5, 5, W[31], W[32], q[31], q[33])
+        pl = op.plan
+        t = [torch.from_numpy(inputs.random_dense((n,), seed)).to(dev)
+             for n, seed in ((pl.n_L, 1), (pl.n_R, 2), (pl.n_theta, 3))]
+        W1, W2 = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (W[31], W[32]))
+        y = torch.empty_like(t[2])
+        for _ in range(3):
+            B.osmps_heff_apply_u1(ctx, pl, t[0], W1, W2, t[1], t[2], y, precision=prec)
+        stream = torch.cuda.current_stream()
+        reps = 20
+        B.osmps_profile_enable(ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            B.osmps_heff_apply_u1(ctx, pl, t[0], W1, W2, t[1], t[2], y, precision=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        prof = B.osmps_profile_read(ctx, "gemm_tc")
+        B.osmps_profile_enable(ctx, False)
+        dense = 2.0 * 25 * 512 * 512 * (4 * 512 + 4 * 512)
+        out[prec] = {"ms_per_product": ms, "block_gemm_tflops": pl.flops / (ms / 1e3) / 1e12,
+                     "block_gemm_gflop": pl.flops / 1e9, "dense_equivalent_gflop": dense / 1e9,
+                     "grouped_gemm_share": prof["ms"] / (ms * reps) if ms > 0 else None,
+                     "grouped_gemm_launches": prof["launches"],
+                     "grouped_gemm_issued_tflops": (prof["tensor_flops"] / (prof["ms"] / 1e3) / 1e12
+                                                   if prof["ms"] > 0 else None),
+                     "n_theta": pl.n_theta, "n_theta_dense": 512 * 25 * 512}
+        op.close()
+    return {"workload": "Bose-Hubbard J=1 U=4, L=64, N=64, n<=4 (d=5), w=4, chi=512 per bond "
+                        "(13 sectors each), two-site H_eff.theta at sites 31,32", **out}
 
 
 def cpu_leg(B, ctx, Wh):

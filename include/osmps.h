@@ -330,6 +330,50 @@ osmps_status osmps_sweep_batch(osmps_ctx* const* ctxs, int n_workers, osmps_mps*
                                osmps_status* chain_status);
 
 /* ------------------------------------------------------------------------
+ * U(1)-symmetric H_eff . theta (Sec. 3.4 with a conserved particle number:
+ * block-sparse tensors; every sector block of a GEMM stage in one grouped
+ * tcgen05 launch).
+ * Every bond index carries a charge; a local state s carries charge s; MPO
+ * channel w carries q_w. Allowed entries:
+ *   theta[a,s1,s2,c], y[...]: q(a) + s1 + s2 = q(c)
+ *   L[a2,w,a]: q(a2) = q(a) + q_wl[w];   R[c2,w,c]: q(c2) = q(c) + q_wr[w]
+ * Packed format of theta, y, L, R: their allowed entries in C order of the
+ * dense tensor (numpy: dense[mask]). A bond is given as its sectors in
+ * index order: charge and size of each (charges distinct, sizes >= 1).
+ * W1 (wl, d1, d1, wm) and W2 (wm, d2, d2, wr) are dense; the result is the
+ * dense product restricted to the allowed entries of y.                   */
+typedef struct {
+  int64_t n_left;            /* sectors of the left bond (index of a, a2)          */
+  const int64_t* q_left;     /* their charges (HOST array, n_left)                  */
+  const int64_t* chi_left;   /* their sizes   (HOST array, n_left)                  */
+  int64_t n_right;           /* sectors of the right bond (index of c, c2)         */
+  const int64_t* q_right;
+  const int64_t* chi_right;
+  int64_t d1, d2;            /* local dimensions (state s has charge s)            */
+  int64_t wl, wm, wr;        /* MPO bond dimensions                                 */
+  const int64_t* q_wl;       /* charge of each left MPO channel (HOST, wl)         */
+  const int64_t* q_wr;       /* charge of each right MPO channel (HOST, wr)        */
+} osmps_u1_desc;
+typedef struct osmps_u1_heff osmps_u1_heff;
+
+/* Build the block plan for one (left bond, right bond, MPO) structure: sector
+ * bookkeeping on the host, index tables and operand buffers on the device
+ * (owned by the handle). EINVAL for repeated charges, ESHAPE for bad sizes. */
+osmps_status osmps_u1_heff_create(osmps_ctx* ctx, const osmps_u1_desc* desc, osmps_u1_heff** out);
+osmps_status osmps_u1_heff_destroy(osmps_u1_heff* plan);
+/* Packed lengths of theta (= y), L and R, and the GEMM FLOPs of one product
+ * (sum over the sector blocks of 2 M N K, both GEMM stages). Host outputs,
+ * any may be NULL.                                                          */
+osmps_status osmps_u1_heff_sizes(const osmps_u1_heff* plan, int64_t* n_theta, int64_t* n_L,
+                                 int64_t* n_R, double* flops);
+/* y = H_eff theta on packed device arrays (layouts above). precision:
+ * OSMPS_PREC_BF16X3 or OSMPS_PREC_TF32X3 (others EUNSUPPORTED). Calls with
+ * one plan must not overlap on the GPU (its buffers are reused).           */
+osmps_status osmps_heff_apply_u1(osmps_ctx* ctx, osmps_u1_heff* plan, const double* L,
+                                 const double* W1, const double* W2, const double* R,
+                                 const double* theta, double* y, int precision, void* stream);
+
+/* ------------------------------------------------------------------------
  * Gradients (differentiation of the Sec. 3.4 operators; the paper has no
  * backward pass). Every quantity below is linear in the tensor it is
  * differentiated by, so each gradient is a full contraction of the incoming

@@ -52,6 +52,13 @@ class StepStats(_c.Structure):
                 ("converged", _c.c_int)]
 
 
+class U1Desc(_c.Structure):
+    _fields_ = [("n_left", _i64), ("q_left", _c.POINTER(_i64)), ("chi_left", _c.POINTER(_i64)),
+                ("n_right", _i64), ("q_right", _c.POINTER(_i64)), ("chi_right", _c.POINTER(_i64)),
+                ("d1", _i64), ("d2", _i64), ("wl", _i64), ("wm", _i64), ("wr", _i64),
+                ("q_wl", _c.POINTER(_i64)), ("q_wr", _c.POINTER(_i64))]
+
+
 _LIB = None
 
 _SIGS = {
@@ -90,6 +97,10 @@ _SIGS = {
     "osmps_heff_backward": (_c.c_int, [_vp] + [_vp] * 9 + [_i64] * 7 + [_c.c_int, _vp]),
     "osmps_energy_grad": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _c.c_int, _dp, _dp, _vp]),
     "osmps_coupling_grad": (_c.c_int, [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp]),
+    "osmps_u1_heff_create": (_c.c_int, [_vp, _c.POINTER(U1Desc), _c.POINTER(_vp)]),
+    "osmps_u1_heff_destroy": (_c.c_int, [_vp]),
+    "osmps_u1_heff_sizes": (_c.c_int, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64), _dp]),
+    "osmps_heff_apply_u1": (_c.c_int, [_vp, _vp] + [_vp] * 6 + [_c.c_int, _vp]),
     "osmps_sweep_batch": (_c.c_int, [_c.POINTER(_vp), _c.c_int, _c.POINTER(_vp), _c.POINTER(_vp),
                                      _c.POINTER(SweepParams), _i64, _c.POINTER(SweepStats),
                                      _c.POINTER(_c.c_int)]),
@@ -453,3 +464,50 @@ def osmps_sweep_batch(ctxs, mps_list, mpo_list, params_list):
         err.chain_status = list(cst)
         raise err
     return stats, list(cst)
+
+
+def _i64arr(x):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.int64))
+    return a, a.ctypes.data_as(_c.POINTER(_i64))
+
+
+class U1Heff:
+    """Block plan of the U(1)-symmetric H_eff (osmps_u1_heff): sectors of the
+    left and right bond (charges and sizes, in index order), local dims and
+    the charges of the MPO channels on the two outer MPO bonds."""
+
+    def __init__(self, ctx, q_left, chi_left, q_right, chi_right, d1, d2, wl, wm, wr, q_wl, q_wr):
+        self.ctx = ctx
+        keep = [_i64arr(v) for v in (q_left, chi_left, q_right, chi_right, q_wl, q_wr)]
+        self._keep = keep
+        desc = U1Desc(len(keep[0][0]), keep[0][1], keep[1][1], len(keep[2][0]), keep[2][1],
+                      keep[3][1], int(d1), int(d2), int(wl), int(wm), int(wr), keep[4][1], keep[5][1])
+        self.ptr = _vp()
+        _check(lib().osmps_u1_heff_create(ctx.ptr, _c.byref(desc), _c.byref(self.ptr)))
+        nt, nl, nr, fl = _i64(), _i64(), _i64(), _c.c_double()
+        _check(lib().osmps_u1_heff_sizes(self.ptr, _c.byref(nt), _c.byref(nl), _c.byref(nr),
+                                         _c.byref(fl)))
+        self.n_theta, self.n_L, self.n_R, self.flops = nt.value, nl.value, nr.value, fl.value
+
+    def close(self):
+        if self.ptr:
+            lib().osmps_u1_heff_destroy(self.ptr)
+            self.ptr = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def osmps_heff_apply_u1(ctx, plan, L, W1, W2, R, theta, y, precision="bf16x3", stream=None):
+    """y = H_eff theta on packed block-sparse vectors (see U1Heff)."""
+    for t, n, name in ((L, plan.n_L, "L"), (R, plan.n_R, "R"), (theta, plan.n_theta, "theta"),
+                       (y, plan.n_theta, "y")):
+        if t.numel() != n:
+            raise ValueError(f"{name} has {t.numel()} entries, the plan expects {n}")
+    _check(lib().osmps_heff_apply_u1(ctx.ptr, plan.ptr, _dev(L, "L"), _dev(W1, "W1"), _dev(W2, "W2"),
+                                     _dev(R, "R"), _dev(theta, "theta"), _dev(y, "y"),
+                                     _prec(precision), _stream(stream)))
+    return y

@@ -200,6 +200,37 @@ struct GemmTc {
 osmps_status gemm_tc(osmps_ctx* ctx, const GemmTc& g, cudaStream_t stream);
 inline size_t tc_elem_bytes(int kind) { return kind == TC_BF16 ? 2 : 4; }
 
+// Grouped split-precision GEMM: many independent problems in one persistent
+// launch. Problem p computes
+//   C[c_off + m ldc + n] = sum_{k < 64 nkb-ish} A[a_row0 + m][k] B[b_row0 + n][k]
+// (the three split products) for m < M, n < N. A and B are packed split
+// operands whose rows hold [hi(0..Kpl) | lo(0..Kpl)]; problem p reads the
+// first nkb K slices of its rows, which must be zero beyond its own K.
+struct GroupProblem {
+  int a_row0, b_row0;  // first rows of the problem in the packed A / B operands
+  int M, N;            // output rows / columns
+  int nkb;             // K slices (128 bytes of K each) of the problem
+  int tile0, tiles_n;  // first global tile, N tiles (filled by group_tiles)
+  int pad;
+  int64_t c_off, ldc;  // element offset of the problem's C[0,0], row stride
+};
+// Fills tile0 / tiles_n (128 x 256 tiles) and returns the total tile count.
+int64_t group_tiles(GroupProblem* probs, int n_prob);
+struct GemmTcGrouped {
+  int kind = TC_BF16, out = TC_OUT_F32;
+  const void* A = nullptr;  // packed operand rows, 2 * Kpl elements each
+  int64_t rowsA = 0;
+  const void* B = nullptr;
+  int64_t rowsB = 0;
+  int64_t Kpl = 0;          // lo-half offset (multiple of 64)
+  void* C = nullptr;
+  const GroupProblem* probs = nullptr;  // DEVICE table, tile0 ascending
+  int n_prob = 0;
+  int64_t n_tiles = 0;
+  double logical_flops = 0.0;  // for profiling records
+};
+osmps_status gemm_tc_grouped(osmps_ctx* ctx, const GemmTcGrouped& g, cudaStream_t stream);
+
 // Split a float64 (or float32) matrix view into the hi|lo operand layout.
 // Source element (row r, col k) with r = r0*n1 + r1 (r1 < n1) lives at
 // src[r0*s0 + r1*s1 + k*sk]. Destination row r holds hi at [0,K), zeros at

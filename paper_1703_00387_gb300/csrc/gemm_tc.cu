@@ -85,11 +85,57 @@ __device__ __forceinline__ void store_row(void* C, int64_t row, int64_t col0, in
 // registers with round-to-nearest. This keeps the tensor core's own
 // accumulation to 16 additions per partial sum, so its truncating
 // accumulator does not build a bias over long K.
+// One output tile: where its operand rows start, its K-slice count and where
+// its results go. Plain GEMM: one problem. Grouped GEMM: tile -> problem by
+// binary search over the problems' first tiles (GroupProblem table).
+struct TileJob {
+  int a_row, b_row, nkb;
+  int64_t row0, col0, M, N, ldc;
+  void* C;
+};
+
+template <int OUT>
+__device__ __forceinline__ TileJob tile_job(int tile, void* C, int64_t M, int64_t N, int64_t ldc,
+                                            int nkb, int tiles_n,
+                                            const GroupProblem* __restrict__ probs, int n_prob) {
+  TileJob j;
+  if (probs == nullptr) {
+    j.row0 = (int64_t)(tile / tiles_n) * BM;
+    j.col0 = (int64_t)(tile % tiles_n) * BN;
+    j.a_row = (int)j.row0;
+    j.b_row = (int)j.col0;
+    j.nkb = nkb;
+    j.M = M;
+    j.N = N;
+    j.ldc = ldc;
+    j.C = C;
+    return j;
+  }
+  int lo = 0, hi = n_prob - 1;  // last problem with tile0 <= tile
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+  }
+  const GroupProblem& p = probs[lo];
+  const int local = tile - p.tile0;
+  j.row0 = (int64_t)(local / p.tiles_n) * BM;
+  j.col0 = (int64_t)(local % p.tiles_n) * BN;
+  j.a_row = p.a_row0 + (int)j.row0;
+  j.b_row = p.b_row0 + (int)j.col0;
+  j.nkb = p.nkb;
+  j.M = p.M;
+  j.N = p.N;
+  j.ldc = p.ldc;
+  j.C = reinterpret_cast<uint8_t*>(C) + p.c_off * (OUT == TC_OUT_F32 ? 4 : 8);
+  return j;
+}
+
 template <int KIND, int OUT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               void* __restrict__ C, int64_t M, int64_t N, int64_t ldc, int nkb, int kelem,
-              int Kp, int tiles_n, int n_tiles, int* __restrict__ err) {
+              int Kp, int tiles_n, int n_tiles, int* __restrict__ err,
+              const GroupProblem* __restrict__ probs, int n_prob) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -123,8 +169,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int total = 3 * nkb;                    // K slices over the three products
-  const int nchunk = (total + CHUNK - 1) / CHUNK;
 
   if (warp == 0 && lane == 0) {
     // Producer. Slice it of a tile covers K slice kb = it / 3 of product
@@ -133,7 +177,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t issued = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      const TileJob job = tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob);
+      const int total = 3 * job.nkb;  // K slices over the three products
       for (int it = 0; it < total; ++it, ++g) {
         const int s = g % STAGES;
         const uint32_t ph = (g / STAGES) & 1u;
@@ -143,8 +188,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         const int kb = it / 3, p = it % 3;
         mbar_expect_tx(&full[s], STAGE_BYTES);
-        tma_load_2d(sA + s * A_STAGE, &tmA, kb * kelem + (p == 2 ? Kp : 0), m0, &full[s]);
-        tma_load_2d(sB + s * B_STAGE, &tmB, kb * kelem + (p == 1 ? Kp : 0), n0, &full[s]);
+        tma_load_2d(sA + s * A_STAGE, &tmA, kb * kelem + (p == 2 ? Kp : 0), job.a_row, &full[s]);
+        tma_load_2d(sB + s * B_STAGE, &tmB, kb * kelem + (p == 1 ? Kp : 0), job.b_row, &full[s]);
         issued = g + 1;
       }
     }
@@ -157,6 +202,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t g = 0, gc = 0;  // slices / chunks consumed by this CTA
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int total = 3 * tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob).nkb;
       for (int it = 0; it < total && ok; ++it, ++g) {
         const bool first = (it % CHUNK) == 0;
         const uint32_t buf = gc & 1u;
@@ -195,7 +241,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t gc = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      const int nchunk =
+          (3 * tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob).nkb + CHUNK - 1) / CHUNK;
       float acc[EPI_COLS];
 #pragma unroll
       for (int j = 0; j < EPI_COLS; ++j) acc[j] = 0.0f;
@@ -219,8 +266,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) mbar_arrive(&tempty[buf]);
       }
       if (!ok) break;
-      const int64_t row = (int64_t)m0 + q * 32 + lane;
-      if (row < M) store_row<OUT>(C, row, (int64_t)n0 + part * EPI_COLS, N, ldc, acc);
+      // decoded again after the K loop so its fields are not live during it
+      const TileJob job = tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob);
+      const int64_t row = job.row0 + q * 32 + lane;
+      if (row < job.M) store_row<OUT>(job.C, row, job.col0 + part * EPI_COLS, job.N, job.ldc, acc);
     }
     if (!ok) atomicOr(err, 1);
   }
@@ -288,7 +337,7 @@ osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g,
   const int ph = prof_begin(stream);
   { k_gemm_tc<KIND, OUT><<<grid, THREADS, SMEM_BYTES, stream>>>(a, b, g.C, g.M, g.N, g.ldc, nkb,
                                                              kelem, (int)g.Kp, tiles_n, n_tiles,
-                                                             err); note_launch(); }
+                                                             err, nullptr, 0); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   const double logical = 2.0 * (double)g.M * (double)g.N * (double)(g.K > 0 ? g.K : g.Kp);
   prof_end(ph, stream, OSMPS_KERNEL_GEMM_TC, logical, 3.0 * logical);
@@ -296,6 +345,51 @@ osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g,
 }
 
 }  // namespace
+
+int64_t group_tiles(GroupProblem* probs, int n_prob) {
+  int64_t t = 0;
+  for (int i = 0; i < n_prob; ++i) {
+    probs[i].tiles_n = (int)cdiv(probs[i].N, BN);
+    probs[i].tile0 = (int)t;
+    t += (int64_t)probs[i].tiles_n * cdiv(probs[i].M, BM);
+  }
+  return t;
+}
+
+osmps_status gemm_tc_grouped(osmps_ctx* ctx, const GemmTcGrouped& g, cudaStream_t stream) {
+  if (g.n_prob <= 0 || g.n_tiles <= 0) return OSMPS_OK;
+  if (g.Kpl <= 0 || g.Kpl % 64 != 0 || 2 * g.Kpl > (int64_t)1 << 31 || g.n_tiles > ((int64_t)1 << 31) ||
+      g.rowsA > ((int64_t)1 << 31) || g.rowsB > ((int64_t)1 << 31))
+    return set_error(OSMPS_ESHAPE, "gemm_tc_grouped: bad packed operand shape");
+  CUtensorMap ma, mb;
+  OSMPS_TRY(tc_make_map(&ma, g.A, g.kind, g.rowsA, 2 * g.Kpl, BM));
+  OSMPS_TRY(tc_make_map(&mb, g.B, g.kind, g.rowsB, 2 * g.Kpl, BN));
+  const int kelem = KSLICE_BYTES / (int)tc_elem_bytes(g.kind);
+  const int grid = (int)std::min<int64_t>(g.n_tiles, ctx->sm_count);
+  const int ph = prof_begin(stream);
+  int* err = ctx->dev_flags;
+#define OSMPS_GROUPED_LAUNCH(K, O)                                                                   \
+  {                                                                                                 \
+    static const cudaError_t cfg_ = cudaFuncSetAttribute(                                           \
+        k_gemm_tc<K, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);             \
+    OSMPS_CUDA(cfg_);                                                                               \
+    k_gemm_tc<K, O><<<grid, THREADS, SMEM_BYTES, stream>>>(ma, mb, g.C, 0, 0, 0, 0, kelem,          \
+                                                           (int)g.Kpl, 1, (int)g.n_tiles, err,      \
+                                                           g.probs, g.n_prob);                      \
+    note_launch();                                                                                  \
+  }
+  if (g.kind == TC_BF16) {
+    if (g.out == TC_OUT_F32) OSMPS_GROUPED_LAUNCH(TC_BF16, TC_OUT_F32)
+    else OSMPS_GROUPED_LAUNCH(TC_BF16, TC_OUT_F64)
+  } else {
+    if (g.out == TC_OUT_F32) OSMPS_GROUPED_LAUNCH(TC_TF32, TC_OUT_F32)
+    else OSMPS_GROUPED_LAUNCH(TC_TF32, TC_OUT_F64)
+  }
+#undef OSMPS_GROUPED_LAUNCH
+  OSMPS_LAUNCH_CHECK();
+  prof_end(ph, stream, OSMPS_KERNEL_GEMM_TC, g.logical_flops, 3.0 * g.logical_flops);
+  return OSMPS_OK;
+}
 
 osmps_status gemm_tc(osmps_ctx* ctx, const GemmTc& g, cudaStream_t stream) {
   if (g.M <= 0 || g.N <= 0) return OSMPS_OK;

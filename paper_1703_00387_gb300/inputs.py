@@ -82,3 +82,22 @@ def chain_batch(n_chains=64, seed=0):
         param = float(rng.uniform(0.5, 1.5))
         out.append(dict(model=model, L=L, chi_max=chi_max, param=param))
     return out
+
+
+def u1_sector_profile(n_bar, total=512, width=8.0):
+    """Sector charges and sizes of one bond for the U(1) Bose-Hubbard workload:
+    sizes proportional to exp(-(n - n_bar)^2 / width), n integer, keeping the
+    n whose share rounds to at least half a state, each at least 1, the
+    largest adjusted so that the sizes sum to `total`."""
+    n = np.arange(int(np.floor(n_bar - 6 * np.sqrt(width))), int(np.ceil(n_bar + 6 * np.sqrt(width))) + 1)
+    p = np.exp(-(n - n_bar) ** 2 / width)
+    p = p / p.sum()
+    keep = total * p >= 0.5
+    n, p = n[keep], p[keep] / p[keep].sum()
+    chi = np.maximum(1, np.rint(total * p).astype(np.int64))
+    chi[np.argmax(chi)] += total - chi.sum()
+    return n.astype(np.int64), chi
+
+
+def random_dense(shape, seed=0):
+    return np.random.default_rng(seed).standard_normal(shape)

@@ -1,0 +1,113 @@
+"""U(1)-symmetric H_eff.theta on the GPU (grouped sector-block launches)
+against the oracle's dense product of the masked tensors. Bars as for the
+dense split-precision path: 5e-5 (bf16x3) / 1e-5 (tf32x3) on small shapes,
+1e-5 at the Bose-Hubbard workload size."""
+import numpy as np
+import pytest
+
+from oracle import mpo as ompo
+from oracle import u1 as ou1
+from paper_1703_00387_gb300 import binding as B
+from paper_1703_00387_gb300 import hamiltonians, inputs
+from paper_1703_00387_gb300 import u1 as pu1
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16x3": 5e-5, "tf32x3": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import os
+    if not os.path.exists(B.LIB_PATH):
+        from paper_1703_00387_gb300 import build
+        build.build()
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+def _run(ctx, left, right, nmax, sites, prec, seed, L_chain=8):
+    """sites: which two sites of a Bose-Hubbard chain give W1, W2."""
+    d = nmax + 1
+    Wp = hamiltonians.bose_hubbard(L_chain, 1.0, 4.0, nmax)
+    Wo = ompo.bose_hubbard_mpo(L_chain, 1.0, 4.0, nmax)
+    k1, k2 = sites
+    qp = pu1.channel_charges(Wp)
+    qo = ou1.mpo_channel_charges(Wo)
+    op = pu1.U1Operator(ctx, left, right, d, d, Wp[k1], Wp[k2], qp[k1], qp[k2 + 1])
+    ql = ou1.index_charges(*left)
+    qr = ou1.index_charges(*right)
+    wl, wr = Wo[k1].shape[0], Wo[k2].shape[3]
+    Lh = inputs.random_dense((len(ql), wl, len(ql)), seed)
+    Rh = inputs.random_dense((len(qr), wr, len(qr)), seed + 1)
+    th = inputs.random_dense((len(ql), d, d, len(qr)), seed + 2)
+    ref = ou1.heff_apply_u1(Lh, Wo[k1], Wo[k2], Rh, th, ql, qr, qo[k1], qo[k2 + 1])
+    ref_packed = ref[ou1.theta_mask(ql, qr, d, d)]
+    t = [dev(pu1.pack(Lh, op.m_L)), dev(Wp[k1]), dev(Wp[k2]), dev(pu1.pack(Rh, op.m_R)),
+         dev(pu1.pack(th, op.m_theta))]
+    y = torch.empty_like(t[4])
+    B.osmps_heff_apply_u1(ctx, op.plan, *t, y, precision=prec)
+    torch.cuda.synchronize()
+    out = y.cpu().numpy()
+    flops = op.plan.flops
+    op.close()
+    return out, ref_packed, flops
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+CASES = {
+    "small": (([3, 4, 5, 6], [2, 3, 3, 1]), ([5, 6, 7, 8, 9], [1, 2, 3, 2, 1]), 3, (2, 3)),
+    "multi_tile": (([10, 11, 12], [70, 130, 90]), ([12, 13, 14, 15], [100, 150, 60, 40]), 4, (3, 4)),
+    "gaps": (([0, 2, 3], [5, 7, 1]), ([1, 4, 9], [6, 3, 2]), 2, (1, 2)),
+    "left_boundary": (([0], [1]), ([0, 1, 2, 3, 4], [1, 1, 1, 1, 1]), 2, (0, 1)),
+    "right_boundary": (([4, 5, 6], [3, 2, 1]), ([6], [1]), 2, (6, 7)),
+}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_u1_heff_parity(ctx, case, prec):
+    left, right, nmax, sites = CASES[case]
+    y, ref, _ = _run(ctx, left, right, nmax, sites, prec, seed=len(case))
+    assert y.shape == ref.shape
+    assert rel(y, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_u1_heff_bose_hubbard_workload(ctx, prec):
+    """L = 64, N = 64, n <= 4 (d = 5), chi = 512 per bond, sector sizes from
+    the Gaussian profile around N k / L at bonds 31 and 33 (sites 31, 32)."""
+    left = inputs.u1_sector_profile(31.0, total=512, width=8.0)
+    right = inputs.u1_sector_profile(33.0, total=512, width=8.0)
+    y, ref, flops = _run(ctx, left, right, 4, (31, 32), prec, seed=64, L_chain=64)
+    assert rel(y, ref) <= 1e-5
+    assert flops > 0
+
+
+def test_u1_errors(ctx):
+    with pytest.raises(B.OsmpsError) as e:
+        B.U1Heff(ctx, [1, 1], [2, 2], [1], [1], 2, 2, 4, 4, 4, [0, 1, -1, 0], [0, 1, -1, 0])
+    assert e.value.status == B.EINVAL
+    with pytest.raises(B.OsmpsError) as e:
+        B.U1Heff(ctx, [1], [0], [1], [1], 2, 2, 4, 4, 4, [0, 1, -1, 0], [0, 1, -1, 0])
+    assert e.value.status == B.ESHAPE
+    plan = B.U1Heff(ctx, [0, 1], [2, 2], [1, 2], [2, 2], 2, 2, 4, 4, 4, [0, 1, -1, 0], [0, 1, -1, 0])
+    z = lambda n: torch.zeros(n, dtype=torch.float64, device="cuda:0")
+    W = dev(np.zeros((4, 2, 2, 4)))
+    with pytest.raises(B.OsmpsError) as e:
+        B.osmps_heff_apply_u1(ctx, plan, z(plan.n_L), W, W, z(plan.n_R), z(plan.n_theta),
+                              z(plan.n_theta), precision="fp64")
+    assert e.value.status == B.EUNSUPPORTED
+    with pytest.raises(ValueError):
+        B.osmps_heff_apply_u1(ctx, plan, z(plan.n_L + 1), W, W, z(plan.n_R), z(plan.n_theta),
+                              z(plan.n_theta))
+    plan.close()
