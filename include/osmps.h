@@ -366,9 +366,28 @@ osmps_status osmps_u1_heff_destroy(osmps_u1_heff* plan);
  * any may be NULL.                                                          */
 osmps_status osmps_u1_heff_sizes(const osmps_u1_heff* plan, int64_t* n_theta, int64_t* n_L,
                                  int64_t* n_R, double* flops);
-/* y = H_eff theta on packed device arrays (layouts above). precision:
- * OSMPS_PREC_BF16X3 or OSMPS_PREC_TF32X3 (others EUNSUPPORTED). Calls with
- * one plan must not overlap on the GPU (its buffers are reused).           */
+/* Convert the operator (packed L and R, dense W1 and W2) into the plan's
+ * tensor-core operands for `precision` (OSMPS_PREC_BF16X3 or TF32X3; others
+ * EUNSUPPORTED). The operator stays prepared until the next prepare.       */
+osmps_status osmps_u1_heff_prepare(osmps_ctx* ctx, osmps_u1_heff* plan, const double* L,
+                                   const double* W1, const double* W2, const double* R,
+                                   int precision, void* stream);
+/* y = H_eff theta for the prepared operator (packed device arrays; y must not
+ * alias theta). EINVAL if nothing was prepared.                           */
+osmps_status osmps_u1_heff_apply(osmps_ctx* ctx, osmps_u1_heff* plan, const double* theta,
+                                 double* y, void* stream);
+/* Lowest eigenpair of the U(1) block of H_eff by Lanczos (as
+ * osmps_lanczos_ground: float64 Krylov vectors, full reorthogonalisation,
+ * residual estimate <= tol, 1 <= max_iter <= 512), on packed vectors; the
+ * operator is prepared first. theta_inout: start vector in, normalised Ritz
+ * vector out. Host outputs; ENOCONV with the best pair written.            */
+osmps_status osmps_lanczos_ground_u1(osmps_ctx* ctx, osmps_u1_heff* plan, const double* L,
+                                     const double* W1, const double* W2, const double* R,
+                                     double* theta_inout, int max_iter, double tol, int precision,
+                                     double* energy_out, int* iters_out, double* resid_out,
+                                     void* stream);
+/* y = H_eff theta on packed device arrays (layouts above): prepare + apply.
+ * Calls with one plan must not overlap on the GPU (its buffers are reused). */
 osmps_status osmps_heff_apply_u1(osmps_ctx* ctx, osmps_u1_heff* plan, const double* L,
                                  const double* W1, const double* W2, const double* R,
                                  const double* theta, double* y, int precision, void* stream);

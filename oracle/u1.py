@@ -74,3 +74,20 @@ def heff_apply_u1(Lenv, W1, W2, Renv, theta, q_left, q_right, q_wl, q_wr):
     y = dmrg.heff_apply(np.where(ml, Lenv, 0.0), W1, W2, np.where(mr, Renv, 0.0),
                         np.where(mt, theta, 0.0))
     return np.where(mt, y, 0.0)
+
+
+def mps_mask(q_left, q_right, d):
+    """Allowed entries of an MPS tensor A[a, s, b]: q(a) + s = q(b)."""
+    return q_left[:, None, None] + np.arange(d)[None, :, None] == q_right[None, None, :]
+
+
+def sector_heff_matrix(Lenv, W1, W2, Renv, mask):
+    """H_eff as an explicit matrix on the allowed entries of theta (column i =
+    H_eff applied to the i-th allowed unit vector), for small sectors."""
+    idx = np.flatnonzero(mask)
+    H = np.zeros((idx.size, idx.size))
+    for col, i in enumerate(idx):
+        e = np.zeros(mask.shape)
+        e.flat[i] = 1.0
+        H[:, col] = dmrg.heff_apply(Lenv, W1, W2, Renv, e).flat[idx]
+    return H

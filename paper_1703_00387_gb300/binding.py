@@ -101,6 +101,10 @@ _SIGS = {
     "osmps_u1_heff_destroy": (_c.c_int, [_vp]),
     "osmps_u1_heff_sizes": (_c.c_int, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64), _dp]),
     "osmps_heff_apply_u1": (_c.c_int, [_vp, _vp] + [_vp] * 6 + [_c.c_int, _vp]),
+    "osmps_u1_heff_prepare": (_c.c_int, [_vp, _vp] + [_vp] * 4 + [_c.c_int, _vp]),
+    "osmps_u1_heff_apply": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "osmps_lanczos_ground_u1": (_c.c_int, [_vp, _vp] + [_vp] * 5 + [_c.c_int, _c.c_double, _c.c_int,
+                                                                     _dp, _c.POINTER(_c.c_int), _dp, _vp]),
     "osmps_sweep_batch": (_c.c_int, [_c.POINTER(_vp), _c.c_int, _c.POINTER(_vp), _c.POINTER(_vp),
                                      _c.POINTER(SweepParams), _i64, _c.POINTER(SweepStats),
                                      _c.POINTER(_c.c_int)]),
@@ -511,3 +515,27 @@ def osmps_heff_apply_u1(ctx, plan, L, W1, W2, R, theta, y, precision="bf16x3", s
                                      _dev(R, "R"), _dev(theta, "theta"), _dev(y, "y"),
                                      _prec(precision), _stream(stream)))
     return y
+
+
+def osmps_u1_heff_prepare(ctx, plan, L, W1, W2, R, precision="bf16x3", stream=None):
+    _check(lib().osmps_u1_heff_prepare(ctx.ptr, plan.ptr, _dev(L, "L"), _dev(W1, "W1"),
+                                       _dev(W2, "W2"), _dev(R, "R"), _prec(precision),
+                                       _stream(stream)))
+
+
+def osmps_u1_heff_apply(ctx, plan, theta, y, stream=None):
+    _check(lib().osmps_u1_heff_apply(ctx.ptr, plan.ptr, _dev(theta, "theta"), _dev(y, "y"),
+                                     _stream(stream)))
+    return y
+
+
+def osmps_lanczos_ground_u1(ctx, plan, L, W1, W2, R, theta, max_iter=100, tol=1e-12,
+                            precision="bf16x3", stream=None, allow_noconv=True):
+    """Returns (energy, iterations, residual estimate, converged)."""
+    e, it, res = _c.c_double(), _c.c_int(), _c.c_double()
+    st = lib().osmps_lanczos_ground_u1(ctx.ptr, plan.ptr, _dev(L, "L"), _dev(W1, "W1"),
+                                       _dev(W2, "W2"), _dev(R, "R"), _dev(theta, "theta"),
+                                       int(max_iter), float(tol), _prec(precision), _c.byref(e),
+                                       _c.byref(it), _c.byref(res), _stream(stream))
+    _check(st, allow=(ENOCONV,) if allow_noconv else ())
+    return e.value, it.value, res.value, st == 0

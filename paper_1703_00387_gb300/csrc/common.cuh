@@ -7,6 +7,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <functional>
 #include <vector>
 
 #include "osmps.h"
@@ -318,6 +319,13 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
                           int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int max_iter,
                           double tol, int precision, double* energy, int* iters, double* resid,
                           cudaStream_t stream);
+// Lanczos ground state of a symmetric operator given as y = A x (device
+// vectors of length n, work launched on s). Float64 Krylov basis with full
+// reorthogonalisation; theta is the start vector and receives the Ritz vector.
+using Matvec = std::function<osmps_status(const double* x, double* y)>;
+osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter, double tol,
+                          const Matvec& matvec, double* energy, int* iters, double* resid,
+                          cudaStream_t s);
 osmps_status theta_form_tc(osmps_ctx* ctx, const double* A1, const double* A2, double* theta,
                            int64_t chi_l, int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
                            int precision, cudaStream_t stream);

@@ -310,13 +310,10 @@ osmps_status project(osmps_ctx* ctx, const double* V, int64_t ld, int64_t n, int
 
 }  // namespace
 
-osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
-                          const double* R, double* theta, int64_t chi_l, int64_t d1, int64_t d2,
-                          int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int max_iter,
-                          double tol, int precision, double* energy, int* iters, double* resid,
+osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter, double tol,
+                          const Matvec& matvec, double* energy, int* iters, double* resid,
                           cudaStream_t s) {
   osmps_status st = OSMPS_OK;
-  const int64_t n = chi_l * d1 * d2 * chi_r;
   const int64_t ld = (n + 1) & ~(int64_t)1;  // even row stride: 16-byte aligned rows
   if (max_iter > n) max_iter = (int)n;
   double* V = (double*)ws_get(ctx, SLOT_LZ_BASIS, (size_t)max_iter * ld * 8, s, &st);
@@ -328,7 +325,6 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
   double* part = (double*)ws_get(ctx, SLOT_LZ_PART, (size_t)MAXIT * DOT_MAX_BLOCKS * 8, s, &st);
   if (!part) return st;
   OSMPS_TRY(pinned_reserve(ctx, 16));
-  OSMPS_TRY(heff_prepare(ctx, L, W1, W2, R, chi_l, d1, d2, chi_r, wl, wm, wr, precision, s));
 
   // v_0 = theta / ||theta||
   OSMPS_TRY(vec_norm2(ctx, theta, n, sc + OFF_MISC + 4, s));
@@ -345,8 +341,7 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
   bool converged = false;
   for (int j = 0; j < max_iter; ++j) {
     double* vj = V + (int64_t)j * ld;
-    OSMPS_TRY(heff_apply_impl(ctx, nullptr, nullptr, nullptr, nullptr, vj, w, chi_l, d1, d2,
-                              chi_r, wl, wm, wr, precision, s, true));
+    OSMPS_TRY(matvec(vj, w));
     OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C1, s));
     OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C2, s));
     OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, s));
@@ -386,6 +381,20 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
     return set_error(OSMPS_ENOCONV, "lanczos: residual %.3e above tol %.3e after %d steps", res,
                      tol, m);
   return OSMPS_OK;
+}
+
+osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                          const double* R, double* theta, int64_t chi_l, int64_t d1, int64_t d2,
+                          int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int max_iter,
+                          double tol, int precision, double* energy, int* iters, double* resid,
+                          cudaStream_t s) {
+  OSMPS_TRY(heff_prepare(ctx, L, W1, W2, R, chi_l, d1, d2, chi_r, wl, wm, wr, precision, s));
+  const Matvec mv = [&](const double* x, double* y) {
+    return heff_apply_impl(ctx, nullptr, nullptr, nullptr, nullptr, x, y, chi_l, d1, d2, chi_r,
+                           wl, wm, wr, precision, s, true);
+  };
+  return lanczos_core(ctx, chi_l * d1 * d2 * chi_r, theta, max_iter, tol, mv, energy, iters,
+                      resid, s);
 }
 
 }  // namespace osmps

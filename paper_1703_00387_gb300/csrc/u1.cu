@@ -38,7 +38,8 @@ struct osmps_u1_heff {
   std::vector<int64_t> kp1, kp4;
   int64_t tiles1 = 0, rowsA1 = 0, rowsB1 = 0, Kpl1 = 64, n_T1 = 0;
   int64_t tiles4 = 0, rowsA4 = 0, rowsB4 = 0, Kpl4 = 64, n_Y = 0;
-  int kind_loaded = -1;
+  int kind_loaded = -1;    // operand type of the problem table on the device
+  int prepared_kind = -1;  // operand type of the prepared L, R operands (-1: none)
   // device memory
   int64_t* d_tab = nullptr;
   osmps::GroupProblem* d_prob = nullptr;
@@ -436,9 +437,8 @@ osmps_status u1_build(osmps_u1_heff* h) {
 }
 
 template <int KIND>
-osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* L, const double* W1,
-                           const double* W2, const double* R, const double* theta, double* y,
-                           cudaStream_t s) {
+osmps_status u1_prepare_kind(osmps_u1_heff* h, const double* L, const double* W1, const double* W2,
+                             const double* R, cudaStream_t s) {
   const int64_t* T = h->d_tab;
   uint8_t* B = h->d_buf;
   if (h->kind_loaded != KIND) {
@@ -454,7 +454,7 @@ osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* L, co
                             cudaMemcpyHostToDevice));
     h->kind_loaded = KIND;
   }
-  // operator: L and R operands, combined W coefficients
+  // L and R as split operands, combined W coefficients
   if (h->rowsA1 > 0) {
     k_row_gather_split<KIND><<<ew_grid(h->rowsA1 * h->Kpl1), 256, 0, s>>>(
         L, T + h->t_a1src, T + h->t_a1len, h->rowsA1, h->Kpl1, B + h->o_A1);
@@ -468,6 +468,16 @@ osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* L, co
   { k_wcomb<<<ew_grid(h->wl * h->d1 * h->d2 * h->d1 * h->d2 * h->wr), 256, 0, s>>>(
         W1, W2, (int)h->d1, (int)h->d2, (int)h->wl, (int)h->wm, (int)h->wr,
         reinterpret_cast<float*>(B + h->o_Wc)); note_launch(); }
+  OSMPS_LAUNCH_CHECK();
+  h->prepared_kind = KIND;
+  return OSMPS_OK;
+}
+
+template <int KIND>
+osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* theta, double* y,
+                           cudaStream_t s) {
+  const int64_t* T = h->d_tab;
+  uint8_t* B = h->d_buf;
   // stage 1
   if (h->rowsB1 > 0) {
     dim3 grid((unsigned)cdiv(h->rowsB1, 32), (unsigned)cdiv(h->Kpl1, 32));
@@ -623,6 +633,57 @@ osmps_status osmps_u1_heff_sizes(const osmps_u1_heff* h, int64_t* n_theta, int64
   return OSMPS_OK;
 }
 
+osmps_status osmps_u1_heff_prepare(osmps_ctx* ctx, osmps_u1_heff* h, const double* L,
+                                   const double* W1, const double* W2, const double* R,
+                                   int precision, void* stream) {
+  clear_error();
+  if (!ctx || !h || !L || !W1 || !W2 || !R)
+    return set_error(OSMPS_EINVAL, "osmps_u1_heff_prepare: null argument");
+  if (precision != OSMPS_PREC_BF16X3 && precision != OSMPS_PREC_TF32X3)
+    return set_error(OSMPS_EUNSUPPORTED, "osmps_u1_heff_prepare: precision %d (bf16x3 or tf32x3)", precision);
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == OSMPS_PREC_BF16X3) return u1_prepare_kind<TC_BF16>(h, L, W1, W2, R, s);
+  return u1_prepare_kind<TC_TF32>(h, L, W1, W2, R, s);
+}
+
+osmps_status osmps_u1_heff_apply(osmps_ctx* ctx, osmps_u1_heff* h, const double* theta, double* y,
+                                 void* stream) {
+  clear_error();
+  if (!ctx || !h || !theta || !y) return set_error(OSMPS_EINVAL, "osmps_u1_heff_apply: null argument");
+  if (y == theta) return set_error(OSMPS_EINVAL, "osmps_u1_heff_apply: y aliases theta");
+  if (h->prepared_kind < 0) return set_error(OSMPS_EINVAL, "osmps_u1_heff_apply: no prepared operator");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->prepared_kind == TC_BF16) return u1_apply_kind<TC_BF16>(ctx, h, theta, y, s);
+  return u1_apply_kind<TC_TF32>(ctx, h, theta, y, s);
+}
+
+osmps_status osmps_lanczos_ground_u1(osmps_ctx* ctx, osmps_u1_heff* h, const double* L,
+                                     const double* W1, const double* W2, const double* R,
+                                     double* theta_inout, int max_iter, double tol, int precision,
+                                     double* energy_out, int* iters_out, double* resid_out,
+                                     void* stream) {
+  clear_error();
+  if (!ctx || !h || !L || !W1 || !W2 || !R || !theta_inout || !energy_out || !iters_out)
+    return set_error(OSMPS_EINVAL, "osmps_lanczos_ground_u1: null argument");
+  if (max_iter < 1 || max_iter > 512)
+    return set_error(OSMPS_EINVAL, "osmps_lanczos_ground_u1: max_iter %d outside [1, 512]", max_iter);
+  if (!(tol >= 0.0)) return set_error(OSMPS_EINVAL, "osmps_lanczos_ground_u1: tol %g", tol);
+  if (h->n_theta < 1) return set_error(OSMPS_ESHAPE, "osmps_lanczos_ground_u1: empty sector");
+  OSMPS_TRY(osmps_u1_heff_prepare(ctx, h, L, W1, W2, R, precision, stream));
+  CtxScope scope_(ctx);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Matvec mv = [&](const double* x, double* y) {
+    return h->prepared_kind == TC_BF16 ? u1_apply_kind<TC_BF16>(ctx, h, x, y, s)
+                                       : u1_apply_kind<TC_TF32>(ctx, h, x, y, s);
+  };
+  return lanczos_core(ctx, h->n_theta, theta_inout, max_iter, tol, mv, energy_out, iters_out,
+                      resid_out, s);
+}
+
 osmps_status osmps_heff_apply_u1(osmps_ctx* ctx, osmps_u1_heff* h, const double* L,
                                  const double* W1, const double* W2, const double* R,
                                  const double* theta, double* y, int precision, void* stream) {
@@ -632,11 +693,8 @@ osmps_status osmps_heff_apply_u1(osmps_ctx* ctx, osmps_u1_heff* h, const double*
   if (y == theta) return set_error(OSMPS_EINVAL, "osmps_heff_apply_u1: y aliases theta");
   if (precision != OSMPS_PREC_BF16X3 && precision != OSMPS_PREC_TF32X3)
     return set_error(OSMPS_EUNSUPPORTED, "osmps_heff_apply_u1: precision %d (bf16x3 or tf32x3)", precision);
-  OSMPS_CUDA(cudaSetDevice(ctx->device));
-  CtxScope scope_(ctx);
-  cudaStream_t s = (cudaStream_t)stream;
-  if (precision == OSMPS_PREC_BF16X3) return u1_apply_kind<TC_BF16>(ctx, h, L, W1, W2, R, theta, y, s);
-  return u1_apply_kind<TC_TF32>(ctx, h, L, W1, W2, R, theta, y, s);
+  OSMPS_TRY(osmps_u1_heff_prepare(ctx, h, L, W1, W2, R, precision, stream));
+  return osmps_u1_heff_apply(ctx, h, theta, y, stream);
 }
 
 }  // extern "C"

@@ -111,3 +111,69 @@ def test_u1_errors(ctx):
         B.osmps_heff_apply_u1(ctx, plan, z(plan.n_L + 1), W, W, z(plan.n_R), z(plan.n_theta),
                               z(plan.n_theta))
     plan.close()
+
+
+def _u1_chain_operator(Lc=6, nmax=2, N=6, chi_sec=2, seed=10):
+    """Environments of a random particle-number-conserving Bose-Hubbard MPS
+    (oracle contractions) around sites 2, 3, with the sector structure."""
+    from oracle import dmrg
+    d = nmax + 1
+    sectors = []
+    for k in range(Lc + 1):
+        qs = list(range(max(0, N - (Lc - k) * nmax), min(N, k * nmax) + 1))
+        sectors.append((qs, [1 if k in (0, Lc) else chi_sec] * len(qs)))
+    q = [ou1.index_charges(*s) for s in sectors]
+    A = [inputs.random_dense((len(q[k]), d, len(q[k + 1])), seed + k) * ou1.mps_mask(q[k], q[k + 1], d)
+         for k in range(Lc)]
+    Wo = ompo.bose_hubbard_mpo(Lc, 1.0, 4.0, nmax)
+    Le = np.ones((1, 1, 1))
+    for k in range(2):
+        Le = dmrg.env_left(Le, A[k], Wo[k])
+    Re = np.ones((1, 1, 1))
+    for k in range(Lc - 1, 3, -1):
+        Re = dmrg.env_right(Re, A[k], Wo[k])
+    return sectors, q, Wo, Le, Re, d
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_u1_lanczos_ground_matches_sector_eigenvalue(ctx, prec):
+    sectors, q, Wo, Le, Re, d = _u1_chain_operator()
+    mt = ou1.theta_mask(q[2], q[4], d, d)
+    E0 = np.linalg.eigvalsh(ou1.sector_heff_matrix(Le, Wo[2], Wo[3], Re, mt))[0]
+    Wp = hamiltonians.bose_hubbard(6, 1.0, 4.0, 2)
+    qp = pu1.channel_charges(Wp)
+    op = pu1.U1Operator(ctx, sectors[2], sectors[4], d, d, Wp[2], Wp[3], qp[2], qp[4])
+    th = dev(pu1.pack(inputs.random_dense(mt.shape, 5), op.m_theta))
+    e, it, res, conv = B.osmps_lanczos_ground_u1(ctx, op.plan, dev(pu1.pack(Le, op.m_L)), dev(Wp[2]),
+                                                 dev(Wp[3]), dev(pu1.pack(Re, op.m_R)), th,
+                                                 max_iter=200, tol=1e-9, precision=prec)
+    assert conv
+    assert abs(e - E0) <= 1e-5 * abs(E0)
+    # the Ritz vector is normalised and is an eigenvector of the oracle matrix
+    v = th.cpu().numpy()
+    assert abs(np.linalg.norm(v) - 1.0) < 1e-12
+    H = ou1.sector_heff_matrix(Le, Wo[2], Wo[3], Re, mt)
+    assert np.linalg.norm(H @ v - E0 * v) <= 1e-4 * abs(E0)
+    op.close()
+
+
+def test_u1_prepare_apply_matches_combined(ctx):
+    left, right, nmax, sites = CASES["multi_tile"]
+    Wp = hamiltonians.bose_hubbard(8, 1.0, 4.0, nmax)
+    qp = pu1.channel_charges(Wp)
+    k1, k2 = sites
+    op = pu1.U1Operator(ctx, left, right, nmax + 1, nmax + 1, Wp[k1], Wp[k2], qp[k1], qp[k2 + 1])
+    pl = op.plan
+    L = dev(inputs.random_dense((pl.n_L,), 1))
+    R = dev(inputs.random_dense((pl.n_R,), 2))
+    th = dev(inputs.random_dense((pl.n_theta,), 3))
+    W1, W2 = dev(Wp[k1]), dev(Wp[k2])
+    y1 = torch.empty_like(th)
+    y2 = torch.empty_like(th)
+    B.osmps_heff_apply_u1(ctx, pl, L, W1, W2, R, th, y1, precision="tf32x3")
+    B.osmps_u1_heff_prepare(ctx, pl, L, W1, W2, R, precision="tf32x3")
+    B.osmps_u1_heff_apply(ctx, pl, th, y2)
+    B.osmps_u1_heff_apply(ctx, pl, th, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    op.close()

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import mpo, u1
+from oracle import u1 as ou1
 from paper_1703_00387_gb300 import inputs
 
 
@@ -61,3 +62,28 @@ def test_sector_profile_recipe():
     assert sum(chi) == 512 and min(chi) >= 1
     assert list(q) == sorted(q) and len(set(q)) == len(q)
     assert chi[list(q).index(31)] == max(chi)
+
+
+def test_sector_heff_from_u1_mps_is_symmetric_and_closed():
+    """Environments of a random particle-number-conserving MPS give an H_eff
+    that maps the sector into itself and is symmetric on it."""
+    from oracle import dmrg
+    Lc, nmax, N, d = 6, 2, 6, 3
+    q = [ou1.index_charges(list(range(max(0, N - (Lc - k) * nmax), min(N, k * nmax) + 1)),
+                           [1 if k in (0, Lc) else 2] * (min(N, k * nmax) - max(0, N - (Lc - k) * nmax) + 1))
+         for k in range(Lc + 1)]
+    A = [inputs.random_dense((len(q[k]), d, len(q[k + 1])), 10 + k) * ou1.mps_mask(q[k], q[k + 1], d)
+         for k in range(Lc)]
+    W = mpo.bose_hubbard_mpo(Lc, 1.0, 4.0, nmax)
+    Le = np.ones((1, 1, 1))
+    for k in (0, 1):
+        Le = dmrg.env_left(Le, A[k], W[k])
+    Re = np.ones((1, 1, 1))
+    for k in (5, 4):
+        Re = dmrg.env_right(Re, A[k], W[k])
+    qw = ou1.mpo_channel_charges(W)
+    assert np.abs(np.where(ou1.env_mask(q[2], qw[2], q[2]), 0.0, Le)).max() == 0.0
+    assert np.abs(np.where(ou1.env_mask(q[4], qw[4], q[4]), 0.0, Re)).max() == 0.0
+    mt = ou1.theta_mask(q[2], q[4], d, d)
+    H = ou1.sector_heff_matrix(Le, W[2], W[3], Re, mt)
+    assert np.abs(H - H.T).max() <= 1e-12 * np.abs(H).max()
