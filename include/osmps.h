@@ -74,6 +74,17 @@ const char* osmps_status_string(osmps_status s);
  * Owns the workspace, a cuSOLVER handle and a device error flag.            */
 osmps_status osmps_ctx_create(int device, size_t ws_bytes, osmps_ctx** out);
 osmps_status osmps_ctx_destroy(osmps_ctx* ctx);
+/* Eigensolver used by the split (osmps_split and the sweeps):
+ *   OSMPS_EIG_AUTO     (default) the faster of the two as measured at
+ *                      chi = 1024 on GB300: currently cuSOLVER;
+ *   OSMPS_EIG_CUSOLVER cuSOLVER dsyevd / dsyevdx (largest pairs) always;
+ *   OSMPS_EIG_TRIDIAG  Householder reduction (cuSOLVER dsytrd), then this
+ *                      library's bisection, inverse iteration, Cholesky QR and
+ *                      blocked back-transformation (float64-accurate emulated
+ *                      GEMMs) for every Gram dimension >= 2.
+ * Both are float64-accurate. EINVAL for another value.                      */
+typedef enum { OSMPS_EIG_AUTO = 0, OSMPS_EIG_CUSOLVER = 1, OSMPS_EIG_TRIDIAG = 2 } osmps_eig_solver;
+osmps_status osmps_ctx_set_eig_solver(osmps_ctx* ctx, int solver);
 /* Bytes of device memory currently held by the context's workspace.         */
 size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx);
 
@@ -143,6 +154,18 @@ osmps_status osmps_heff_apply_noalloc(const double* L, const double* W1, const d
  * C must not alias A or B. Scratch from the context.                       */
 osmps_status osmps_dgemm_emu(osmps_ctx* ctx, const double* A, const double* B, double* C,
                              int64_t M, int64_t N, int64_t K, void* stream);
+
+/* Householder reduction of a symmetric matrix to tridiagonal form, the first
+ * step of the float64 eigendecomposition of the split (Sec. 2, Eq.
+ * AAD_ULLUD): Q^T A Q = T with d (n) its diagonal, e (n-1) its off-diagonal,
+ * Q = H(0) ... H(n-2), H(j) = I - tau[j] v v^T, v = (0..0, 1 at j+1,
+ * A[j+2.., j]) stored below the subdiagonal of column j (column-major view;
+ * the layout of LAPACK's dsytrd with uplo = L). A: n x n device array
+ * holding the full symmetric matrix (both triangles), overwritten. Panels of
+ * 32 columns on a cooperative kernel, the trailing updates on the
+ * float64-accurate emulated tensor-core GEMM. 2 <= n <= 8192, else ESHAPE. */
+osmps_status osmps_sytrd(osmps_ctx* ctx, double* A, int64_t n, double* d, double* e, double* tau,
+                         void* stream);
 
 /* Environment update (Sec. 3.4: the fixed sites are contracted into L and R
  * one site at a time).

@@ -67,12 +67,14 @@ _SIGS = {
     "osmps_ctx_create": (_c.c_int, [_c.c_int, _c.c_size_t, _c.POINTER(_vp)]),
     "osmps_ctx_destroy": (_c.c_int, [_vp]),
     "osmps_ctx_workspace_bytes": (_c.c_size_t, [_vp]),
+    "osmps_ctx_set_eig_solver": (_c.c_int, [_vp, _c.c_int]),
     "osmps_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "osmps_profile_read": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_i64), _dp, _dp, _dp]),
     "osmps_kernel_launches": (_i64, []),
     "osmps_heff_apply": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 + [_c.c_int, _vp]),
     "osmps_heff_apply_noalloc": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 + [_vp]),
     "osmps_dgemm_emu": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _vp]),
+    "osmps_sytrd": (_c.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "osmps_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_c.c_int, _vp]),
     "osmps_lanczos_ground": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 +
                              [_c.c_int, _c.c_double, _c.c_int, _dp, _c.POINTER(_c.c_int), _dp, _vp]),
@@ -165,6 +167,11 @@ class Context:
         self.ptr = _vp()
         _check(lib().osmps_ctx_create(int(device), int(ws_bytes), _c.byref(self.ptr)))
         self.device = device
+
+    def set_eig_solver(self, solver):
+        """'auto', 'cusolver' or 'tridiag' (the split's float64 eigensolver)."""
+        code = {"auto": 0, "cusolver": 1, "tridiag": 2}[solver] if isinstance(solver, str) else int(solver)
+        _check(lib().osmps_ctx_set_eig_solver(self.ptr, code))
 
     def workspace_bytes(self):
         return int(lib().osmps_ctx_workspace_bytes(self.ptr))
@@ -539,3 +546,10 @@ def osmps_lanczos_ground_u1(ctx, plan, L, W1, W2, R, theta, max_iter=100, tol=1e
                                        _c.byref(it), _c.byref(res), _stream(stream))
     _check(st, allow=(ENOCONV,) if allow_noconv else ())
     return e.value, it.value, res.value, st == 0
+
+
+def osmps_sytrd(ctx, A, d, e, tau, stream=None):
+    """Householder tridiagonalisation of the symmetric A (overwritten, dsytrd layout)."""
+    n = A.shape[0]
+    _check(lib().osmps_sytrd(ctx.ptr, _dev(A, "A"), n, _dev(d, "d"), _dev(e, "e"), _dev(tau, "tau"),
+                             _stream(stream)))

@@ -77,6 +77,7 @@ enum Slot {
   SLOT_SPLIT_EV,
   SLOT_SPLIT_WORK,
   SLOT_SPLIT_TMP,
+  SLOT_SPLIT_TMP2,
   SLOT_QR_WORK,
   SLOT_QR_TAU,
   SLOT_QR_R,
@@ -88,6 +89,8 @@ enum Slot {
   SLOT_EMU_A,
   SLOT_EMU_B,
   SLOT_EMU_EXP,
+  SLOT_EMU_MAX,
+  SLOT_TRD,
   SLOT_EIG_X,
   SLOT_EIG_F32,
   SLOT_EIG_R,
@@ -134,6 +137,8 @@ struct osmps_ctx {
   bool heff_ready = false;
   int heff_prec = -1;
   int64_t heff_dims[7] = {0, 0, 0, 0, 0, 0, 0};
+  // eigensolver of the split: OSMPS_EIG_AUTO / OSMPS_EIG_CUSOLVER / OSMPS_EIG_TRIDIAG
+  int eig_solver = 0;
 };
 
 namespace osmps {
@@ -332,6 +337,15 @@ osmps_status theta_form_tc(osmps_ctx* ctx, const double* A1, const double* A2, d
 osmps_status theta_form_impl(const double* A1, const double* A2, double* theta, int64_t chi_l,
                              int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
                              cudaStream_t stream);
+// Householder tridiagonalisation (dsytrd layout: reflectors below the
+// subdiagonal of column j, d, e, tau) of a full symmetric n x n matrix.
+bool sytrd_supported(int64_t n);
+osmps_status sytrd_tc(osmps_ctx* ctx, double* A, int64_t n, double* d, double* e, double* tau,
+                      cudaStream_t s);
+// Largest nev eigenpairs of the symmetric n x n matrix G (overwritten):
+// eigenvalues ascending in ev, eigenvectors as the rows of Y (nev x n).
+osmps_status eig_top(osmps_ctx* ctx, double* G, int64_t n, int64_t nev, double* ev, double* Y,
+                     cudaStream_t s);
 osmps_status split_impl(osmps_ctx* ctx, const double* theta, double* A1, double* A2,
                         int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r, int move_right,
                         int64_t chi_max, double eps_local, int64_t* chi_new, double* discarded,

@@ -356,3 +356,12 @@ size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx) {
 }
 
 }  // extern "C"
+
+extern "C" osmps_status osmps_ctx_set_eig_solver(osmps_ctx* ctx, int solver) {
+  osmps::clear_error();
+  if (!ctx) return osmps::set_error(OSMPS_EINVAL, "osmps_ctx_set_eig_solver: null context");
+  if (solver < OSMPS_EIG_AUTO || solver > OSMPS_EIG_TRIDIAG)
+    return osmps::set_error(OSMPS_EINVAL, "osmps_ctx_set_eig_solver: solver %d", solver);
+  ctx->eig_solver = solver;
+  return OSMPS_OK;
+}

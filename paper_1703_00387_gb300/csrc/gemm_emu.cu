@@ -273,14 +273,31 @@ __global__ void k_rowexp_contig(SplitView v, int* __restrict__ e) {
   }
 }
 
-// e[r] for rows that are adjacent in memory (K strided): one thread per row.
-__global__ void k_rowexp_strided(SplitView v, int* __restrict__ e) {
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < v.rows;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long m = 0;
-    for (int64_t k = 0; k < v.K; ++k) m = max(m, mag_bits(load_view(v, r, k)));
-    e[r] = exponent_of_max(m);
+// Row maxima (of the magnitude bits) for rows that are adjacent in memory (K
+// strided): 32 rows x a chunk of K per block, threads along the rows read
+// neighbouring addresses; partial maxima combined with atomicMax into m[r].
+constexpr int ROWMAX_KCHUNK = 256;
+__global__ void k_rowmax_strided(SplitView v, unsigned long long* __restrict__ m) {
+  __shared__ unsigned long long sh[8][33];
+  const int64_t r = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.y * ROWMAX_KCHUNK;
+  const int64_t k1 = min(k0 + (int64_t)ROWMAX_KCHUNK, v.K);
+  unsigned long long a = 0;
+  if (r < v.rows)
+    for (int64_t k = k0 + threadIdx.y; k < k1; k += 8) a = max(a, mag_bits(load_view(v, r, k)));
+  sh[threadIdx.y][threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.y == 0 && r < v.rows) {
+    for (int i = 1; i < 8; ++i) a = max(a, sh[i][threadIdx.x]);
+    atomicMax(&m[r], a);
   }
+}
+
+__global__ void k_exp_from_max(const unsigned long long* __restrict__ m, int64_t rows,
+                               int* __restrict__ e) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+       r += (int64_t)gridDim.x * blockDim.x)
+    e[r] = exponent_of_max(m[r]);
 }
 
 // x * 2^(56 - e) rounded to the nearest integer, from the IEEE bits (integer
@@ -348,8 +365,8 @@ int blocks_1d(int64_t n, int t) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 65536));
 }
 
-osmps_status slice_operand(const SplitView& v, int64_t Kp, int* e, __nv_bfloat16* dst,
-                           cudaStream_t s) {
+osmps_status slice_operand(osmps_ctx* ctx, const SplitView& v, int64_t Kp, int* e,
+                           __nv_bfloat16* dst, cudaStream_t s) {
   if (v.rows <= 0) return OSMPS_OK;
   const bool contig = (v.sk == 1);
   if (contig) {
@@ -357,8 +374,15 @@ osmps_status slice_operand(const SplitView& v, int64_t Kp, int* e, __nv_bfloat16
     { k_rowexp_contig<<<(unsigned)v.rows, 256, 0, s>>>(v, e); note_launch(); }
     { k_slice_direct<<<blocks_1d(v.rows * Kp, 256), 256, 0, s>>>(v, e, dst, Kp); note_launch(); }
   } else {
-    { k_rowexp_strided<<<blocks_1d(v.rows, 256), 256, 0, s>>>(v, e); note_launch(); }
-    if (cdiv(Kp, 32) > 65535) return set_error(OSMPS_ESHAPE, "emulated GEMM: K too large");
+    if (cdiv(Kp, 32) > 65535 || cdiv(v.K, ROWMAX_KCHUNK) > 65535)
+      return set_error(OSMPS_ESHAPE, "emulated GEMM: K too large");
+    osmps_status st = OSMPS_OK;
+    auto* mx = (unsigned long long*)ws_get(ctx, SLOT_EMU_MAX, (size_t)v.rows * 8, s, &st);
+    if (!mx) return st;
+    OSMPS_CUDA(cudaMemsetAsync(mx, 0, (size_t)v.rows * 8, s));
+    dim3 g1((unsigned)cdiv(v.rows, 32), (unsigned)std::max<int64_t>(1, cdiv(v.K, ROWMAX_KCHUNK)));
+    { k_rowmax_strided<<<g1, dim3(32, 8), 0, s>>>(v, mx); note_launch(); }
+    { k_exp_from_max<<<blocks_1d(v.rows, 256), 256, 0, s>>>(mx, v.rows, e); note_launch(); }
     dim3 grid((unsigned)cdiv(v.rows, 32), (unsigned)cdiv(Kp, 32));
     { k_slice_transpose<<<grid, dim3(32, 8), 0, s>>>(v, e, dst, Kp); note_launch(); }
   }
@@ -397,8 +421,8 @@ osmps_status gemm_emu(osmps_ctx* ctx, const SplitView& a, const SplitView& b, in
   if (!ex) return st;
   int* eA = ex;
   int* eB = ex + ((M + 63) / 64) * 64;
-  OSMPS_TRY(slice_operand(a, Kp, eA, sa, s));
-  OSMPS_TRY(slice_operand(b, Kp, eB, sb, s));
+  OSMPS_TRY(slice_operand(ctx, a, Kp, eA, sa, s));
+  OSMPS_TRY(slice_operand(ctx, b, Kp, eB, sb, s));
   CUtensorMap ma, mb;
   OSMPS_TRY(tc_make_map(&ma, sa, TC_BF16, M, SLICES * Kp, EBM));
   OSMPS_TRY(tc_make_map(&mb, sb, TC_BF16, N, SLICES * Kp, EBN));

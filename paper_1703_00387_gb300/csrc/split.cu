@@ -8,8 +8,11 @@
 // with discarded weight <= eps_local), lambda^2 normalised to sum 1. The
 // eigenvalues are copied to the host to fix chi' (the next shapes depend on it).
 //
-// Arithmetic: the eigenpairs come from cuSOLVER in float64 (dsyevdx for the
-// largest min(chi_max, rank) only, dsyevd when that is all of them). The
+// Arithmetic: the eigenpairs are float64, from cuSOLVER (dsyevdx for the
+// largest min(chi_max, rank) only, dsyevd when that is all of them) or, when
+// the context selects it (osmps_ctx_set_eig_solver), from the tridiagonal
+// route of eig.cu (cuSOLVER dsytrd, then bisection, inverse iteration,
+// Cholesky QR and blocked back-transformation on emulated-float64 GEMMs). The
 // Gram matrix and the projection are float64 GEMMs: on the DMMA kernel for
 // OSMPS_PREC_FP64, on the float64-accurate emulated tensor-core GEMM for
 // every other precision.
@@ -206,7 +209,15 @@ osmps_status split_impl(osmps_ctx* ctx, const double* theta, double* A1, double*
   OSMPS_SOLVER(cusolverDnSetStream(ctx->solver, s));
   int lwork = 0, found = 0;
   double* Z = nullptr;  // eigenvectors, column-major n x nev (rows of a row-major nev x n)
-  if (nev == n) {
+  const bool tridiag = ctx->eig_solver == OSMPS_EIG_TRIDIAG;
+  if (tridiag && n >= 2) {
+    double* Y = (double*)ws_get(ctx, SLOT_SPLIT_TMP2, (size_t)nev * n * 8, s, &st);
+    if (!Y) return st;
+    OSMPS_TRY(eig_top(ctx, G, n, nev, ev, Y, s));
+    found = (int)nev;
+    Z = Y;
+    OSMPS_CUDA(cudaMemsetAsync(ctx->dev_info, 0, sizeof(int), s));
+  } else if (nev == n) {
     OSMPS_SOLVER(cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
                                              CUBLAS_FILL_MODE_LOWER, (int)n, G, (int)n, ev, &lwork));
     double* work = (double*)ws_get(ctx, SLOT_SPLIT_WORK, (size_t)std::max(lwork, 1) * 8, s, &st);

@@ -235,3 +235,94 @@ def test_invalid_arguments_are_reported(ctx):
     with pytest.raises(B.OsmpsError) as e:
         B.osmps_lanczos_ground(ctx, Lh, W1, W2, Rh, z, max_iter=5)
     assert e.value.status == 1  # zero start vector
+
+
+def _split_case_spectrum(seed, shape, s):
+    chi_l, d1, d2, chi_r = shape
+    rng = np.random.default_rng(seed)
+    m, n = chi_l * d1, d2 * chi_r
+    r = len(s)
+    U, _ = np.linalg.qr(rng.standard_normal((m, r)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    M = (U * s) @ V.T
+    return (M / np.linalg.norm(M)).reshape(shape)
+
+
+SPECTRA = {  # (fast decay to the noise floor is covered by test_split_parity)
+    "slow_decay": lambda r: np.exp(-0.01 * np.arange(r)),
+    "multiplets": lambda r: np.repeat(np.exp(-0.05 * np.arange((r + 2) // 3)), 3)[:r],
+    "rank_deficient": lambda r: np.r_[np.exp(-0.02 * np.arange(r // 3)), np.zeros(r - r // 3)],
+}
+
+
+@pytest.mark.parametrize("solver", ["tridiag", "cusolver"])
+@pytest.mark.parametrize("move_right", [1, 0])
+@pytest.mark.parametrize("spectrum", list(SPECTRA))
+@pytest.mark.parametrize("shape,chi_max", [((100, 2, 2, 90), 60), ((300, 2, 2, 256), 255),
+                                           ((24, 5, 5, 30), 81)])
+def test_split_eigensolvers(ctx, solver, move_right, spectrum, shape, chi_max):
+    """Both float64 eigensolvers of the split (cuSOLVER dsyevdx and the
+    tridiagonal route: bisection, inverse iteration, Cholesky QR, blocked
+    back-transformation) against the oracle's SVD truncation, on spectra
+    with slow decay, exact multiplets and exact zeros."""
+    chi_l, d1, d2, chi_r = shape
+    r = min(chi_l * d1, d2 * chi_r)
+    theta = _split_case_spectrum(7, shape, SPECTRA[spectrum](r))
+    # exact zeros: a tolerance stops both sides at the rank (cuts are multiples of 3 so
+    # that no exact multiplet is split)
+    eps = 1e-14 if spectrum == "rank_deficient" else 0.0
+    a_ref, b_ref, info = od.split_svd(theta, chi_max, eps, bool(move_right))
+    cap = r
+    A1 = torch.empty(chi_l * d1 * cap, dtype=torch.float64, device="cuda:0")
+    A2 = torch.empty(cap * d2 * chi_r, dtype=torch.float64, device="cuda:0")
+    ctx.set_eig_solver(solver)
+    try:
+        chn, disc, ent, lam2 = B.osmps_split(ctx, dev(theta), A1, A2, move_right, chi_max, eps,
+                                             precision="fp64emu")
+    finally:
+        ctx.set_eig_solver("auto")
+    assert chn == info["keep"]
+    k = min(chi_max, len(info["lam2"]))
+    np.testing.assert_allclose(lam2[:k], info["lam2"][:k], rtol=1e-12, atol=1e-14)
+    assert abs(disc - info["discarded"]) <= 1e-13
+    a = A1[: chi_l * d1 * chn].cpu().numpy().reshape(chi_l, d1, chn)
+    b = A2[: chn * d2 * chi_r].cpu().numpy().reshape(chn, d2, chi_r)
+    s_min = np.sqrt(info["lam2"][chn - 1])
+    tol = 1e-11 + 10 * 2.2e-16 / s_min
+    np.testing.assert_allclose(np.tensordot(a, b, axes=([2], [0])),
+                               np.tensordot(a_ref, b_ref, axes=([2], [0])), atol=tol)
+    if move_right:
+        assert od.left_isometry_defect(a) < 1e-12
+    else:
+        assert od.right_isometry_defect(b) < 1e-12
+
+
+@pytest.mark.parametrize("n", [2, 37, 300, 1000])
+def test_sytrd_matches_lapack(ctx, n):
+    """osmps_sytrd (cooperative panels + emulated-GEMM trailing updates)
+    against LAPACK dsytrd: Q^T G Q = T with Q rebuilt from the stored
+    reflectors, the spectrum of T, and d, e, tau (same reflector convention)."""
+    from scipy.linalg import lapack
+    rng = np.random.default_rng(n)
+    M = rng.standard_normal((n, n))
+    G = M @ M.T
+    A = dev(G.copy())
+    d = torch.empty(n, dtype=torch.float64, device="cuda:0")
+    e = torch.empty(max(n - 1, 1), dtype=torch.float64, device="cuda:0")
+    tau = torch.empty(max(n - 1, 1), dtype=torch.float64, device="cuda:0")
+    B.osmps_sytrd(ctx, A, d, e, tau)
+    torch.cuda.synchronize()
+    Ah, dh, eh, th = A.cpu().numpy(), d.cpu().numpy(), e.cpu().numpy()[: n - 1], tau.cpu().numpy()[: n - 1]
+    T = np.diag(dh) + np.diag(eh, 1) + np.diag(eh, -1)
+    Q = np.eye(n)
+    for j in range(n - 1):  # Q = H(0) ... H(n-2); the reflector of column j is row j of Ah
+        v = np.zeros(n)
+        v[j + 1] = 1.0
+        v[j + 2:] = Ah[j, j + 2:]
+        Q = Q @ (np.eye(n) - th[j] * np.outer(v, v))
+    scale = np.abs(G).max()
+    assert np.abs(Q.T @ G @ Q - T).max() <= 1e-12 * scale
+    np.testing.assert_allclose(np.linalg.eigvalsh(T), np.linalg.eigvalsh(G), rtol=0, atol=1e-13 * scale)
+    _, dl, el, taul, _ = lapack.dsytrd(G.copy(order="F"), lower=1)
+    np.testing.assert_allclose(dh, dl, rtol=0, atol=1e-10 * scale)
+    np.testing.assert_allclose(np.abs(eh), np.abs(el), rtol=0, atol=1e-10 * scale)
