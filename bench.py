@@ -407,8 +407,12 @@ def sweep_leg(B, ctx, mpo, prec):
     p = B.sweep_params(CHI, 1, prec, lanczos_tol=LANCZOS_TOL, lanczos_max_iter=LANCZOS_CAP)
     torch.cuda.synchronize()
     st = B.osmps_sweep(ctx, mps, mpo, p, record_steps=False)
+    t0 = time.perf_counter()
+    E, V = B.osmps_variance(ctx, mps, mpo)
+    var_s = time.perf_counter() - t0
     mps.close()
     return {"seconds": st["sweep_seconds"], "steps": st["steps"], "lanczos_iters": st["lanczos_iters"],
+            "variance": V, "variance_seconds": var_s,
             "precision": prec, "energy_fp64": st["energy"], "setup_seconds": st["setup_seconds"],
             "energy_seconds": st["energy_seconds"],
             "note": "one left-right-left sweep; QR canonicalisation + environment build (setup) "

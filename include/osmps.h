@@ -334,6 +334,17 @@ osmps_status osmps_sweep(osmps_ctx* ctx, osmps_mps* mps, const osmps_mpo* mpo,
 osmps_status osmps_energy(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo* mpo,
                           double* energy_out, void* stream);
 
+/* Energy and variance of the MPS as it stands (Sec. 3.4 convergence
+ * parameters: V = <H^2> - <H>^2 of the normalised state). V is formed as
+ * <psi|(H - E)^2|psi> / <psi|psi> to avoid cancelling against E^2: the MPO
+ * of H - E (each site's local term, the block [start = w_l - 1, :, :, done =
+ * 0] of the nearest-neighbour MPO form, shifted by -E/L) is squared site by
+ * site and contracted with float64-accurate environment updates.
+ * Squared blocks w^2 d above 64 give EUNSUPPORTED. Host outputs
+ * (energy_out may be NULL). Synchronises `stream`.                          */
+osmps_status osmps_variance(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo* mpo,
+                            double* energy_out, double* variance_out, void* stream);
+
 /* Sweeps of many independent chains at once (the paper's data parallelism
  * over independent simulations, appendix "Convenient features", MPI item:
  * jobs are handed to workers one by one, largest systems first).

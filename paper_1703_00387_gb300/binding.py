@@ -95,6 +95,7 @@ _SIGS = {
                                     _c.POINTER(StepStats), _vp]),
     "osmps_sweep": (_c.c_int, [_vp, _vp, _vp, _c.POINTER(SweepParams), _c.POINTER(SweepStats), _vp]),
     "osmps_energy": (_c.c_int, [_vp, _vp, _vp, _dp, _vp]),
+    "osmps_variance": (_c.c_int, [_vp, _vp, _vp, _dp, _dp, _vp]),
     "osmps_mpo_set": (_c.c_int, [_vp, _c.POINTER(_dp)]),
     "osmps_heff_backward": (_c.c_int, [_vp] + [_vp] * 9 + [_i64] * 7 + [_c.c_int, _vp]),
     "osmps_energy_grad": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _c.c_int, _dp, _dp, _vp]),
@@ -553,3 +554,10 @@ def osmps_sytrd(ctx, A, d, e, tau, stream=None):
     n = A.shape[0]
     _check(lib().osmps_sytrd(ctx.ptr, _dev(A, "A"), n, _dev(d, "d"), _dev(e, "e"), _dev(tau, "tau"),
                              _stream(stream)))
+
+
+def osmps_variance(ctx, mps, mpo, stream=None):
+    """(E, V) of the MPS, V = <(H - E)^2>."""
+    e, v = _c.c_double(), _c.c_double()
+    _check(lib().osmps_variance(ctx.ptr, mps.ptr, mpo.ptr, _c.byref(e), _c.byref(v), _stream(stream)))
+    return e.value, v.value

@@ -91,6 +91,7 @@ enum Slot {
   SLOT_EMU_EXP,
   SLOT_EMU_MAX,
   SLOT_TRD,
+  SLOT_VAR,
   SLOT_EIG_X,
   SLOT_EIG_F32,
   SLOT_EIG_R,

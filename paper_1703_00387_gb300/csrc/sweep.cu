@@ -266,7 +266,7 @@ osmps_status two_site_step(osmps_ctx* ctx, osmps_mps* m, const osmps_mpo* h, int
 }
 
 osmps_status energy_impl(osmps_ctx* ctx, const osmps_mps* m, const osmps_mpo* h, double* E,
-                         cudaStream_t s) {
+                         cudaStream_t s, double* norm_out = nullptr) {
   osmps_status st = OSMPS_OK;
   int64_t maxsz = 1;
   for (int64_t k = 0; k <= m->L; ++k) maxsz = std::max(maxsz, m->chi[k] * m->chi[k] * h->w[k]);
@@ -292,6 +292,82 @@ osmps_status energy_impl(osmps_ctx* ctx, const osmps_mps* m, const osmps_mpo* h,
   OSMPS_CUDA(cudaStreamSynchronize(s));
   if (!(vals[1] > 0.0)) return set_error(OSMPS_ENAN, "energy: state norm %g", vals[1]);
   *E = vals[0] / vals[1];
+  if (norm_out) *norm_out = vals[1];
+  return OSMPS_OK;
+}
+
+// Site tensor of (H - c)^2 from W[a,t,u,x] (dims wl, d, d, wr):
+//   out[(a wl + b), t, s, (x wr + y)] = sum_u W'[a,t,u,x] W'[b,u,s,y],
+//   W' = W - (c / L) 1 on the local-term block [start = wl - 1, :, :, done = 0].
+__global__ void k_mpo_shift_square(const double* __restrict__ W, int wl, int d, int wr, double cl,
+                                   double* __restrict__ out) {
+  const int64_t total = (int64_t)wl * wl * d * d * wr * wr;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = e;
+    const int y = (int)(r % wr); r /= wr;
+    const int x = (int)(r % wr); r /= wr;
+    const int sx = (int)(r % d); r /= d;
+    const int t = (int)(r % d); r /= d;
+    const int b = (int)(r % wl);
+    const int a = (int)(r / wl);
+    double acc = 0.0;
+    for (int u = 0; u < d; ++u) {
+      double w1 = W[(((int64_t)a * d + t) * d + u) * wr + x];
+      double w2 = W[(((int64_t)b * d + u) * d + sx) * wr + y];
+      if (a == wl - 1 && x == 0 && t == u) w1 -= cl;
+      if (b == wl - 1 && y == 0 && u == sx) w2 -= cl;
+      acc = fma(w1, w2, acc);
+    }
+    out[e] = acc;
+  }
+}
+
+// V = <psi|(H - E)^2|psi> / <psi|psi> (Sec. 3.4 convergence parameters: the
+// variance of the state), formed without the cancellation of <H^2> - E^2:
+// E first, then the squared shifted MPO contracted with the state by
+// float64-accurate left environment updates.
+osmps_status variance_impl(osmps_ctx* ctx, const osmps_mps* m, const osmps_mpo* h, double* E,
+                           double* V, cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  double nrm = 0.0;
+  OSMPS_TRY(energy_impl(ctx, m, h, E, s, &nrm));
+  const int64_t L = m->L;
+  std::vector<int64_t> off(L + 1, 0);
+  int64_t maxsz = 1;
+  for (int64_t k = 0; k < L; ++k) {
+    const int64_t wl = h->w[k], wr = h->w[k + 1], d = h->d[k];
+    if (wl * wl * d > 64 || d * wr * wr > 64)
+      return set_error(OSMPS_EUNSUPPORTED, "variance: squared MPO block (w^2 d = %lld) above 64",
+                       (long long)std::max(wl * wl * d, d * wr * wr));
+    off[k + 1] = off[k] + wl * wl * d * d * wr * wr;
+  }
+  for (int64_t k = 0; k <= L; ++k) maxsz = std::max(maxsz, m->chi[k] * m->chi[k] * h->w[k] * h->w[k]);
+  double* W2 = (double*)ws_get(ctx, SLOT_VAR, (size_t)off[L] * 8, s, &st);
+  if (!W2) return st;
+  for (int64_t k = 0; k < L; ++k) {
+    const int64_t n = off[k + 1] - off[k];
+    { k_mpo_shift_square<<<(int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 4096)), 256, 0, s>>>(
+          h->W[k], (int)h->w[k], (int)h->d[k], (int)h->w[k + 1], *E / (double)L, W2 + off[k]); note_launch(); }
+  }
+  OSMPS_LAUNCH_CHECK();
+  double* e1 = (double*)ws_get(ctx, SLOT_SWEEP_ENV, (size_t)maxsz * 8, s, &st);
+  if (!e1) return st;
+  double* e2 = (double*)ws_get(ctx, SLOT_SWEEP_ENV2, (size_t)maxsz * 8, s, &st);
+  if (!e2) return st;
+  { k_fill<<<1, 32, 0, s>>>(e1, 1, 1.0); note_launch(); }
+  OSMPS_LAUNCH_CHECK();
+  double* a = e1;
+  double* b = e2;
+  for (int64_t k = 0; k < L; ++k) {
+    OSMPS_TRY(env_update_impl(ctx, 0, a, m->A[k], W2 + off[k], b, m->chi[k], m->d[k], m->chi[k + 1],
+                              h->w[k] * h->w[k], h->w[k + 1] * h->w[k + 1], OSMPS_PREC_FP64_EMU, s));
+    std::swap(a, b);
+  }
+  double v = 0.0;
+  OSMPS_CUDA(cudaMemcpyAsync(&v, a, 8, cudaMemcpyDeviceToHost, s));
+  OSMPS_CUDA(cudaStreamSynchronize(s));
+  *V = v / nrm;
   return OSMPS_OK;
 }
 
@@ -673,6 +749,20 @@ osmps_status osmps_energy_grad(osmps_ctx* ctx, const osmps_mps* mps, const osmps
                              (cudaStream_t)stream));
   if (energy_out) *energy_out = E;
   if (norm_out) *norm_out = nrm;
+  return OSMPS_OK;
+}
+
+osmps_status osmps_variance(osmps_ctx* ctx, const osmps_mps* mps, const osmps_mpo* mpo,
+                            double* energy_out, double* variance_out, void* stream) {
+  clear_error();
+  if (!ctx || !mps || !mpo || !variance_out) return set_error(OSMPS_EINVAL, "osmps_variance: null argument");
+  OSMPS_TRY(check_pair(mps, mpo));
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
+  double E = 0.0, V = 0.0;
+  OSMPS_TRY(variance_impl(ctx, mps, mpo, &E, &V, (cudaStream_t)stream));
+  if (energy_out) *energy_out = E;
+  *variance_out = V;
   return OSMPS_OK;
 }
 
