@@ -301,6 +301,7 @@ def run_ours(args, ws, rank, local):
         if not args.no_batch:
             line["batch_sweeps"] = batch_leg(B, args)
         line["u1_heff"] = u1_leg(B, ctx, args)
+        line["long_range_sweep"] = long_range_leg(B, ctx, args)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"], line["matvec_rel_err"] = cpu_leg(B, ctx, Wh)
     mps.close()
@@ -512,6 +513,26 @@ def u1_leg(B, ctx, args):
         op.close()
     return {"workload": "Bose-Hubbard J=1 U=4, L=64, N=64, n<=4 (d=5), w=4, chi=512 per bond "
                         "(13 sectors each), two-site H_eff.theta at sites 31,32", **out}
+
+
+def long_range_leg(B, ctx, args):
+    """Long-range transverse-field Ising chain (Eq. LRIsing), J=1, g=1,
+    alpha=1.5 written as 8 exponentials (MPO w=10), L=128, chi_max=256: one
+    left-right-left sweep from a seeded random MPS (split-precision
+    contractions, float64 Lanczos and split)."""
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+    L, chi = 128, 256
+    a, lam, err = hamiltonians.exponential_fit(lambda r: r ** -1.5, L - 1, 8)
+    mpo = B.MPO(ctx, hamiltonians.long_range_ising(L, 1.0, 1.0, a, lam))
+    mps = B.MPS(ctx, inputs.random_mps(L, D, chi, seed=5), chi_cap=chi)
+    st = B.osmps_sweep(ctx, mps, mpo, B.sweep_params(chi, 1, args.precision, lanczos_tol=LANCZOS_TOL,
+                                                     lanczos_max_iter=LANCZOS_CAP), record_steps=False)
+    mps.close()
+    mpo.close()
+    return {"workload": "long-range TFI J=1 g=1 alpha=1.5 (8 exponentials, w=10), L=128, chi_max=256",
+            "fit_max_error": err, "sweep_seconds": st["sweep_seconds"], "steps": st["steps"],
+            "lanczos_iters": st["lanczos_iters"], "energy_fp64": st["energy"],
+            "precision": args.precision}
 
 
 def cpu_leg(B, ctx, Wh):

@@ -135,3 +135,45 @@ def mpo_to_dense(W):
         acc = new.reshape(D_o * d_t, D_i * d_s, w2)
     assert acc.shape[2] == 1
     return acc[:, :, 0]
+
+
+def long_range_ising_mpo(L, J, g, amps, decays):
+    """Eq. LRIsing with the distance dependence f(r) = sum_k amps_k decays_k^r
+    (the paper's exponential rule: a channel per exponential whose diagonal
+    entry is the decay times the identity). Channel layout as in
+    nearest_neighbour_mpo: 0 'done', 1..K the open exponential terms, K+1
+    'start'."""
+    o = ops.spin_half()
+    K = len(amps)
+    w = K + 2
+    bulk = np.zeros((w, 2, 2, w))
+    bulk[0, :, :, 0] = o["id"]
+    bulk[w - 1, :, :, w - 1] = o["id"]
+    bulk[w - 1, :, :, 0] = -J * g * o["sigma_x"]
+    for c, (a, lam) in enumerate(zip(amps, decays)):
+        bulk[w - 1, :, :, 1 + c] = -J * a * lam * o["sigma_z"]   # open: amplitude and first decay
+        bulk[1 + c, :, :, 1 + c] = lam * o["id"]             # pass one more site
+        bulk[1 + c, :, :, 0] = o["sigma_z"]                       # close
+    W = [bulk.copy() for _ in range(L)]
+    W[0] = W[0][w - 1:w].copy()
+    W[-1] = W[-1][..., 0:1].copy()
+    return W
+
+
+def long_range_ising_dense(L, J, g, coupling):
+    """Dense Eq. LRIsing from its pair sum, coupling(r) for r = j - i."""
+    o = ops.spin_half()
+    dim = 2 ** L
+
+    def site_op(op, i):
+        out = np.array([[1.0]])
+        for k in range(L):
+            out = np.kron(out, op if k == i else o["id"])
+        return out
+
+    H = np.zeros((dim, dim))
+    for i in range(L):
+        H -= J * g * site_op(o["sigma_x"], i)
+        for j in range(i + 1, L):
+            H -= J * coupling(j - i) * site_op(o["sigma_z"], i) @ site_op(o["sigma_z"], j)
+    return H

@@ -152,3 +152,45 @@ def xxz_coupling_basis(L, delta=1.0):
         row_ptr.append(row_ptr[-1] + nz.size)
     return (W0, np.asarray(row_ptr, dtype=np.int64), np.concatenate(cols).astype(np.int64),
             np.concatenate(vals))
+
+
+def exponential_fit(f, rmax, n_exp):
+    """Amplitudes a_k and decays l_k with sum_k a_k l_k^r ~ f(r) for r = 1..rmax
+    (the paper expresses every infinite-range coupling as a sum of
+    exponentials): decays on a geometric grid of length scales from 1/2 to
+    rmax, amplitudes by linear least squares. Returns (a, l, max |error|)."""
+    r = np.arange(1, rmax + 1, dtype=np.float64)
+    scales = np.geomspace(0.5, max(float(rmax), 1.0), n_exp)
+    lam = np.exp(-1.0 / scales)
+    V = lam[None, :] ** r[:, None]
+    a, *_ = np.linalg.lstsq(V, f(r), rcond=None)
+    return a, lam, float(np.abs(V @ a - f(r)).max())
+
+
+def long_range_ising(L, J=1.0, g=1.0, amps=(), decays=()):
+    """Long-range transverse-field Ising chain (Eq. LRIsing) with the coupling
+    as a sum of exponentials, f(r) = sum_k amps_k decays_k^r:
+        H = -J sum_{i<j} f(j - i) sz_i sz_j - J g sum_i sx_i.
+    Channel 1 + k carries the term started by amps_k decays_k sz on the left
+    and multiplies by decays_k on every site it passes (the decay factor on
+    the MPO diagonal); sz closes it into 'done'. w = len(amps) + 2."""
+    o = _spin_half()
+    K = len(amps)
+    w = K + 2
+    done, start = 0, w - 1
+    out = []
+    for k in range(L):
+        W = np.zeros((w, 2, 2, w))
+        W[done, :, :, done] = o["1"]
+        W[start, :, :, start] = o["1"]
+        W[start, :, :, done] = -J * g * o["sx"]
+        for c in range(K):
+            W[start, :, :, 1 + c] = -J * amps[c] * decays[c] * o["sz"]
+            W[1 + c, :, :, 1 + c] = decays[c] * o["1"]
+            W[1 + c, :, :, done] = o["sz"]
+        if k == 0:
+            W = W[start:start + 1]
+        if k == L - 1:
+            W = W[..., done:done + 1]
+        out.append(np.ascontiguousarray(W))
+    return out

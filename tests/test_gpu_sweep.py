@@ -126,3 +126,16 @@ def test_fp64_emulated_sweep_matches_oracle(ctx):
     r = run_gpu(ctx, hamiltonians.xxz(L, 1.0, 1.0, 0.0), mps0, chi, 3, precision="fp64emu")
     E_ref, _, _ = od.dmrg(ompo.xxz_mpo(L, 1.0, 1.0, 0.0), mps0, chi, 3)
     assert abs(r["stats"]["energy"] - E_ref) <= 1e-10 * abs(E_ref)
+
+
+@pytest.mark.parametrize("precision,refine", [("fp64", 0), ("bf16x3", 1)])
+def test_long_range_ising_matches_exact(ctx, precision, refine):
+    """Eq. LRIsing, alpha = 1.5 fitted by 4 exponentials (MPO w = 6), L = 10 at
+    the exact bond dimension 32: the GPU ground energy equals exact
+    diagonalisation of the same MPO Hamiltonian to 1e-10."""
+    L = 10
+    a, lam, _ = hamiltonians.exponential_fit(lambda r: r ** -1.5, L - 1, 4)
+    E0 = np.linalg.eigvalsh(ompo.mpo_to_dense(ompo.long_range_ising_mpo(L, 1.0, 0.7, a, lam)))[0]
+    r = run_gpu(ctx, hamiltonians.long_range_ising(L, 1.0, 0.7, a, lam),
+                inputs.random_mps(L, 2, 32, seed=3), 32, 4, precision=precision, refine=refine)
+    assert abs(r["stats"]["energy"] - E0) <= 1e-10 * abs(E0)
