@@ -302,6 +302,7 @@ def run_ours(args, ws, rank, local):
             line["batch_sweeps"] = batch_leg(B, args)
         line["u1_heff"] = u1_leg(B, ctx, args)
         line["long_range_sweep"] = long_range_leg(B, ctx, args)
+        line["excited_state"] = excited_leg(B, ctx, args)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"], line["matvec_rel_err"] = cpu_leg(B, ctx, Wh)
     mps.close()
@@ -533,6 +534,35 @@ def long_range_leg(B, ctx, args):
             "fit_max_error": err, "sweep_seconds": st["sweep_seconds"], "steps": st["steps"],
             "lanczos_iters": st["lanczos_iters"], "energy_fp64": st["energy"],
             "precision": args.precision}
+
+
+def excited_leg(B, ctx, args):
+    """Excited-state search (eMPS) on the paper's example system, the
+    long-range Ising chain: L=32, J=1, g=1, alpha=1.5 as 3 exponentials (w=5),
+    chi_max=64. Ground state by 3 sweeps, first excited state by 4 projected
+    sweeps; seconds of each and the overlap of the two."""
+    import torch
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+    from paper_1703_00387_gb300.excited import excited_state
+    L, chi = 32, 64
+    a, lam, _ = hamiltonians.exponential_fit(lambda r: r ** -1.5, L - 1, 3)
+    W = hamiltonians.long_range_ising(L, 1.0, 1.0, a, lam)
+    mpo = B.MPO(ctx, W)
+    mps = B.MPS(ctx, inputs.random_mps(L, D, chi, seed=11), chi_cap=chi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = B.osmps_sweep(ctx, mps, mpo, B.sweep_params(chi, 3, "fp64", lanczos_tol=1e-12),
+                       record_steps=False)
+    t_ground = time.perf_counter() - t0
+    ground = mps.tensors()
+    mps.close()
+    mpo.close()
+    t0 = time.perf_counter()
+    r = excited_state(ctx, W, [ground], inputs.random_mps(L, D, chi, seed=12), chi, n_sweeps=4)
+    t_exc = time.perf_counter() - t0
+    return {"workload": "long-range TFI J=1 g=1 alpha=1.5 (3 exponentials, w=5), L=32, chi_max=64",
+            "ground_energy": st["energy"], "excited_energy": r["energy"],
+            "overlap": r["overlaps"][0], "ground_seconds": t_ground, "excited_seconds": t_exc}
 
 
 def cpu_leg(B, ctx, Wh):

@@ -364,6 +364,48 @@ osmps_status osmps_sweep_batch(osmps_ctx* const* ctxs, int n_workers, osmps_mps*
                                osmps_status* chain_status);
 
 /* ------------------------------------------------------------------------
+ * Excited states (Sec. 4.1 eMPS, Eq. emps_lagrange: Lagrange multipliers
+ * keep the state orthogonal to the lower eigenstates; locally, the Lanczos
+ * search runs in the orthogonal complement of the lower states' two-site
+ * blocks seen in the current basis).
+ * ---------------------------------------------------------------------- */
+
+/* osmps_lanczos_ground on H_eff restricted to the orthogonal complement of
+ * the k rows of P (k x n row-major device array, n = chi_l d1 d2 chi_r; any
+ * linearly independent rows, 0 <= k <= 64; copied and orthonormalised
+ * internally). theta_inout is projected into the complement first (EINVAL if
+ * it lies in the span of P). Other arguments and results as
+ * osmps_lanczos_ground.                                                    */
+osmps_status osmps_lanczos_ground_projected(osmps_ctx* ctx, const double* L, const double* W1,
+                                            const double* W2, const double* R,
+                                            double* theta_inout, const double* P, int k,
+                                            int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r,
+                                            int64_t wl, int64_t wm, int64_t wr, int max_iter,
+                                            double tol, int precision, double* energy_out,
+                                            int* iters_out, double* resid_out, void* stream);
+
+/* Overlap environment of the state being optimised (bra, site tensor A
+ * (chi_l, d, chi_r)) with a lower state (ket, site tensor Bk (chik_l, d,
+ * chik_r)), grown past one site (float64):
+ *   side 0: env_out[b2, bk] = sum A[a2, t, b2] env_in[a2, ak] Bk[ak, t, bk]
+ *           env_in (chi_l, chik_l), env_out (chi_r, chik_r)
+ *   side 1: env_out[a2, ak] = sum A[a2, t, b2] env_in[b2, bk] Bk[ak, t, bk]
+ *           env_in (chi_r, chik_r), env_out (chi_l, chik_l)                  */
+osmps_status osmps_overlap_env_update(osmps_ctx* ctx, int side, const double* env_in,
+                                      const double* A, const double* Bk, double* env_out,
+                                      int64_t chi_l, int64_t d, int64_t chi_r, int64_t chik_l,
+                                      int64_t chik_r, void* stream);
+
+/* The lower state's two-site block in the current basis:
+ *   v[a, s1, s2, c] = sum OL[a, ak] B1[ak, s1, m] B2[m, s2, ck] OR[c, ck]
+ * OL (chi_l, chik_l), B1 (chik_l, d1, chik_m), B2 (chik_m, d2, chik_r),
+ * OR (chi_r, chik_r), v (chi_l, d1, d2, chi_r) (float64).                  */
+osmps_status osmps_projected_state(osmps_ctx* ctx, const double* OL, const double* B1,
+                                   const double* B2, const double* OR, double* v, int64_t chi_l,
+                                   int64_t d1, int64_t d2, int64_t chi_r, int64_t chik_l,
+                                   int64_t chik_m, int64_t chik_r, void* stream);
+
+/* ------------------------------------------------------------------------
  * U(1)-symmetric H_eff . theta (Sec. 3.4 with a conserved particle number:
  * block-sparse tensors; every sector block of a GEMM stage in one grouped
  * tcgen05 launch).

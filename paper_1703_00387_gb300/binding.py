@@ -78,6 +78,11 @@ _SIGS = {
     "osmps_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_c.c_int, _vp]),
     "osmps_lanczos_ground": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 +
                              [_c.c_int, _c.c_double, _c.c_int, _dp, _c.POINTER(_c.c_int), _dp, _vp]),
+    "osmps_lanczos_ground_projected": (_c.c_int, [_vp] * 7 + [_c.c_int] + [_i64] * 7 +
+                                       [_c.c_int, _c.c_double, _c.c_int, _dp, _c.POINTER(_c.c_int),
+                                        _dp, _vp]),
+    "osmps_overlap_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_vp]),
+    "osmps_projected_state": (_c.c_int, [_vp] * 6 + [_i64] * 7 + [_vp]),
     "osmps_theta_form": (_c.c_int, [_vp, _vp, _vp, _vp] + [_i64] * 5 + [_vp]),
     "osmps_split": (_c.c_int, [_vp, _vp, _vp, _vp] + [_i64] * 4 +
                     [_c.c_int, _i64, _c.c_double, _c.POINTER(_i64), _dp, _dp, _dp, _c.c_int, _vp]),
@@ -561,3 +566,37 @@ def osmps_variance(ctx, mps, mpo, stream=None):
     e, v = _c.c_double(), _c.c_double()
     _check(lib().osmps_variance(ctx.ptr, mps.ptr, mpo.ptr, _c.byref(e), _c.byref(v), _stream(stream)))
     return e.value, v.value
+
+
+def osmps_lanczos_ground_projected(ctx, L, W1, W2, R, theta, P, max_iter=100, tol=1e-12,
+                                   precision="fp64", stream=None, allow_noconv=True):
+    """Lanczos in the orthogonal complement of the rows of P (k x n, or None)."""
+    chi_l, d1, d2, chi_r = theta.shape
+    wl, wm, wr = W1.shape[0], W1.shape[3], W2.shape[3]
+    k = 0 if P is None else P.shape[0]
+    e, it, res = _c.c_double(), _c.c_int(), _c.c_double()
+    st = lib().osmps_lanczos_ground_projected(
+        ctx.ptr, _dev(L, "L"), _dev(W1, "W1"), _dev(W2, "W2"), _dev(R, "R"), _dev(theta, "theta"),
+        _vp(0) if P is None else _dev(P, "P"), k, chi_l, d1, d2, chi_r, wl, wm, wr, int(max_iter),
+        float(tol), _prec(precision), _c.byref(e), _c.byref(it), _c.byref(res), _stream(stream))
+    _check(st, allow=(ENOCONV,) if allow_noconv else ())
+    return e.value, it.value, res.value, st == 0
+
+
+def osmps_overlap_env_update(ctx, side, env_in, A, Bk, env_out, stream=None):
+    chi_l, d, chi_r = A.shape
+    chik_l, _, chik_r = Bk.shape
+    _check(lib().osmps_overlap_env_update(ctx.ptr, int(side), _dev(env_in, "env_in"), _dev(A, "A"),
+                                          _dev(Bk, "Bk"), _dev(env_out, "env_out"), chi_l, d, chi_r,
+                                          chik_l, chik_r, _stream(stream)))
+    return env_out
+
+
+def osmps_projected_state(ctx, OL, B1, B2, OR, v, stream=None):
+    chi_l, d1, d2, chi_r = v.shape
+    chik_l, _, chik_m = B1.shape
+    chik_r = B2.shape[2]
+    _check(lib().osmps_projected_state(ctx.ptr, _dev(OL, "OL"), _dev(B1, "B1"), _dev(B2, "B2"),
+                                       _dev(OR, "OR"), _dev(v, "v"), chi_l, d1, d2, chi_r, chik_l,
+                                       chik_m, chik_r, _stream(stream)))
+    return v

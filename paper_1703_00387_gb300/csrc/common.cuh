@@ -73,6 +73,7 @@ enum Slot {
   SLOT_LZ_W,
   SLOT_LZ_SCAL,
   SLOT_LZ_PART,
+  SLOT_LZ_PROJ,
   SLOT_SPLIT_G,
   SLOT_SPLIT_EV,
   SLOT_SPLIT_WORK,
@@ -92,6 +93,7 @@ enum Slot {
   SLOT_EMU_MAX,
   SLOT_TRD,
   SLOT_VAR,
+  SLOT_OV_X,
   SLOT_EIG_X,
   SLOT_EIG_F32,
   SLOT_EIG_R,
@@ -331,7 +333,7 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
 using Matvec = std::function<osmps_status(const double* x, double* y)>;
 osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter, double tol,
                           const Matvec& matvec, double* energy, int* iters, double* resid,
-                          cudaStream_t s);
+                          cudaStream_t s, const double* P = nullptr, int64_t ldp = 0, int kp = 0);
 osmps_status theta_form_tc(osmps_ctx* ctx, const double* A1, const double* A2, double* theta,
                            int64_t chi_l, int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
                            int precision, cudaStream_t stream);

@@ -31,7 +31,9 @@ constexpr int OFF_C1 = 2 * MAXIT;
 constexpr int OFF_C2 = 3 * MAXIT;
 constexpr int OFF_S = 4 * MAXIT;
 constexpr int OFF_MISC = 5 * MAXIT;  // [0] e, [1] resid, [2] beta, [3] ||w||^2, [4] ||theta||^2
-constexpr int SCAL_COUNT = 5 * MAXIT + 16;
+constexpr int OFF_PROJ = 5 * MAXIT + 16;  // coefficients against the projector rows
+constexpr int MAX_PROJ = 64;
+constexpr int SCAL_COUNT = 5 * MAXIT + 16 + 2 * MAX_PROJ;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -312,7 +314,7 @@ osmps_status project(osmps_ctx* ctx, const double* V, int64_t ld, int64_t n, int
 
 osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter, double tol,
                           const Matvec& matvec, double* energy, int* iters, double* resid,
-                          cudaStream_t s) {
+                          cudaStream_t s, const double* P, int64_t ldp, int kp) {
   osmps_status st = OSMPS_OK;
   const int64_t ld = (n + 1) & ~(int64_t)1;  // even row stride: 16-byte aligned rows
   if (max_iter > n) max_iter = (int)n;
@@ -334,6 +336,16 @@ osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter
     return set_error(ctx->host_pinned[0] == 0.0 ? OSMPS_EINVAL : OSMPS_ENAN,
                      "lanczos: start vector has norm^2 %g", ctx->host_pinned[0]);
   OSMPS_CUDA(cudaMemcpyAsync(V, theta, n * 8, cudaMemcpyDeviceToDevice, s));
+  if (kp > 0) {
+    // start in the orthogonal complement of the projector rows (two passes)
+    OSMPS_TRY(project(ctx, P, ldp, n, kp, V, part, sc + OFF_PROJ, s));
+    OSMPS_TRY(project(ctx, P, ldp, n, kp, V, part, sc + OFF_PROJ + MAX_PROJ, s));
+    OSMPS_TRY(vec_norm2(ctx, V, n, sc + OFF_MISC + 4, s));
+    OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC + 4, 8, cudaMemcpyDeviceToHost, s));
+    OSMPS_CUDA(cudaStreamSynchronize(s));
+    if (!(ctx->host_pinned[0] > 0.0))
+      return set_error(OSMPS_EINVAL, "lanczos: start vector lies in the span of the projector rows");
+  }
   OSMPS_TRY(vec_scale_by_inv_sqrt(V, n, sc + OFF_MISC + 4, s));
 
   int m = 0;
@@ -342,6 +354,10 @@ osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter
   for (int j = 0; j < max_iter; ++j) {
     double* vj = V + (int64_t)j * ld;
     OSMPS_TRY(matvec(vj, w));
+    if (kp > 0) {  // the operator restricted to the complement: w <- (1 - P^T P) H v_j
+      OSMPS_TRY(project(ctx, P, ldp, n, kp, w, part, sc + OFF_PROJ, s));
+      OSMPS_TRY(project(ctx, P, ldp, n, kp, w, part, sc + OFF_PROJ + MAX_PROJ, s));
+    }
     OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C1, s));
     OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C2, s));
     OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, s));
@@ -425,3 +441,65 @@ extern "C" osmps_status osmps_lanczos_ground(osmps_ctx* ctx, const double* L, co
   return lanczos_impl(ctx, L, W1, W2, R, theta_inout, chi_l, d1, d2, chi_r, wl, wm, wr, max_iter,
                       tol, precision, energy_out, iters_out, resid_out, (cudaStream_t)stream);
 }
+
+// Lanczos on the operator restricted to the orthogonal complement of k given
+// vectors (the local problem of the excited-state search, Sec. 4.1 eMPS,
+// Eq. emps_lagrange: the Lagrange multipliers keep the state orthogonal to
+// the lower eigenstates). The rows of P are copied, orthonormalised (two
+// Gram-Schmidt passes each) and used as the projector.
+extern "C" osmps_status osmps_lanczos_ground_projected(
+    osmps_ctx* ctx, const double* L, const double* W1, const double* W2, const double* R,
+    double* theta_inout, const double* P, int k, int64_t chi_l, int64_t d1, int64_t d2,
+    int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int max_iter, double tol, int precision,
+    double* energy_out, int* iters_out, double* resid_out, void* stream) {
+  clear_error();
+  if (!ctx || !L || !W1 || !W2 || !R || !theta_inout || !energy_out || !iters_out || (k > 0 && !P))
+    return set_error(OSMPS_EINVAL, "osmps_lanczos_ground_projected: null argument");
+  if (k < 0 || k > MAX_PROJ) return set_error(OSMPS_EINVAL, "osmps_lanczos_ground_projected: k=%d outside [0, %d]", k, MAX_PROJ);
+  if (max_iter < 1 || max_iter > MAXIT)
+    return set_error(OSMPS_EINVAL, "osmps_lanczos_ground_projected: max_iter %d", max_iter);
+  if (!(tol >= 0.0)) return set_error(OSMPS_EINVAL, "osmps_lanczos_ground_projected: tol %g", tol);
+  if (!valid_precision(precision))
+    return set_error(OSMPS_EINVAL, "osmps_lanczos_ground_projected: precision %d", precision);
+  for (int64_t x : {chi_l, d1, d2, chi_r, wl, wm, wr})
+    if (x <= 0 || x > ((int64_t)1 << 31))
+      return set_error(OSMPS_ESHAPE, "osmps_lanczos_ground_projected: bad dimension");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
+  cudaStream_t s = (cudaStream_t)stream;
+  osmps_status st = OSMPS_OK;
+  const int64_t n = chi_l * d1 * d2 * chi_r;
+  const int64_t ld = (n + 1) & ~(int64_t)1;
+  double* Q = nullptr;
+  if (k > 0) {
+    Q = (double*)ws_get(ctx, SLOT_LZ_PROJ, (size_t)k * ld * 8, s, &st);
+    if (!Q) return st;
+    double* part = (double*)ws_get(ctx, SLOT_LZ_PART, (size_t)MAXIT * DOT_MAX_BLOCKS * 8, s, &st);
+    if (!part) return st;
+    double* sc = (double*)ws_get(ctx, SLOT_LZ_SCAL, SCAL_COUNT * 8, s, &st);
+    if (!sc) return st;
+    OSMPS_TRY(pinned_reserve(ctx, 16));
+    for (int i = 0; i < k; ++i) {
+      double* qi = Q + (int64_t)i * ld;
+      OSMPS_CUDA(cudaMemcpyAsync(qi, P + (int64_t)i * n, n * 8, cudaMemcpyDeviceToDevice, s));
+      if (i > 0) {
+        OSMPS_TRY(project(ctx, Q, ld, n, i, qi, part, sc + OFF_PROJ, s));
+        OSMPS_TRY(project(ctx, Q, ld, n, i, qi, part, sc + OFF_PROJ + MAX_PROJ, s));
+      }
+      OSMPS_TRY(vec_norm2(ctx, qi, n, sc + OFF_MISC + 5, s));
+      OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC + 5, 8, cudaMemcpyDeviceToHost, s));
+      OSMPS_CUDA(cudaStreamSynchronize(s));
+      if (!(ctx->host_pinned[0] > 1e-300))
+        return set_error(OSMPS_EINVAL, "osmps_lanczos_ground_projected: projector row %d is dependent", i);
+      OSMPS_TRY(vec_scale_by_inv_sqrt(qi, n, sc + OFF_MISC + 5, s));
+    }
+  }
+  OSMPS_TRY(heff_prepare(ctx, L, W1, W2, R, chi_l, d1, d2, chi_r, wl, wm, wr, precision, s));
+  const Matvec mv = [&](const double* x, double* y) {
+    return heff_apply_impl(ctx, nullptr, nullptr, nullptr, nullptr, x, y, chi_l, d1, d2, chi_r,
+                           wl, wm, wr, precision, s, true);
+  };
+  return lanczos_core(ctx, n, theta_inout, max_iter, tol, mv, energy_out, iters_out, resid_out, s,
+                      Q, ld, k);
+}
+
