@@ -303,6 +303,7 @@ def run_ours(args, ws, rank, local):
         line["u1_heff"] = u1_leg(B, ctx, args)
         line["long_range_sweep"] = long_range_leg(B, ctx, args)
         line["excited_state"] = excited_leg(B, ctx, args)
+        line["gradients"] = grad_leg(B, ctx, args)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"], line["matvec_rel_err"] = cpu_leg(B, ctx, Wh)
     mps.close()
@@ -538,15 +539,17 @@ def long_range_leg(B, ctx, args):
 
 def excited_leg(B, ctx, args):
     """Excited-state search (eMPS) on the paper's example system, the
-    long-range Ising chain: L=32, J=1, g=1, alpha=1.5 as 3 exponentials (w=5),
-    chi_max=64. Ground state by 3 sweeps, first excited state by 4 projected
-    sweeps; seconds of each and the overlap of the two."""
+    long-range Ising chain: L=32, J=1, g=4 (paramagnetic, gapped; at g=1 the
+    chain is ordered and the first excited state is the other member of the
+    ground doublet), alpha=1.5 as 3 exponentials (w=5), chi_max=64. Ground
+    state by 3 sweeps, first excited state by 4 projected sweeps; seconds of
+    each and the overlap of the two."""
     import torch
     from paper_1703_00387_gb300 import hamiltonians, inputs
     from paper_1703_00387_gb300.excited import excited_state
     L, chi = 32, 64
     a, lam, _ = hamiltonians.exponential_fit(lambda r: r ** -1.5, L - 1, 3)
-    W = hamiltonians.long_range_ising(L, 1.0, 1.0, a, lam)
+    W = hamiltonians.long_range_ising(L, 1.0, 4.0, a, lam)
     mpo = B.MPO(ctx, W)
     mps = B.MPS(ctx, inputs.random_mps(L, D, chi, seed=11), chi_cap=chi)
     torch.cuda.synchronize()
@@ -560,9 +563,58 @@ def excited_leg(B, ctx, args):
     t0 = time.perf_counter()
     r = excited_state(ctx, W, [ground], inputs.random_mps(L, D, chi, seed=12), chi, n_sweeps=4)
     t_exc = time.perf_counter() - t0
-    return {"workload": "long-range TFI J=1 g=1 alpha=1.5 (3 exponentials, w=5), L=32, chi_max=64",
+    return {"workload": "long-range TFI J=1 g=4 alpha=1.5 (3 exponentials, w=5), L=32, chi_max=64",
             "ground_energy": st["energy"], "excited_energy": r["energy"],
             "overlap": r["overlaps"][0], "ground_seconds": t_ground, "excited_seconds": t_exc}
+
+
+def grad_leg(B, ctx, args):
+    """Config 5 (differentiation): XXZ L=64, chi=256, J_i in [0.8, 1.2], h_i in
+    [-0.5, 0.5] from seed 0. Times of the H_eff.theta backward at chi=256
+    (g_theta, g_W1, g_W2) and of the energy gradient dE/d(J, h) with
+    checkpointed right environments; the gradient of one coupling against a
+    central difference of the energy with step 1e-6."""
+    import torch
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+    from paper_1703_00387_gb300.autograd import xxz_energy
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ops = inputs.random_heff_operands(256, 2, 2, 256, 5, 5, 5, seed=256)
+    t = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in ops]
+    gy = torch.from_numpy(np.random.default_rng(257).standard_normal(ops[4].shape)).to(dev)
+    out = {}
+    for prec in ("bf16x3", "fp64emu"):
+        gt, g1, g2 = torch.empty_like(t[4]), torch.empty_like(t[1]), torch.empty_like(t[2])
+        B.osmps_heff_backward(ctx, *t[:4], t[4], gy, gt, g1, g2, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            B.osmps_heff_backward(ctx, *t[:4], t[4], gy, gt, g1, g2, precision=prec)
+        torch.cuda.synchronize()
+        out[f"heff_backward_ms_{prec}"] = 1e3 * (time.perf_counter() - t0) / 5
+    L = 64
+    J, h = inputs.random_couplings(L, seed=0)
+    mps = B.MPS(ctx, inputs.random_mps(L, 2, 256, seed=0), chi_cap=256)
+    model = xxz_energy(ctx, mps, L, delta=1.0, checkpoint_every=8)
+    p = torch.tensor(np.concatenate([J, h]), dtype=torch.float64, device=dev, requires_grad=True)
+    model(p).backward()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = model.coupling_grad()
+    torch.cuda.synchronize()
+    out["energy_grad_seconds"] = time.perf_counter() - t0
+    j = 10
+    e = []
+    for sgn in (1.0, -1.0):
+        q = np.concatenate([J, h])
+        q[j] += sgn * 1e-6
+        e.append(model(torch.tensor(q, dtype=torch.float64, device=dev)).item())
+    fd = (e[0] - e[1]) / 2e-6
+    out["fd_check"] = {"coupling": "J_10", "gradient": float(g[j]), "central_difference": fd,
+                       "abs_error": abs(fd - float(g[j]))}
+    mps.close()
+    out["workload"] = ("XXZ Delta=1, L=64, chi=256, J_i ~ U[0.8,1.2], h_i ~ U[-0.5,0.5] (seed 0); "
+                       "H_eff backward at chi_l=chi_r=256, w=5")
+    return out
 
 
 def cpu_leg(B, ctx, Wh):
