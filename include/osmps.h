@@ -78,13 +78,36 @@ osmps_status osmps_ctx_destroy(osmps_ctx* ctx);
  *   OSMPS_EIG_AUTO     (default) the faster of the two as measured at
  *                      chi = 1024 on GB300: currently cuSOLVER;
  *   OSMPS_EIG_CUSOLVER cuSOLVER dsyevd / dsyevdx (largest pairs) always;
- *   OSMPS_EIG_TRIDIAG  Householder reduction (cuSOLVER dsytrd), then this
- *                      library's bisection, inverse iteration, Cholesky QR and
- *                      blocked back-transformation (float64-accurate emulated
- *                      GEMMs) for every Gram dimension >= 2.
+ *   OSMPS_EIG_TRIDIAG  this library's Householder reduction (osmps_sytrd;
+ *                      cuSOLVER dsytrd above n = 8192), bisection, inverse
+ *                      iteration, Cholesky QR and blocked back-transformation
+ *                      (float64-accurate emulated GEMMs) for every Gram
+ *                      dimension >= 2.
  * Both are float64-accurate. EINVAL for another value.                      */
 typedef enum { OSMPS_EIG_AUTO = 0, OSMPS_EIG_CUSOLVER = 1, OSMPS_EIG_TRIDIAG = 2 } osmps_eig_solver;
 osmps_status osmps_ctx_set_eig_solver(osmps_ctx* ctx, int solver);
+/* How Lanczos (osmps_lanczos_ground, its projected and U(1) forms, and the
+ * sweeps) drives its steps:
+ *   OSMPS_LANCZOS_HOST  the host launches every step and reads the Ritz
+ *                       value, residual estimate and beta after each one;
+ *   OSMPS_LANCZOS_GRAPH the first step runs as above without the read; the
+ *                       remaining steps are one CUDA graph whose conditional
+ *                       while-node repeats the recorded step until the device
+ *                       takes the same stopping decision (at most max_iter
+ *                       steps in all); the host synchronises once at the end.
+ *                       The graph is kept in the context and replayed by later
+ *                       calls with the same operator shape and parameters (up
+ *                       to 16 graphs, least recently used dropped first);
+ *   OSMPS_LANCZOS_AUTO  (default) the graph for Krylov vectors of at most
+ *                       2^20 entries, the host loop above that (where the
+ *                       products take milliseconds) and on the worker threads
+ *                       of osmps_sweep_batch (where many streams run at once
+ *                       and the host loop measured faster).
+ * Both run the same kernels on the same data and give bit-identical results.
+ * The graph is not used while kernel profiling is on, nor for max_iter = 1.
+ * A context serves one host thread at a time. EINVAL for another value.     */
+typedef enum { OSMPS_LANCZOS_AUTO = 0, OSMPS_LANCZOS_HOST = 1, OSMPS_LANCZOS_GRAPH = 2 } osmps_lanczos_mode;
+osmps_status osmps_ctx_set_lanczos_mode(osmps_ctx* ctx, int mode);
 /* Bytes of device memory currently held by the context's workspace.         */
 size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx);
 

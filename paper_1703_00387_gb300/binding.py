@@ -68,6 +68,7 @@ _SIGS = {
     "osmps_ctx_destroy": (_c.c_int, [_vp]),
     "osmps_ctx_workspace_bytes": (_c.c_size_t, [_vp]),
     "osmps_ctx_set_eig_solver": (_c.c_int, [_vp, _c.c_int]),
+    "osmps_ctx_set_lanczos_mode": (_c.c_int, [_vp, _c.c_int]),
     "osmps_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "osmps_profile_read": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_i64), _dp, _dp, _dp]),
     "osmps_kernel_launches": (_i64, []),
@@ -178,6 +179,13 @@ class Context:
         """'auto', 'cusolver' or 'tridiag' (the split's float64 eigensolver)."""
         code = {"auto": 0, "cusolver": 1, "tridiag": 2}[solver] if isinstance(solver, str) else int(solver)
         _check(lib().osmps_ctx_set_eig_solver(self.ptr, code))
+
+    def set_lanczos_mode(self, mode):
+        """'auto', 'host' or 'graph': how Lanczos drives its steps (a host loop
+        reading the stopping decision after every step, or one CUDA graph
+        whose while-node repeats the recorded step on the device)."""
+        code = {"auto": 0, "host": 1, "graph": 2}[mode] if isinstance(mode, str) else int(mode)
+        _check(lib().osmps_ctx_set_lanczos_mode(self.ptr, code))
 
     def workspace_bytes(self):
         return int(lib().osmps_ctx_workspace_bytes(self.ptr))

@@ -93,6 +93,7 @@ extern "C" osmps_status osmps_sweep_batch(osmps_ctx* const* ctxs, int n_workers,
       fail(OSMPS_ECUDA, "osmps_sweep_batch: cudaSetDevice failed in a worker");
       return;
     }
+    set_batch_worker(true);  // Lanczos in OSMPS_LANCZOS_AUTO keeps the host loop here
     cudaStream_t s = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
       fail(OSMPS_ECUDA, "osmps_sweep_batch: stream creation failed");

@@ -74,6 +74,7 @@ enum Slot {
   SLOT_LZ_SCAL,
   SLOT_LZ_PART,
   SLOT_LZ_PROJ,
+  SLOT_LZ_X,
   SLOT_SPLIT_G,
   SLOT_SPLIT_EV,
   SLOT_SPLIT_WORK,
@@ -142,6 +143,25 @@ struct osmps_ctx {
   int64_t heff_dims[7] = {0, 0, 0, 0, 0, 0, 0};
   // eigensolver of the split: OSMPS_EIG_AUTO / OSMPS_EIG_CUSOLVER / OSMPS_EIG_TRIDIAG
   int eig_solver = 0;
+  // Lanczos iteration driver: OSMPS_LANCZOS_AUTO / OSMPS_LANCZOS_HOST / OSMPS_LANCZOS_GRAPH
+  int lanczos_mode = 0;
+  // stream used only to record CUDA graphs (created on first use), and a flag
+  // that makes workspace growth an error while a capture is open
+  cudaStream_t capture_stream = nullptr;
+  bool capturing = false;
+  // Recorded Lanczos step graphs kept for replay (lanczos.cu), least recently
+  // used first out, and a count of workspace (re)allocations that every
+  // graph's key includes (a graph holds workspace addresses).
+  struct LzGraph {
+    std::vector<long long> key;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    long long body_launches = 0;
+    unsigned long long last_use = 0;
+  };
+  std::vector<LzGraph> lz_graphs;
+  unsigned long long lz_clock = 0;
+  unsigned long long ws_epoch = 0;
 };
 
 namespace osmps {
@@ -164,6 +184,15 @@ void prof_end(int handle, cudaStream_t stream, int kernel, double flops, double 
 
 // Count of kernels this library has launched (all threads, all contexts).
 void note_launch();
+// Add k launches that ran as nodes of a replayed CUDA graph (k may be
+// negative to take back a count made while recording).
+void note_launches(long long k);
+// Launches made by the calling thread so far.
+long long thread_launch_count();
+// Set by the batch scheduler on its worker threads (OSMPS_LANCZOS_AUTO then
+// keeps the host loop: see lanczos.cu).
+void set_batch_worker(bool on);
+bool is_batch_worker();
 
 // Ensure the pinned host staging area holds `count` doubles.
 osmps_status pinned_reserve(osmps_ctx* ctx, size_t count);
@@ -327,13 +356,22 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
                           int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int max_iter,
                           double tol, int precision, double* energy, int* iters, double* resid,
                           cudaStream_t stream);
-// Lanczos ground state of a symmetric operator given as y = A x (device
+// y = H x on stream q. Inside the Lanczos step graph the calls are recorded
+// by stream capture: launches only, no allocation, no synchronisation.
+using Matvec = std::function<osmps_status(const double* x, double* y, cudaStream_t q)>;
+// Lanczos ground state of a symmetric operator given as a Matvec (device
 // vectors of length n, work launched on s). Float64 Krylov basis with full
 // reorthogonalisation; theta is the start vector and receives the Ritz vector.
-using Matvec = std::function<osmps_status(const double* x, double* y)>;
+// P (kp rows, stride ldp): orthonormal rows whose span the search avoids.
+// mkey[0..nmkey): identifies everything the matvec's launches depend on
+// besides workspace addresses (shapes, precision, operator identity); with
+// it, the recorded step graph is kept in the context and replayed by later
+// calls with the same key. Without it (nmkey = 0) the graph is recorded for
+// this call only.
 osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter, double tol,
                           const Matvec& matvec, double* energy, int* iters, double* resid,
-                          cudaStream_t s, const double* P = nullptr, int64_t ldp = 0, int kp = 0);
+                          cudaStream_t s, const double* P = nullptr, int64_t ldp = 0, int kp = 0,
+                          const long long* mkey = nullptr, int nmkey = 0);
 osmps_status theta_form_tc(osmps_ctx* ctx, const double* A1, const double* A2, double* theta,
                            int64_t chi_l, int64_t d1, int64_t chi_m, int64_t d2, int64_t chi_r,
                            int precision, cudaStream_t stream);

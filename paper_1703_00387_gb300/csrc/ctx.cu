@@ -23,6 +23,11 @@ void* ws_get(osmps_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, osmps
   Buffer& b = ctx->slots[slot];
   if (bytes == 0) bytes = 256;
   if (b.bytes >= bytes) return b.ptr;
+  if (ctx->capturing) {
+    *st = set_error(OSMPS_EUNSUPPORTED, "workspace slot %d would grow inside a CUDA graph capture",
+                    (int)slot);
+    return nullptr;
+  }
   size_t want = bytes + bytes / 8;
   want = (want + 255) & ~size_t(255);
   if (b.ptr) {
@@ -45,13 +50,27 @@ void* ws_get(osmps_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, osmps
   }
   b.ptr = p;
   b.bytes = want;
+  ++ctx->ws_epoch;
   return p;
 }
 
 static thread_local osmps_ctx* g_cur = nullptr;
 static std::atomic<long long> g_launches{0};
 
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;
+static thread_local bool t_batch_worker = false;
+
+void note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void note_launches(long long k) {
+  g_launches.fetch_add(k, std::memory_order_relaxed);
+  t_launches += k;
+}
+long long thread_launch_count() { return t_launches; }
+void set_batch_worker(bool on) { t_batch_worker = on; }
+bool is_batch_worker() { return t_batch_worker; }
 
 CtxScope::CtxScope(osmps_ctx* c) : prev(g_cur) { g_cur = c; }
 CtxScope::~CtxScope() { g_cur = prev; }
@@ -303,6 +322,11 @@ osmps_status osmps_ctx_destroy(osmps_ctx* ctx) {
   if (ctx->dev_info) cudaFree(ctx->dev_info);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  for (auto& gr : ctx->lz_graphs) {
+    if (gr.e) cudaGraphExecDestroy(gr.e);
+    if (gr.g) cudaGraphDestroy(gr.g);
+  }
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
   return OSMPS_OK;
 }
@@ -363,5 +387,14 @@ extern "C" osmps_status osmps_ctx_set_eig_solver(osmps_ctx* ctx, int solver) {
   if (solver < OSMPS_EIG_AUTO || solver > OSMPS_EIG_TRIDIAG)
     return osmps::set_error(OSMPS_EINVAL, "osmps_ctx_set_eig_solver: solver %d", solver);
   ctx->eig_solver = solver;
+  return OSMPS_OK;
+}
+
+extern "C" osmps_status osmps_ctx_set_lanczos_mode(osmps_ctx* ctx, int mode) {
+  osmps::clear_error();
+  if (!ctx) return osmps::set_error(OSMPS_EINVAL, "osmps_ctx_set_lanczos_mode: null context");
+  if (mode < OSMPS_LANCZOS_AUTO || mode > OSMPS_LANCZOS_GRAPH)
+    return osmps::set_error(OSMPS_EINVAL, "osmps_ctx_set_lanczos_mode: mode %d", mode);
+  ctx->lanczos_mode = mode;
   return OSMPS_OK;
 }

@@ -6,14 +6,21 @@
 // the result against every stored Krylov vector twice (classical
 // Gram-Schmidt, two passes: full reorthogonalisation), normalises, and
 // solves the small tridiagonal problem for the lowest Ritz pair:
-//   * the eigenvalue by Sturm-count multisection (32 points per round, one warp),
+//   * the eigenvalue by Sturm-count multisection (64 points per round, one warp),
 //   * its eigenvector by inverse iteration with a partially pivoted
 //     tridiagonal LU (Gaussian elimination with row interchanges).
-// The host reads three numbers per step (energy, residual estimate, beta)
-// to decide whether to stop: residual estimate beta_j |s_j| <= tol.
+// The stopping test (residual estimate beta_j |s_j| <= tol, the iteration
+// cap, an exhausted Krylov space) is taken on the device, by the kernel that
+// solves the tridiagonal problem, and kept with the index of the current
+// Krylov vector in device memory. So one step is the same sequence of
+// launches whatever the step number, and the steps can run either from a
+// host loop that reads the decision after each step or as one CUDA graph
+// whose conditional while-node repeats the recorded step on the device.
 #include <cmath>
+#include <cstring>
 
 #include "common.cuh"
+#include "sturm.cuh"
 
 namespace osmps {
 
@@ -31,9 +38,26 @@ constexpr int OFF_C1 = 2 * MAXIT;
 constexpr int OFF_C2 = 3 * MAXIT;
 constexpr int OFF_S = 4 * MAXIT;
 constexpr int OFF_MISC = 5 * MAXIT;  // [0] e, [1] resid, [2] beta, [3] ||w||^2, [4] ||theta||^2
+constexpr int OFF_STATE = OFF_MISC + 8;  // 4 ints in two double slots, below
 constexpr int OFF_PROJ = 5 * MAXIT + 16;  // coefficients against the projector rows
 constexpr int MAX_PROJ = 64;
 constexpr int SCAL_COUNT = 5 * MAXIT + 16 + 2 * MAX_PROJ;
+constexpr int MISC_READ = 10;  // doubles of OFF_MISC the host reads (the state included)
+
+// Iteration state (ints at OFF_STATE): the index J of the Krylov vector the
+// next step applies H_eff to, the stop code, and the number of Krylov vectors
+// the Ritz vector combines.
+constexpr int ST_J = 0, ST_STOP = 1, ST_M = 2;
+constexpr int STOP_NONE = 0, STOP_CONVERGED = 1, STOP_CAP = 2, STOP_NONFINITE = 3;
+
+__host__ __device__ inline int* lz_state(double* sc) { return reinterpret_cast<int*>(sc + OFF_STATE); }
+__host__ __device__ inline const int* lz_state(const double* sc) {
+  return reinterpret_cast<const int*>(sc + OFF_STATE);
+}
+// The state inside a host copy of the MISC_READ doubles from OFF_MISC on.
+inline const int* lz_state_in_misc(const double* misc) {
+  return reinterpret_cast<const int*>(misc + (OFF_STATE - OFF_MISC));
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -88,10 +112,13 @@ __device__ __forceinline__ void multidot_group(const double* __restrict__ V, int
 
 // part[i * nb + b] = sum over block b's elements of V[i][e] * w[e], i < nv:
 // groups of DOT_GROUP vectors, then one group of the remainder.
+// With jcur set, nv = jcur[0] + 1 (the Krylov vectors up to the current one).
 __global__ void __launch_bounds__(DOT_THREADS, 3) k_multidot(const double* __restrict__ V, int64_t ld,
                                                           int nv, const double* __restrict__ w,
-                                                          int64_t n, double* __restrict__ part) {
+                                                          int64_t n, double* __restrict__ part,
+                                                          const int* __restrict__ jcur) {
   __shared__ double sh[DOT_THREADS / 32][DOT_GROUP];
+  if (jcur) nv = jcur[0] + 1;
   int g0 = 0;
   for (; g0 + DOT_GROUP <= nv; g0 += DOT_GROUP) multidot_group<DOT_GROUP>(V, ld, g0, w, n, part, sh);
   switch (nv - g0) {
@@ -106,9 +133,12 @@ __global__ void __launch_bounds__(DOT_THREADS, 3) k_multidot(const double* __res
   }
 }
 
-// out[i] = sum_b part[i * nb + b] in a fixed order (one block per vector).
-__global__ void k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+// out[i] = sum_b part[i * nb + b] in a fixed order (one block per vector;
+// with jcur set, blocks past vector jcur[0] return at once).
+__global__ void k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ out,
+                                 const int* __restrict__ jcur) {
   __shared__ double sh[32];
+  if (jcur && (int)blockIdx.x > jcur[0]) return;
   double s = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)blockIdx.x * nb + b];
   s = warp_sum(s);
@@ -126,8 +156,9 @@ __global__ void k_multidot_final(const double* __restrict__ part, int nb, double
 // 256-byte aligned with an even stride).
 __global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
                           const double* __restrict__ c, double* __restrict__ w, int64_t n,
-                          int mode) {
+                          int mode, const int* __restrict__ jcur) {
   __shared__ double cs[MAXIT];
+  if (jcur) nv = jcur[0] + 1;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = c[i];
   __syncthreads();
   const int64_t n2 = n >> 1;
@@ -154,10 +185,16 @@ __global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
   }
 }
 
-// x[e] = sum_i c[i] V[i][e] into an arbitrary (8-byte aligned) caller buffer.
-__global__ void k_combine_scalar(const double* __restrict__ V, int64_t ld, int nv,
-                                 const double* __restrict__ c, double* __restrict__ x, int64_t n) {
+// The Ritz vector x[e] = sum_i s[i] V[i][e], i < m (the state's vector
+// count), into an arbitrary (8-byte aligned) caller buffer; x is left as it
+// is when the iteration stopped on a non-finite value.
+__global__ void k_combine_scalar(const double* __restrict__ V, int64_t ld,
+                                 const double* __restrict__ sc, double* __restrict__ x, int64_t n) {
   __shared__ double cs[MAXIT];
+  const int* st = lz_state(sc);
+  if (st[ST_STOP] == STOP_NONFINITE) return;
+  const int nv = st[ST_M];
+  const double* c = sc + OFF_S;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = c[i];
   __syncthreads();
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -168,27 +205,42 @@ __global__ void k_combine_scalar(const double* __restrict__ V, int64_t ld, int n
   }
 }
 
-__device__ int sturm_count(const double* a, const double* b, int m, double x) {
-  // number of eigenvalues of the tridiagonal (a, b) below x
-  int cnt = 0;
-  double q = a[0] - x;
-  if (q < 0.0) ++cnt;
-  for (int i = 1; i < m; ++i) {
-    if (q == 0.0) q = 1e-300;
-    q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
-    if (q < 0.0) ++cnt;
-  }
-  return cnt;
-}
-
-// Record alpha_j, beta_j, then the lowest eigenpair of T_{j+1}; one warp.
-// Eigenvalue: Sturm-count multisection, 32 points per round (5 bits).
-// Eigenvector: inverse iteration (3 solves) with a partially pivoted
-// tridiagonal LU, run by lane 0.
-__global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int j) {
-  __shared__ double a[MAXIT], b[MAXIT], x[MAXIT], dl[MAXIT], dd[MAXIT], du[MAXIT];
-  const int m = j + 1;
+// Step j = state J: record alpha_j, beta_j, then the lowest eigenpair of
+// T_{j+1}; one warp.
+//   * Eigenvalue: multisection on division-free Sturm counts (sturm.cuh),
+//     64 points per round (two per lane, independent chains), from the
+//     Gershgorin interval down to 4e-16 relative width.
+//   * Eigenvector: inverse iteration, three solves from a flat start with one
+//     partially pivoted LU factorisation of T - e I (Gaussian elimination
+//     with row interchanges, lane 0); the reciprocals of the pivots are taken
+//     once, in parallel across the warp, so the solves are multiply-adds only.
+// A dependent float64 operation costs tens of cycles on this GPU and a
+// division hundreds, so the per-call chain holds one run of m divisions (the
+// factorisation) and none in the multisection.
+// Then the stopping decision: a non-finite Ritz value or residual; converged
+// (residual estimate <= tol, beta = 0, or the Krylov space is the whole
+// space); the step cap. Without a stop, J advances. With set_cond, the
+// decision is also the loop condition of the CUDA graph this kernel runs in
+// (1 = run another step), so a graph loop ends after at most max_iter steps:
+// J only advances below max_iter - 1.
+__global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int max_iter, double tol,
+                                                long long n, cudaGraphConditionalHandle cond,
+                                                int set_cond) {
+  __shared__ double a[MAXIT], b[MAXIT], b2[MAXIT], x[MAXIT], dd[MAXIT], du[MAXIT], du2[MAXIT],
+      ml[MAXIT], rd[MAXIT];
+  __shared__ unsigned char piv[MAXIT];
+  int* st = lz_state(sc);
+  const int j = st[ST_J];
   const int lane = threadIdx.x;
+  if (j < 0 || j >= max_iter || j >= MAXIT) {  // not reachable from the drivers below
+    if (lane == 0) {
+      st[ST_STOP] = STOP_NONFINITE;
+      st[ST_M] = 1;
+      if (set_cond) cudaGraphSetConditional(cond, 0u);
+    }
+    return;
+  }
+  const int m = j + 1;
   if (lane == 0) {
     sc[OFF_ALPHA + j] = sc[OFF_C1 + j] + sc[OFF_C2 + j];
     sc[OFF_BETA + j] = sqrt(sc[OFF_MISC + 3]);
@@ -197,6 +249,7 @@ __global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int j) 
   for (int i = lane; i < m; i += 32) {
     a[i] = sc[OFF_ALPHA + i];
     b[i] = sc[OFF_BETA + i];  // b[i] couples i and i+1 (b[j] is the residual norm)
+    b2[i] = b[i] * b[i];
   }
   __syncwarp();
   double l = 1e300, h = -1e300;
@@ -213,57 +266,80 @@ __global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int j) 
   double lo = l - pad, hi = h + pad;
   for (int round = 0; round < 16; ++round) {
     if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
-    const double xt = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-    const unsigned hit = __ballot_sync(0xffffffffu, sturm_count(a, b, m, xt) >= 1);
-    const int t = hit ? (__ffs(hit) - 1) : 32;
-    const double nlo = lo + (hi - lo) * (double)t / 33.0;
-    const double nhi = (t < 32) ? lo + (hi - lo) * (double)(t + 1) / 33.0 : hi;
+    const double step = (hi - lo) * (1.0 / 65.0);
+    const double xs[2] = {lo + step * (double)(2 * lane + 1), lo + step * (double)(2 * lane + 2)};
+    int c[2];
+    sturm_counts<2>(a, b2, m, xs, c);
+    // counts grow with x: the first point with a count >= 1 brackets the
+    // lowest eigenvalue from above, its predecessor from below
+    const unsigned h0 = __ballot_sync(0xffffffffu, c[0] >= 1);
+    const unsigned h1 = __ballot_sync(0xffffffffu, c[1] >= 1);
+    int t = 64;
+    if (h1) {
+      const int l1 = __ffs(h1) - 1;
+      t = 2 * l1 + (((h0 >> l1) & 1u) ? 0 : 1);
+    }
+    const double nlo = lo + step * (double)t;
+    const double nhi = (t < 64) ? lo + step * (double)(t + 1) : hi;
     lo = nlo;
     hi = nhi;
   }
+  const double e = 0.5 * (lo + hi);
   if (lane == 0) {
-    const double e = 0.5 * (lo + hi);
     double tnorm = 0.0;
     for (int i = 0; i < m; ++i) tnorm = fmax(tnorm, fabs(a[i]) + 2.0 * fabs(b[i]));
     const double tiny = 1e-300 + 1e-18 * tnorm;
-    for (int i = 0; i < m; ++i) x[i] = 1.0 / sqrt((double)m);
-    for (int iter = 0; iter < 3; ++iter) {
-      for (int i = 0; i < m; ++i) {
-        dd[i] = a[i] - e;
-        du[i] = (i < m - 1) ? b[i] : 0.0;
-        dl[i] = (i < m - 1) ? b[i] : 0.0;
-      }
-      // Gaussian elimination with partial pivoting; dl[i] becomes the second
-      // superdiagonal entry of row i after the sweep.
-      for (int i = 0; i + 1 < m; ++i) {
-        if (fabs(dd[i]) >= fabs(dl[i])) {
-          if (dd[i] == 0.0) dd[i] = tiny;
-          const double f = dl[i] / dd[i];
-          dd[i + 1] -= f * du[i];
-          x[i + 1] -= f * x[i];
-          dl[i] = 0.0;
-        } else {
-          const double f = dd[i] / dl[i];
-          dd[i] = dl[i];
-          const double t = dd[i + 1];
-          dd[i + 1] = du[i] - f * t;
-          if (i + 2 < m) {
-            dl[i] = du[i + 1];
-            du[i + 1] = -f * dl[i];
-          } else {
-            dl[i] = 0.0;
-          }
-          du[i] = t;
-          const double bt = x[i];
-          x[i] = x[i + 1];
-          x[i + 1] = bt - f * x[i + 1];
+    for (int i = 0; i < m; ++i) {
+      dd[i] = a[i] - e;
+      du[i] = (i < m - 1) ? b[i] : 0.0;
+      du2[i] = 0.0;
+    }
+    // P (T - e I) = L U: row i+1 enters with sub-diagonal b[i]; piv[i] marks
+    // an interchange of rows i and i+1, ml[i] the multiplier, du2[i] the
+    // fill-in on the second superdiagonal.
+    for (int i = 0; i + 1 < m; ++i) {
+      const double sub = b[i];
+      if (fabs(dd[i]) >= fabs(sub)) {
+        if (dd[i] == 0.0) dd[i] = tiny;
+        const double f = sub / dd[i];
+        dd[i + 1] -= f * du[i];
+        ml[i] = f;
+        piv[i] = 0;
+      } else {
+        const double f = dd[i] / sub;
+        const double t = dd[i + 1];
+        dd[i] = sub;
+        dd[i + 1] = du[i] - f * t;
+        du[i] = t;
+        if (i + 2 < m) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du2[i];
         }
+        ml[i] = f;
+        piv[i] = 1;
       }
-      if (dd[m - 1] == 0.0) dd[m - 1] = tiny;
-      x[m - 1] /= dd[m - 1];
-      if (m > 1) x[m - 2] = (x[m - 2] - du[m - 2] * x[m - 1]) / dd[m - 2];
+    }
+    if (dd[m - 1] == 0.0) dd[m - 1] = tiny;
+  }
+  __syncwarp();
+  for (int i = lane; i < m; i += 32) rd[i] = 1.0 / dd[i];
+  __syncwarp();
+  if (lane == 0) {
+    const double x0 = 1.0 / sqrt((double)m);
+    for (int i = 0; i < m; ++i) x[i] = x0;
+    for (int iter = 0; iter < 3; ++iter) {
+      for (int i = 0; i + 1 < m; ++i) {  // x <- L^-1 P x
+        if (piv[i]) {
+          const double t = x[i];
+          x[i] = x[i + 1];
+          x[i + 1] = t;
+        }
+        x[i + 1] -= ml[i] * x[i];
+      }
+      x[m - 1] *= rd[m - 1];  // x <- U^-1 x
+      if (m > 1) x[m - 2] = (x[m - 2] - du[m - 2] * x[m - 1]) * rd[m - 2];
       for (int i = m - 3; i >= 0; --i)
-        x[i] = (x[i] - du[i] * x[i + 1] - dl[i] * x[i + 2]) / dd[i];
+        x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) * rd[i];
       double nrm = 0.0;
       for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
       nrm = sqrt(nrm);
@@ -271,13 +347,56 @@ __global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int j) 
         for (int i = 0; i < m; ++i) x[i] = (i == 0) ? 1.0 : 0.0;
         break;
       }
-      for (int i = 0; i < m; ++i) x[i] /= nrm;
+      const double inv = 1.0 / nrm;
+      for (int i = 0; i < m; ++i) x[i] *= inv;
     }
     for (int i = 0; i < m; ++i) sc[OFF_S + i] = x[i];
+    const double res = b[j] * fabs(x[m - 1]);
     sc[OFF_MISC + 0] = e;
-    sc[OFF_MISC + 1] = b[j] * fabs(x[m - 1]);
+    sc[OFF_MISC + 1] = res;
     sc[OFF_MISC + 2] = b[j];
+    int stop = STOP_NONE;
+    if (!isfinite(e) || !isfinite(res))
+      stop = STOP_NONFINITE;
+    else if (res <= tol || b[j] == 0.0 || (long long)m == n)
+      stop = STOP_CONVERGED;
+    else if (m >= max_iter)
+      stop = STOP_CAP;
+    st[ST_M] = m;
+    st[ST_STOP] = stop;
+    if (stop == STOP_NONE) st[ST_J] = j + 1;
+    if (set_cond) cudaGraphSetConditional(cond, stop == STOP_NONE ? 1u : 0u);
   }
+}
+
+// Next Krylov vector V[J] = w / beta_{J-1} after a step that did not stop
+// (the same arithmetic as vec_scale_by_inv).
+__global__ void k_next_vector(double* __restrict__ V, int64_t ld, const double* __restrict__ w,
+                              int64_t n, const double* __restrict__ sc) {
+  const int* st = lz_state(sc);
+  if (st[ST_STOP] != STOP_NONE) return;
+  const int jn = st[ST_J];
+  const double f = 1.0 / sc[OFF_BETA + jn - 1];
+  double* y = V + (int64_t)jn * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = w[i] * f;
+}
+
+// x = V[J]: the fixed input buffer of the matrix-vector product recorded in
+// the step graph.
+__global__ void k_copy_current(const double* __restrict__ V, int64_t ld, double* __restrict__ x,
+                               int64_t n, const double* __restrict__ sc) {
+  const double* v = V + (int64_t)lz_state(sc)[ST_J] * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v[i];
+}
+
+// First node of the step graph: enter the loop only if the step run before
+// the graph did not stop.
+__global__ void k_loop_init(const double* __restrict__ sc, cudaGraphConditionalHandle cond) {
+  cudaGraphSetConditional(cond, lz_state(sc)[ST_STOP] == STOP_NONE ? 1u : 0u);
 }
 
 // Blocks for k_multidot: at least 16 element pairs per thread, and no more
@@ -299,22 +418,110 @@ int ew_blocks(int64_t n) {
 }
 
 // w -= V^T-projection of w onto the nv stored Krylov vectors (rows of V with
-// an even stride ld, 16-byte aligned like w), coefficients to coef.
+// an even stride ld, 16-byte aligned like w), coefficients to coef. With
+// jcur set, the kernels take nv = jcur[0] + 1 from the device and nv only
+// bounds it (the blocks of the final reduction).
 osmps_status project(osmps_ctx* ctx, const double* V, int64_t ld, int64_t n, int nv, double* w,
-                     double* part, double* coef, cudaStream_t s) {
+                     double* part, double* coef, cudaStream_t s, const int* jcur = nullptr) {
   const int nb = dot_blocks(n, ctx->sm_count);
-  { k_multidot<<<nb, DOT_THREADS, 0, s>>>(V, ld, nv, w, n, part); note_launch(); }
-  { k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef); note_launch(); }
-  { k_combine<<<ew_blocks(n), 256, 0, s>>>(V, ld, nv, coef, w, n, 0); note_launch(); }
+  { k_multidot<<<nb, DOT_THREADS, 0, s>>>(V, ld, nv, w, n, part, jcur); note_launch(); }
+  { k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef, jcur); note_launch(); }
+  { k_combine<<<ew_blocks(n), 256, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur); note_launch(); }
   OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+// OSMPS_LANCZOS_AUTO: the graph for small Krylov vectors, except on the
+// batch scheduler's worker threads, where many streams run at once and the
+// host loop measured faster (64-chain batch, 8 workers: 2.29 sweeps/s with
+// the host loop, 1.79 with graphs).
+bool use_step_graph(const osmps_ctx* ctx, int64_t n, int max_iter) {
+  if (ctx->prof_on || max_iter < 2) return false;
+  if (ctx->lanczos_mode == OSMPS_LANCZOS_HOST) return false;
+  if (ctx->lanczos_mode == OSMPS_LANCZOS_GRAPH) return true;
+  return n <= ((int64_t)1 << 20) && !is_batch_worker();
+}
+
+using StepRecorder = std::function<osmps_status(cudaStream_t, cudaGraphConditionalHandle)>;
+using LzGraph = osmps_ctx::LzGraph;
+constexpr size_t LZ_GRAPHS_KEPT = 16;
+
+void destroy_graph(LzGraph& gr) {
+  if (gr.e) cudaGraphExecDestroy(gr.e);
+  if (gr.g) cudaGraphDestroy(gr.g);
+  gr.e = nullptr;
+  gr.g = nullptr;
+}
+
+// A graph recorded for one call only, destroyed when the call returns (after
+// the stream has drained: SyncOnExit is declared after it).
+struct OneShotGraph {
+  LzGraph gr;
+  ~OneShotGraph() { destroy_graph(gr); }
+};
+struct SyncOnExit {
+  cudaStream_t s = nullptr;
+  bool armed = false;
+  ~SyncOnExit() {
+    if (armed) cudaStreamSynchronize(s);
+  }
+};
+
+// Record [k_loop_init] -> while (cond) { step } and instantiate it. The step
+// is recorded by stream capture on the context's capture stream; workspace
+// growth is an error while the capture is open. gr.body_launches: kernels
+// one step launches (the capture's own count is taken back: recording
+// launches nothing).
+osmps_status record_step_graph(osmps_ctx* ctx, const double* sc, const StepRecorder& record,
+                               LzGraph& gr) {
+  if (!ctx->capture_stream)
+    OSMPS_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = ctx->capture_stream;
+  OSMPS_CUDA(cudaGraphCreate(&gr.g, 0));
+  cudaGraphConditionalHandle cond;
+  OSMPS_CUDA(cudaGraphConditionalHandleCreate(&cond, gr.g, 0, cudaGraphCondAssignDefault));
+  cudaKernelNodeParams kn = {};
+  void* args[2] = {(void*)&sc, (void*)&cond};
+  kn.func = (void*)k_loop_init;
+  kn.gridDim = dim3(1);
+  kn.blockDim = dim3(1);
+  kn.sharedMemBytes = 0;
+  kn.kernelParams = args;
+  kn.extra = nullptr;
+  cudaGraphNode_t init = nullptr, loop = nullptr;
+  OSMPS_CUDA(cudaGraphAddKernelNode(&init, gr.g, nullptr, 0, &kn));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  OSMPS_CUDA(cudaGraphAddNode(&loop, gr.g, &init, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const long long before = thread_launch_count();
+  OSMPS_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+  ctx->capturing = true;
+  const osmps_status st = record(cs, cond);
+  ctx->capturing = false;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+  gr.body_launches = thread_launch_count() - before;
+  note_launches(-gr.body_launches);
+  if (st != OSMPS_OK) return st;
+  if (ce != cudaSuccess)
+    return set_error(OSMPS_ECUDA, "lanczos: recording the step graph failed: %s",
+                     cudaGetErrorString(ce));
+  OSMPS_CUDA(cudaGraphInstantiate(&gr.e, gr.g, 0));
   return OSMPS_OK;
 }
 
 }  // namespace
 
+
 osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter, double tol,
                           const Matvec& matvec, double* energy, int* iters, double* resid,
-                          cudaStream_t s, const double* P, int64_t ldp, int kp) {
+                          cudaStream_t s, const double* P, int64_t ldp, int kp,
+                          const long long* mkey, int nmkey) {
   osmps_status st = OSMPS_OK;
   const int64_t ld = (n + 1) & ~(int64_t)1;  // even row stride: 16-byte aligned rows
   if (max_iter > n) max_iter = (int)n;
@@ -326,7 +533,14 @@ osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter
   if (!sc) return st;
   double* part = (double*)ws_get(ctx, SLOT_LZ_PART, (size_t)MAXIT * DOT_MAX_BLOCKS * 8, s, &st);
   if (!part) return st;
+  const bool graph = use_step_graph(ctx, n, max_iter);
+  double* X = nullptr;
+  if (graph) {
+    X = (double*)ws_get(ctx, SLOT_LZ_X, (size_t)n * 8, s, &st);
+    if (!X) return st;
+  }
   OSMPS_TRY(pinned_reserve(ctx, 16));
+  int* state = lz_state(sc);
 
   // v_0 = theta / ||theta||
   OSMPS_TRY(vec_norm2(ctx, theta, n, sc + OFF_MISC + 4, s));
@@ -347,53 +561,116 @@ osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter
       return set_error(OSMPS_EINVAL, "lanczos: start vector lies in the span of the projector rows");
   }
   OSMPS_TRY(vec_scale_by_inv_sqrt(V, n, sc + OFF_MISC + 4, s));
+  OSMPS_CUDA(cudaMemsetAsync(state, 0, 4 * sizeof(int), s));
 
-  int m = 0;
-  double e = 0.0, res = 0.0;
-  bool converged = false;
-  for (int j = 0; j < max_iter; ++j) {
-    double* vj = V + (int64_t)j * ld;
-    OSMPS_TRY(matvec(vj, w));
+  // One step on stream q: w = H_eff V[J] (x is V[J] itself, or the buffer X
+  // that k_copy_current fills), projected out of the projector rows and
+  // twice out of V[0..J], its norm, the tridiagonal solve with the stopping
+  // decision, and V[J+1]. final_blocks bounds J + 1.
+  auto step = [&](cudaStream_t q, const double* x, int final_blocks,
+                  cudaGraphConditionalHandle cond, int set_cond) -> osmps_status {
+    if (x == X) {
+      { k_copy_current<<<ew_blocks(n), 256, 0, q>>>(V, ld, X, n, sc); note_launch(); }
+      OSMPS_LAUNCH_CHECK();
+    }
+    OSMPS_TRY(matvec(x, w, q));
     if (kp > 0) {  // the operator restricted to the complement: w <- (1 - P^T P) H v_j
-      OSMPS_TRY(project(ctx, P, ldp, n, kp, w, part, sc + OFF_PROJ, s));
-      OSMPS_TRY(project(ctx, P, ldp, n, kp, w, part, sc + OFF_PROJ + MAX_PROJ, s));
+      OSMPS_TRY(project(ctx, P, ldp, n, kp, w, part, sc + OFF_PROJ, q));
+      OSMPS_TRY(project(ctx, P, ldp, n, kp, w, part, sc + OFF_PROJ + MAX_PROJ, q));
     }
-    OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C1, s));
-    OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C2, s));
-    OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, s));
-    { k_tridiag<<<1, 32, 0, s>>>(sc, j); note_launch(); }
+    OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C1, q, state));
+    OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C2, q, state));
+    OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, q));
+    { k_tridiag<<<1, 32, 0, q>>>(sc, max_iter, tol, (long long)n, cond, set_cond); note_launch(); }
     OSMPS_LAUNCH_CHECK();
-    OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC, 3 * 8, cudaMemcpyDeviceToHost, s));
-    OSMPS_CUDA(cudaStreamSynchronize(s));
-    e = ctx->host_pinned[0];
-    res = ctx->host_pinned[1];
-    const double beta = ctx->host_pinned[2];
-    m = j + 1;
-    if (!std::isfinite(e) || !std::isfinite(res))
-      return set_error(OSMPS_ENAN, "lanczos: non-finite Ritz value at step %d", j);
-    if (res <= tol || beta == 0.0 || m == n) {
-      converged = true;
-      break;
+    { k_next_vector<<<ew_blocks(n), 256, 0, q>>>(V, ld, w, n, sc); note_launch(); }
+    OSMPS_LAUNCH_CHECK();
+    return OSMPS_OK;
+  };
+
+  OneShotGraph once;
+  SyncOnExit drain;
+  long long body_launches = 0;
+  if (!graph) {
+    for (int j = 0; j < max_iter; ++j) {
+      OSMPS_TRY(step(s, V + (int64_t)j * ld, j + 1, 0, 0));
+      OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC, MISC_READ * 8,
+                                 cudaMemcpyDeviceToHost, s));
+      OSMPS_CUDA(cudaStreamSynchronize(s));
+      if (lz_state_in_misc(ctx->host_pinned)[ST_STOP] != STOP_NONE) break;
     }
-    if (j + 1 == max_iter) break;
-    OSMPS_TRY(vec_scale_by_inv(V + (int64_t)(j + 1) * ld, w, n, sc + OFF_BETA + j, s));
+  } else {
+    // Step 0 runs directly: it sizes every workspace slot a step uses, so
+    // nothing grows while the step is recorded. The other steps run in the
+    // graph loop, recorded now or replayed from the context's cache.
+    OSMPS_TRY(step(s, V, 1, 0, 0));
+    std::vector<long long> key(mkey, mkey + (mkey ? nmkey : 0));
+    long long tol_bits;
+    memcpy(&tol_bits, &tol, sizeof tol_bits);
+    for (long long k : {(long long)n, (long long)max_iter, tol_bits, (long long)kp, (long long)ldp,
+                        (long long)(intptr_t)P, (long long)ctx->ws_epoch})
+      key.push_back(k);
+    LzGraph* gr = nullptr;
+    if (mkey && nmkey > 0)
+      for (auto& c : ctx->lz_graphs)
+        if (c.key == key) gr = &c;
+    if (!gr) {
+      const StepRecorder rec = [&](cudaStream_t q, cudaGraphConditionalHandle cond) {
+        return step(q, X, max_iter, cond, 1);
+      };
+      LzGraph fresh;
+      fresh.key = key;
+      const osmps_status rs = record_step_graph(ctx, sc, rec, fresh);
+      if (rs != OSMPS_OK) {
+        destroy_graph(fresh);
+        return rs;
+      }
+      if (mkey && nmkey > 0) {
+        if (ctx->lz_graphs.size() >= LZ_GRAPHS_KEPT) {  // every earlier call has drained
+          size_t lru = 0;
+          for (size_t i = 1; i < ctx->lz_graphs.size(); ++i)
+            if (ctx->lz_graphs[i].last_use < ctx->lz_graphs[lru].last_use) lru = i;
+          destroy_graph(ctx->lz_graphs[lru]);
+          ctx->lz_graphs.erase(ctx->lz_graphs.begin() + lru);
+        }
+        ctx->lz_graphs.push_back(fresh);
+        gr = &ctx->lz_graphs.back();
+      } else {
+        once.gr = fresh;
+        gr = &once.gr;
+      }
+    }
+    gr->last_use = ++ctx->lz_clock;
+    body_launches = gr->body_launches;
+    drain.s = s;
+    drain.armed = true;
+    OSMPS_CUDA(cudaGraphLaunch(gr->e, s));
+    note_launch();  // k_loop_init
   }
   // Ritz vector theta = sum_i s_i v_i, normalised
-  { k_combine_scalar<<<ew_blocks(n), 256, 0, s>>>(V, ld, m, sc + OFF_S, theta, n); note_launch(); }
+  { k_combine_scalar<<<ew_blocks(n), 256, 0, s>>>(V, ld, sc, theta, n); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   OSMPS_TRY(vec_norm2(ctx, theta, n, sc + OFF_MISC + 4, s));
   OSMPS_TRY(vec_scale_by_inv_sqrt(theta, n, sc + OFF_MISC + 4, s));
-  int flag = 0;
-  OSMPS_CUDA(cudaMemcpyAsync(&flag, ctx->dev_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int* hflag = reinterpret_cast<int*>(ctx->host_pinned + MISC_READ);
+  OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC, MISC_READ * 8,
+                             cudaMemcpyDeviceToHost, s));
+  OSMPS_CUDA(cudaMemcpyAsync(hflag, ctx->dev_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
   OSMPS_CUDA(cudaStreamSynchronize(s));
-  if (flag & 1) {
+  const double e = ctx->host_pinned[0], res = ctx->host_pinned[1];
+  const int* hs = lz_state_in_misc(ctx->host_pinned);
+  const int stop = hs[ST_STOP], m = hs[ST_M];
+  if (graph) note_launches(body_launches * (long long)(m - 1));  // the loop ran m - 1 steps
+  if (*hflag & 1) {
     cudaMemsetAsync(ctx->dev_flags, 0, sizeof(int), s);
     return set_error(OSMPS_ETIMEOUT, "lanczos: a bounded device wait gave up");
   }
+  if (stop == STOP_NONFINITE)
+    return set_error(OSMPS_ENAN, "lanczos: non-finite Ritz value at step %d", m - 1);
   *energy = e;
   *iters = m;
   if (resid) *resid = res;
-  if (!converged)
+  if (stop != STOP_CONVERGED)
     return set_error(OSMPS_ENOCONV, "lanczos: residual %.3e above tol %.3e after %d steps", res,
                      tol, m);
   return OSMPS_OK;
@@ -405,12 +682,13 @@ osmps_status lanczos_impl(osmps_ctx* ctx, const double* L, const double* W1, con
                           double tol, int precision, double* energy, int* iters, double* resid,
                           cudaStream_t s) {
   OSMPS_TRY(heff_prepare(ctx, L, W1, W2, R, chi_l, d1, d2, chi_r, wl, wm, wr, precision, s));
-  const Matvec mv = [&](const double* x, double* y) {
+  const Matvec mv = [&](const double* x, double* y, cudaStream_t q) {
     return heff_apply_impl(ctx, nullptr, nullptr, nullptr, nullptr, x, y, chi_l, d1, d2, chi_r,
-                           wl, wm, wr, precision, s, true);
+                           wl, wm, wr, precision, q, true);
   };
+  const long long key[9] = {1, chi_l, d1, d2, chi_r, wl, wm, wr, precision};
   return lanczos_core(ctx, chi_l * d1 * d2 * chi_r, theta, max_iter, tol, mv, energy, iters,
-                      resid, s);
+                      resid, s, nullptr, 0, 0, key, 9);
 }
 
 }  // namespace osmps
@@ -495,11 +773,12 @@ extern "C" osmps_status osmps_lanczos_ground_projected(
     }
   }
   OSMPS_TRY(heff_prepare(ctx, L, W1, W2, R, chi_l, d1, d2, chi_r, wl, wm, wr, precision, s));
-  const Matvec mv = [&](const double* x, double* y) {
+  const Matvec mv = [&](const double* x, double* y, cudaStream_t q) {
     return heff_apply_impl(ctx, nullptr, nullptr, nullptr, nullptr, x, y, chi_l, d1, d2, chi_r,
-                           wl, wm, wr, precision, s, true);
+                           wl, wm, wr, precision, q, true);
   };
+  const long long key[9] = {1, chi_l, d1, d2, chi_r, wl, wm, wr, precision};
   return lanczos_core(ctx, n, theta_inout, max_iter, tol, mv, energy_out, iters_out, resid_out, s,
-                      Q, ld, k);
+                      Q, ld, k, key, 9);
 }
 

@@ -11,8 +11,9 @@
 // Arithmetic: the eigenpairs are float64, from cuSOLVER (dsyevdx for the
 // largest min(chi_max, rank) only, dsyevd when that is all of them) or, when
 // the context selects it (osmps_ctx_set_eig_solver), from the tridiagonal
-// route of eig.cu (cuSOLVER dsytrd, then bisection, inverse iteration,
-// Cholesky QR and blocked back-transformation on emulated-float64 GEMMs). The
+// route of eig.cu (this library's Householder tridiagonalisation, then
+// bisection, inverse iteration, Cholesky QR and blocked back-transformation
+// on emulated-float64 GEMMs). The
 // Gram matrix and the projection are float64 GEMMs: on the DMMA kernel for
 // OSMPS_PREC_FP64, on the float64-accurate emulated tensor-core GEMM for
 // every other precision.

@@ -24,10 +24,13 @@
 
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 struct osmps_u1_heff {
   osmps_ctx* ctx = nullptr;
+  uint64_t uid = 0;  // unique per plan in the process (keys recorded Lanczos graphs)
   int64_t nl = 0, nr = 0, d1 = 0, d2 = 0, wl = 0, wm = 0, wr = 0;
   std::vector<int64_t> ql, chil, qr, chir, qwl, qwr;
   int64_t qmin = 0, nq = 0;
@@ -576,7 +579,9 @@ osmps_status osmps_u1_heff_create(osmps_ctx* ctx, const osmps_u1_desc* d, osmps_
     return set_error(OSMPS_ESHAPE, "osmps_u1_heff_create: bad sizes");
   if (!d->q_left || !d->chi_left || !d->q_right || !d->chi_right || !d->q_wl || !d->q_wr)
     return set_error(OSMPS_EINVAL, "osmps_u1_heff_create: null table");
+  static std::atomic<uint64_t> next_uid{1};
   osmps_u1_heff* h = new osmps_u1_heff();
+  h->uid = next_uid.fetch_add(1);
   h->ctx = ctx;
   h->nl = d->n_left;
   h->nr = d->n_right;
@@ -676,12 +681,13 @@ osmps_status osmps_lanczos_ground_u1(osmps_ctx* ctx, osmps_u1_heff* h, const dou
   OSMPS_TRY(osmps_u1_heff_prepare(ctx, h, L, W1, W2, R, precision, stream));
   CtxScope scope_(ctx);
   cudaStream_t s = (cudaStream_t)stream;
-  const Matvec mv = [&](const double* x, double* y) {
-    return h->prepared_kind == TC_BF16 ? u1_apply_kind<TC_BF16>(ctx, h, x, y, s)
-                                       : u1_apply_kind<TC_TF32>(ctx, h, x, y, s);
+  const Matvec mv = [&](const double* x, double* y, cudaStream_t q) {
+    return h->prepared_kind == TC_BF16 ? u1_apply_kind<TC_BF16>(ctx, h, x, y, q)
+                                       : u1_apply_kind<TC_TF32>(ctx, h, x, y, q);
   };
+  const long long key[3] = {2, (long long)h->uid, (long long)h->prepared_kind};
   return lanczos_core(ctx, h->n_theta, theta_inout, max_iter, tol, mv, energy_out, iters_out,
-                      resid_out, s);
+                      resid_out, s, nullptr, 0, 0, key, 3);
 }
 
 osmps_status osmps_heff_apply_u1(osmps_ctx* ctx, osmps_u1_heff* h, const double* L,
