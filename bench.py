@@ -651,7 +651,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--batch-workers", type=int, default=16)
+    ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiler runs)")
     args = ap.parse_args()

@@ -111,7 +111,9 @@ __device__ __forceinline__ void multidot_group(const double* __restrict__ V, int
 }
 
 // part[i * nb + b] = sum over block b's elements of V[i][e] * w[e], i < nv:
-// groups of DOT_GROUP vectors, then one group of the remainder.
+// block (b, y) takes element chunk b (nb = gridDim.x chunks) of the vector
+// group starting at y * DOT_GROUP, so small vectors still spread over many
+// SMs (the float64 FMA rate of one SM is the limit there).
 // With jcur set, nv = jcur[0] + 1 (the Krylov vectors up to the current one).
 __global__ void __launch_bounds__(DOT_THREADS, 3) k_multidot(const double* __restrict__ V, int64_t ld,
                                                           int nv, const double* __restrict__ w,
@@ -119,8 +121,12 @@ __global__ void __launch_bounds__(DOT_THREADS, 3) k_multidot(const double* __res
                                                           const int* __restrict__ jcur) {
   __shared__ double sh[DOT_THREADS / 32][DOT_GROUP];
   if (jcur) nv = jcur[0] + 1;
-  int g0 = 0;
-  for (; g0 + DOT_GROUP <= nv; g0 += DOT_GROUP) multidot_group<DOT_GROUP>(V, ld, g0, w, n, part, sh);
+  const int g0 = (int)blockIdx.y * DOT_GROUP;
+  if (g0 >= nv) return;
+  if (g0 + DOT_GROUP <= nv) {
+    multidot_group<DOT_GROUP>(V, ld, g0, w, n, part, sh);
+    return;
+  }
   switch (nv - g0) {
     case 1: multidot_group<1>(V, ld, g0, w, n, part, sh); break;
     case 2: multidot_group<2>(V, ld, g0, w, n, part, sh); break;
@@ -153,7 +159,9 @@ __global__ void k_multidot_final(const double* __restrict__ part, int nb, double
 
 // mode 0: w[e] -= sum_i c[i] V[i][e];  mode 1: w[e] = sum_i c[i] V[i][e]
 // (two consecutive elements per thread, 16-byte loads; the vectors are
-// 256-byte aligned with an even stride).
+// 256-byte aligned with an even stride). The sum over i runs in four
+// interleaved partial sums (i mod 4), added in a fixed order, which cuts the
+// dependent float64 chain per element by four.
 __global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
                           const double* __restrict__ c, double* __restrict__ w, int64_t n,
                           int mode, const int* __restrict__ jcur) {
@@ -164,18 +172,29 @@ __global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
   const int64_t n2 = n >> 1;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double ax = 0.0, ay = 0.0;
-    for (int i = 0; i < nv; ++i) {
-      const double2 x = reinterpret_cast<const double2*>(V + (int64_t)i * ld)[e];
-      ax = fma(cs[i], x.x, ax);
-      ay = fma(cs[i], x.y, ay);
+    double ax[4] = {0.0, 0.0, 0.0, 0.0}, ay[4] = {0.0, 0.0, 0.0, 0.0};
+    int i = 0;
+    for (; i + 4 <= nv; i += 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double2 x = reinterpret_cast<const double2*>(V + (int64_t)(i + q) * ld)[e];
+        ax[q] = fma(cs[i + q], x.x, ax[q]);
+        ay[q] = fma(cs[i + q], x.y, ay[q]);
+      }
     }
+    for (int q = 0; i < nv; ++i, ++q) {
+      const double2 x = reinterpret_cast<const double2*>(V + (int64_t)i * ld)[e];
+      ax[q] = fma(cs[i], x.x, ax[q]);
+      ay[q] = fma(cs[i], x.y, ay[q]);
+    }
+    const double sx = (ax[0] + ax[1]) + (ax[2] + ax[3]);
+    const double sy = (ay[0] + ay[1]) + (ay[2] + ay[3]);
     double2* wp = reinterpret_cast<double2*>(w) + e;
     if (mode == 0) {
       const double2 o = *wp;
-      *wp = make_double2(o.x - ax, o.y - ay);
+      *wp = make_double2(o.x - sx, o.y - sy);
     } else {
-      *wp = make_double2(ax, ay);
+      *wp = make_double2(sx, sy);
     }
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -399,14 +418,24 @@ __global__ void k_loop_init(const double* __restrict__ sc, cudaGraphConditionalH
   cudaGraphSetConditional(cond, lz_state(sc)[ST_STOP] == STOP_NONE ? 1u : 0u);
 }
 
-// Blocks for k_multidot: at least 16 element pairs per thread, and no more
-// blocks than fit on the GPU in one wave (3 per SM at its register use).
+// Element chunks for k_multidot: about two element pairs per thread, and no
+// more chunks than fit on the GPU in one wave (3 blocks per SM at its
+// register use); the vector groups multiply the blocks.
 int dot_blocks(int64_t n, int sm_count) {
-  int64_t b = cdiv(n, DOT_THREADS * 32);
+  int64_t b = cdiv(n, DOT_THREADS * 4);
   const int64_t wave = 3 * (int64_t)(sm_count > 0 ? sm_count : 1);
   if (b > wave) b = wave;
   if (b > DOT_MAX_BLOCKS) b = DOT_MAX_BLOCKS;
   if (b < 1) b = 1;
+  return (int)b;
+}
+
+// k_combine (128 threads): one element pair per thread up to 8192 blocks,
+// then grid-stride.
+int combine_blocks(int64_t n) {
+  int64_t b = cdiv(n >> 1, 128);
+  if (b < 1) b = 1;
+  if (b > 8192) b = 8192;
   return (int)b;
 }
 
@@ -424,9 +453,10 @@ int ew_blocks(int64_t n) {
 osmps_status project(osmps_ctx* ctx, const double* V, int64_t ld, int64_t n, int nv, double* w,
                      double* part, double* coef, cudaStream_t s, const int* jcur = nullptr) {
   const int nb = dot_blocks(n, ctx->sm_count);
-  { k_multidot<<<nb, DOT_THREADS, 0, s>>>(V, ld, nv, w, n, part, jcur); note_launch(); }
+  const dim3 dgrid(nb, (unsigned)cdiv(nv, DOT_GROUP));
+  { k_multidot<<<dgrid, DOT_THREADS, 0, s>>>(V, ld, nv, w, n, part, jcur); note_launch(); }
   { k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef, jcur); note_launch(); }
-  { k_combine<<<ew_blocks(n), 256, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur); note_launch(); }
+  { k_combine<<<combine_blocks(n), 128, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }
