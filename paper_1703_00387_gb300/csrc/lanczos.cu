@@ -159,9 +159,12 @@ __global__ void k_multidot_final(const double* __restrict__ part, int nb, double
 
 // mode 0: w[e] -= sum_i c[i] V[i][e];  mode 1: w[e] = sum_i c[i] V[i][e]
 // (two consecutive elements per thread, 16-byte loads; the vectors are
-// 256-byte aligned with an even stride). The sum over i runs in four
-// interleaved partial sums (i mod 4), added in a fixed order, which cuts the
-// dependent float64 chain per element by four.
+// 256-byte aligned with an even stride). With ACC = 4 the sum over i runs
+// in four interleaved partial sums (i mod 4), added in a fixed order, which
+// cuts the dependent float64 chain per element by four: the form for small
+// vectors, where that chain is the cost. Large vectors are bandwidth-bound
+// and stream one vector at a time faster (ACC = 1).
+template <int ACC>
 __global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
                           const double* __restrict__ c, double* __restrict__ w, int64_t n,
                           int mode, const int* __restrict__ jcur) {
@@ -172,11 +175,13 @@ __global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
   const int64_t n2 = n >> 1;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2;
        e += (int64_t)gridDim.x * blockDim.x) {
-    double ax[4] = {0.0, 0.0, 0.0, 0.0}, ay[4] = {0.0, 0.0, 0.0, 0.0};
-    int i = 0;
-    for (; i + 4 <= nv; i += 4) {
+    double ax[ACC], ay[ACC];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < ACC; ++q) ax[q] = ay[q] = 0.0;
+    int i = 0;
+    for (; i + ACC <= nv; i += ACC) {
+#pragma unroll
+      for (int q = 0; q < ACC; ++q) {
         const double2 x = reinterpret_cast<const double2*>(V + (int64_t)(i + q) * ld)[e];
         ax[q] = fma(cs[i + q], x.x, ax[q]);
         ay[q] = fma(cs[i + q], x.y, ay[q]);
@@ -187,8 +192,11 @@ __global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
       ax[q] = fma(cs[i], x.x, ax[q]);
       ay[q] = fma(cs[i], x.y, ay[q]);
     }
-    const double sx = (ax[0] + ax[1]) + (ax[2] + ax[3]);
-    const double sy = (ay[0] + ay[1]) + (ay[2] + ay[3]);
+    double sx = ax[0], sy = ay[0];
+    if (ACC == 4) {
+      sx = (ax[0] + ax[1 % ACC]) + (ax[2 % ACC] + ax[3 % ACC]);
+      sy = (ay[0] + ay[1 % ACC]) + (ay[2 % ACC] + ay[3 % ACC]);
+    }
     double2* wp = reinterpret_cast<double2*>(w) + e;
     if (mode == 0) {
       const double2 o = *wp;
@@ -456,7 +464,12 @@ osmps_status project(osmps_ctx* ctx, const double* V, int64_t ld, int64_t n, int
   const dim3 dgrid(nb, (unsigned)cdiv(nv, DOT_GROUP));
   { k_multidot<<<dgrid, DOT_THREADS, 0, s>>>(V, ld, nv, w, n, part, jcur); note_launch(); }
   { k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef, jcur); note_launch(); }
-  { k_combine<<<combine_blocks(n), 128, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur); note_launch(); }
+  if (n < ((int64_t)1 << 20)) {
+    k_combine<4><<<combine_blocks(n), 128, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur);
+  } else {
+    k_combine<1><<<ew_blocks(n), 256, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur);
+  }
+  note_launch();
   OSMPS_LAUNCH_CHECK();
   return OSMPS_OK;
 }
