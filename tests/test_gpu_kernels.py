@@ -75,6 +75,25 @@ def test_heff_apply_full_size_chi1024(ctx, prec):
     assert rel(y.cpu().numpy(), ref) <= TOL_FULL[prec]
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_heff_apply_many_ragged_tiles(ctx, prec):
+    """GEMMs of more tiles than the GPU has SMs but not a whole number of
+    waves (stage 1: 51 x 5 = 255 tiles, stage 4: 41 x 2 = 82, on 152 SMs),
+    with ragged M and N edges and K padded to the slice size. Parity with the
+    oracle at the full-size bar, and bit-identical repeats."""
+    Lh, W1, W2, Rh, th = inputs.random_heff_operands(1300, 2, 2, 300, 5, 5, 5, seed=1300)
+    ref = od.heff_apply(Lh, W1, W2, Rh, th)
+    t = [dev(x) for x in (Lh, W1, W2, Rh, th)]
+    ys = []
+    for _ in range(2):
+        y = torch.empty_like(t[4])
+        B.osmps_heff_apply(ctx, *t, y, precision=prec)
+        torch.cuda.synchronize()
+        ys.append(y.cpu().numpy())
+    assert rel(ys[0], ref) <= TOL_FULL[prec]
+    np.testing.assert_array_equal(ys[0], ys[1])
+
+
 def test_heff_apply_repeat_is_deterministic(ctx):
     Lh, W1, W2, Rh, th = inputs.random_heff_operands(96, 2, 2, 96, 5, 5, 5, seed=3)
     t = [dev(x) for x in (Lh, W1, W2, Rh, th)]
@@ -86,7 +105,8 @@ def test_heff_apply_repeat_is_deterministic(ctx):
     np.testing.assert_array_equal(ys[0], ys[1])
 
 
-ENV_SHAPES = [(6, 2, 9, 3, 3), (130, 2, 100, 5, 5), (64, 3, 50, 14, 14), (1, 2, 2, 1, 5), (33, 5, 40, 4, 4)]
+ENV_SHAPES = [(6, 2, 9, 3, 3), (130, 2, 100, 5, 5), (64, 3, 50, 14, 14), (1, 2, 2, 1, 5), (33, 5, 40, 4, 4),
+              (600, 2, 500, 5, 5)]  # the last: 96-tile GEMMs
 
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3", "fp64emu"])
