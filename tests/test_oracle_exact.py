@@ -83,3 +83,15 @@ def test_heisenberg_energy_per_site_sanity():
     W = mpo.xxz_mpo(8, 1.0, 1.0, 0.0)
     assert abs(np.linalg.eigvalsh(mpo.mpo_to_dense(W))[0]
                - exact.ground_energy(exact.kron_hamiltonian(8, 2, *exact.xxz_terms(8)))) < 1e-12
+
+
+def test_xxz_l20_golden_matches_oracle():
+    """tests/golden/xxz_l20_ground_energy.json (the exact chi = 1024 reference
+    of the GPU sweeps) is what its script's oracle construction gives."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "xxz_l20_ground_energy.json")
+    with open(path) as f:
+        stored = json.load(f)["ground_energy"]
+    H = exact.kron_hamiltonian(20, 2, *exact.xxz_terms(20, 1.0, 1.0, 0.0))
+    assert abs(exact.ground_energy(H) - stored) <= 1e-12 * abs(stored)
