@@ -50,7 +50,8 @@ struct osmps_u1_heff {
   // offsets (int64 elements) of the tables inside d_tab
   int64_t t_lsec = 0, t_ql = 0, t_qr = 0, t_qwl = 0, t_rowlen = 0, t_t1off = 0, t_rs1 = 0, t_cs = 0,
           t_a1src = 0, t_a1len = 0, t_b1base = 0, t_b1stride = 0, t_b1len = 0, t_a4row = 0,
-          t_a4col = 0, t_a4kp = 0, t_b4src = 0, t_b4len = 0, t_ysrc = 0, t_ydst = 0, t_ylen = 0;
+          t_a4col = 0, t_a4kp = 0, t_b4src = 0, t_b4len = 0, t_ysrc = 0, t_ydst = 0, t_ylen = 0,
+          t_seg = 0, t_pseg = 0;
   // byte offsets of the buffers inside d_buf
   size_t o_A1 = 0, o_B1 = 0, o_T1 = 0, o_A4 = 0, o_B4 = 0, o_Wc = 0, o_Y = 0;
 };
@@ -169,6 +170,8 @@ struct WstepArgs {
   const int64_t* a4row;   // per T3 row: {problem, t1 d2 + t2, sector of a2, a2 within it}
   const int64_t* a4col;   // per T3 column (global): {w2, sector of c, c within it}
   const int64_t* a4kp;    // per T3 row: {column base of its problem, K, Kp}
+  const int64_t* seg;     // column runs of one (w2, sector of c): {w2, sector, first k, length}
+  const int64_t* pseg;    // per stage-4 problem (output sector j): {first run, run count}
   int64_t rows, Kpl, qmin, nq;
   int d1, d2, wl, wr;
 };
@@ -211,6 +214,115 @@ __global__ void k_u1_wsteps(WstepArgs a, void* __restrict__ dst) {
     }
     store_split_f<KIND>(dst, r * 2 * a.Kpl + k, a.Kpl, acc);
   }
+}
+
+// The same W-step, one block per T3 row: the row's lookups staged in shared
+// memory (for every left channel w the T1 row base of (sector of a, a2) and
+// q(a), the first column of every (w, s1, s2), and the combined weights Wc of
+// this (t1, t2) for all w2; size wu_smem_bytes()), then each warp takes whole column runs of one
+// (w2, sector of c), lanes over c, so the term loop is uniform across the
+// warp (the runs are 1..~100 columns: with one thread per column the warps
+// straddled runs and diverged). Same terms in the same order per element:
+// bit-identical to k_u1_wsteps.
+template <int KIND>
+__global__ void __launch_bounds__(128) k_u1_wsteps_seg(WstepArgs a, void* __restrict__ dst) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  const int64_t r = blockIdx.x;
+  if (r >= a.rows) return;
+  const int wl = a.wl, d1 = a.d1, d2 = a.d2, wr = a.wr;
+  const int nin = wl * d1 * d2;
+  int64_t* base = reinterpret_cast<int64_t*>(wsm);
+  int64_t* qaw = base + wl;
+  int64_t* c0t = qaw + wl;
+  float* wsh = reinterpret_cast<float*>(c0t + nin);
+  // per warp: the current column run's terms (T1 offset, weight), in order
+  const int nterm_max = wl * d1;
+  int64_t* toff = reinterpret_cast<int64_t*>(wsh + wr * nin + ((wr * nin) & 1)) +
+                  (threadIdx.x >> 5) * nterm_max;
+  float* twt = reinterpret_cast<float*>(reinterpret_cast<int64_t*>(wsh + wr * nin + ((wr * nin) & 1)) +
+                                        (blockDim.x >> 5) * nterm_max) +
+               (threadIdx.x >> 5) * nterm_max;
+  const int64_t j = a.a4row[4 * r], t12 = a.a4row[4 * r + 1], ia2 = a.a4row[4 * r + 2],
+                a2 = a.a4row[4 * r + 3];
+  const int64_t K = a.a4kp[3 * r + 1], Kp = a.a4kp[3 * r + 2];
+  const int64_t qa2 = a.ql[ia2];
+  for (int w = threadIdx.x; w < wl; w += blockDim.x) {
+    const int64_t qa = qa2 - a.qwl[w];
+    int64_t b = -1;
+    if (qa >= a.qmin && qa < a.qmin + a.nq) {
+      const int64_t ia = a.lsec[qa - a.qmin];
+      if (ia >= 0) {
+        const int64_t rs = a.rs1[ia * wl + w];
+        if (rs >= 0) b = a.t1off[ia] + (rs + a2) * a.rowlen[ia];
+      }
+    }
+    base[w] = b;
+    qaw[w] = qa;
+  }
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+    const int w = i / (d1 * d2), ss = i % (d1 * d2);
+    const int64_t qa = qa2 - a.qwl[w];
+    int64_t c0 = -1;
+    if (qa >= a.qmin && qa < a.qmin + a.nq) {
+      const int64_t ia = a.lsec[qa - a.qmin];
+      if (ia >= 0) c0 = a.cs[ia * d1 * d2 + ss];
+    }
+    c0t[i] = c0;
+  }
+  for (int i = threadIdx.x; i < wr * nin; i += blockDim.x) wsh[i] = a.Wc[t12 * wr * nin + i];
+  __syncthreads();
+  for (int64_t k = K + threadIdx.x; k < Kp; k += blockDim.x)  // zero padding
+    store_split_f<KIND>(dst, r * 2 * a.Kpl + k, a.Kpl, 0.0f);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int64_t s0 = a.pseg[2 * j], ns = a.pseg[2 * j + 1];
+  for (int64_t sg = warp; sg < ns; sg += nwarp) {
+    const int64_t* q = a.seg + 4 * (s0 + sg);
+    const int64_t w2 = q[0], qc = a.qr[q[1]], k0 = q[2], len = q[3];
+    const float* wrow = wsh + w2 * nin;
+    // the run's terms in (w, s1) order: candidate t = w d1 + s1 on lane t % 32
+    int nt = 0;
+    for (int t0 = 0; t0 < nterm_max; t0 += 32) {
+      const int t = t0 + lane;
+      bool ok = false;
+      int64_t off = 0;
+      float wt = 0.0f;
+      if (t < nterm_max) {
+        const int w = t / d1, s1 = t % d1;
+        const int64_t b = base[w];
+        const int64_t s2 = qc - qaw[w] - s1;  // s1 + s2 = q(c) - q(a)
+        if (b >= 0 && s2 >= 0 && s2 < d2) {
+          const int64_t c0 = c0t[(w * d1 + s1) * d2 + s2];
+          if (c0 >= 0) {
+            ok = true;
+            off = b + c0;
+            wt = wrow[(w * d1 + s1) * d2 + s2];
+          }
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (ok) {
+        const int pos = nt + __popc(m & ((1u << lane) - 1u));
+        toff[pos] = off;
+        twt[pos] = wt;
+      }
+      nt += __popc(m);
+    }
+    __syncwarp();
+    for (int64_t c = lane; c < len; c += 32) {
+      float acc = 0.0f;
+#pragma unroll 4
+      for (int t = 0; t < nt; ++t) acc = fmaf(twt[t], a.T1[toff[t] + c], acc);
+      store_split_f<KIND>(dst, r * 2 * a.Kpl + k0 + c, a.Kpl, acc);
+    }
+    __syncwarp();  // the next run overwrites this warp's term list
+  }
+}
+
+size_t wu_smem_bytes(int64_t wl, int64_t d1, int64_t d2, int64_t wr) {
+  const int64_t nin = wl * d1 * d2, wf = wr * nin + ((wr * nin) & 1);  // floats, even count
+  const int64_t warps = 128 / 32;
+  return (size_t)(2 * wl + nin) * sizeof(int64_t) + (size_t)wf * sizeof(float) +
+         (size_t)warps * wl * d1 * (sizeof(int64_t) + sizeof(float));
 }
 
 // y segments from the stage-4 output blocks (zeros where a row has no K).
@@ -335,14 +447,19 @@ osmps_status u1_build(osmps_u1_heff* h) {
   h->n_T1 = nT1;
 
   // stage 4: one problem per output sector j of c2
-  std::vector<int64_t> a4row, a4col, a4kp, b4src, b4len, ysrc, ydst, ylen;
+  std::vector<int64_t> a4row, a4col, a4kp, b4src, b4len, ysrc, ydst, ylen, seg, pseg;
   int64_t nY = 0, kpmax4 = 64, ncol = 0;
   for (int64_t j = 0; j < nr; ++j) {
     const int64_t colbase = ncol;
     int64_t K = 0;
+    pseg.push_back((int64_t)seg.size() / 4);
     for (int64_t w2 = 0; w2 < wr; ++w2) {
       const int64_t jc = find_sector(h->qr, h->qr[j] - h->qwr[w2]);
       if (jc < 0) continue;
+      seg.push_back(w2);
+      seg.push_back(jc);
+      seg.push_back(K);
+      seg.push_back(h->chir[jc]);
       for (int64_t c = 0; c < h->chir[jc]; ++c) {
         a4col.push_back(w2);
         a4col.push_back(jc);
@@ -351,6 +468,7 @@ osmps_status u1_build(osmps_u1_heff* h) {
       K += h->chir[jc];
     }
     ncol += K;
+    pseg.push_back((int64_t)seg.size() / 4 - pseg.back());
     const int64_t Kp = K > 0 ? round_up(K, 64) : 0;
     const int64_t N = h->chir[j];
     const int64_t row0 = (int64_t)ylen.size();
@@ -417,6 +535,8 @@ osmps_status u1_build(osmps_u1_heff* h) {
   h->t_a4row = put(a4row);
   h->t_a4col = put(a4col);
   h->t_a4kp = put(a4kp);
+  h->t_seg = put(seg);
+  h->t_pseg = put(pseg);
   h->t_b4src = put(b4src);
   h->t_b4len = put(b4len);
   h->t_ysrc = put(ysrc);
@@ -521,6 +641,8 @@ osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* theta
     a.a4row = T + h->t_a4row;
     a.a4col = T + h->t_a4col;
     a.a4kp = T + h->t_a4kp;
+    a.seg = T + h->t_seg;
+    a.pseg = T + h->t_pseg;
     a.rows = h->rowsA4;
     a.Kpl = h->Kpl4;
     a.qmin = h->qmin;
@@ -530,7 +652,11 @@ osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* theta
     a.wl = (int)h->wl;
     a.wr = (int)h->wr;
     dim3 grid((unsigned)std::max<int64_t>(1, cdiv(h->Kpl4, 256)), (unsigned)h->rowsA4);
-    k_u1_wsteps<KIND><<<grid, 256, 0, s>>>(a, B + h->o_A4);
+    const size_t sm = wu_smem_bytes(h->wl, h->d1, h->d2, h->wr);
+    if (sm <= 48 * 1024)
+      k_u1_wsteps_seg<KIND><<<(unsigned)h->rowsA4, 128, sm, s>>>(a, B + h->o_A4);
+    else
+      k_u1_wsteps<KIND><<<grid, 256, 0, s>>>(a, B + h->o_A4);
     note_launch();
     OSMPS_LAUNCH_CHECK();
   }
