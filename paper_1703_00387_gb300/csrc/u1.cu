@@ -325,16 +325,15 @@ size_t wu_smem_bytes(int64_t wl, int64_t d1, int64_t d2, int64_t wr) {
          (size_t)warps * wl * d1 * (sizeof(int64_t) + sizeof(float));
 }
 
-// y segments from the stage-4 output blocks (zeros where a row has no K).
+// y segments from the stage-4 output blocks (zeros where a row has no K):
+// one warp per row (rows hold one right sector, 1..~100 entries).
 __global__ void k_u1_scatter(const double* __restrict__ Y, const int64_t* __restrict__ ysrc,
                              const int64_t* __restrict__ ydst, const int64_t* __restrict__ ylen,
                              int64_t rows, double* __restrict__ y) {
-  const int64_t r = blockIdx.y;
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= rows) return;
   const int64_t n = ylen[r], src = ysrc[r], d = ydst[r];
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    y[d + k] = src >= 0 ? Y[src + k] : 0.0;
+  for (int64_t k = threadIdx.x & 31; k < n; k += 32) y[d + k] = src >= 0 ? Y[src + k] : 0.0;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -678,10 +677,7 @@ osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* theta
     OSMPS_TRY(gemm_tc_grouped(ctx, g, s));
   }
   if (h->rowsA4 > 0) {
-    int64_t maxlen = 1;
-    for (int64_t c : h->chir) maxlen = std::max(maxlen, c);
-    dim3 grid((unsigned)cdiv(maxlen, 256), (unsigned)h->rowsA4);
-    k_u1_scatter<<<grid, 256, 0, s>>>(reinterpret_cast<const double*>(B + h->o_Y), T + h->t_ysrc,
+    k_u1_scatter<<<(unsigned)cdiv(h->rowsA4, 8), 256, 0, s>>>(reinterpret_cast<const double*>(B + h->o_Y), T + h->t_ysrc,
                                       T + h->t_ydst, T + h->t_ylen, h->rowsA4, y);
     note_launch();
     OSMPS_LAUNCH_CHECK();
