@@ -6,7 +6,7 @@
 // the result against every stored Krylov vector twice (classical
 // Gram-Schmidt, two passes: full reorthogonalisation), normalises, and
 // solves the small tridiagonal problem for the lowest Ritz pair:
-//   * the eigenvalue by Sturm-count multisection (64 points per round, one warp),
+//   * the eigenvalue by Sturm-count multisection (128 points per round),
 //   * its eigenvector by inverse iteration with a partially pivoted
 //     tridiagonal LU (Gaussian elimination with row interchanges).
 // The stopping test (residual estimate beta_j |s_j| <= tol, the iteration
@@ -233,34 +233,54 @@ __global__ void k_combine_scalar(const double* __restrict__ V, int64_t ld,
 }
 
 // Step j = state J: record alpha_j, beta_j, then the lowest eigenpair of
-// T_{j+1}; one warp.
-//   * Eigenvalue: multisection on division-free Sturm counts (sturm.cuh),
-//     64 points per round (two per lane, independent chains), from the
-//     Gershgorin interval down to 4e-16 relative width.
+// T_{j+1}; one block of four warps (one per SM sub-partition: the float64
+// pipe of a sub-partition is the limit for a single warp).
+//   * Eigenvalue: multisection, 128 points per round (one per thread),
+//     from the Gershgorin interval: first on float32 Sturm counts of T/||T||
+//     down to 1e-5 ||T|| (the float32 pipe is far wider), then the bracket
+//     is padded, checked with float64 counts at its ends (the full interval
+//     again if the check fails), and narrowed to 4e-16 relative width on
+//     division-free float64 counts (sturm.cuh).
 //   * Eigenvector: inverse iteration, three solves from a flat start with one
 //     partially pivoted LU factorisation of T - e I (Gaussian elimination
-//     with row interchanges, lane 0); the reciprocals of the pivots are taken
-//     once, in parallel across the warp, so the solves are multiply-adds only.
-// A dependent float64 operation costs tens of cycles on this GPU and a
-// division hundreds, so the per-call chain holds one run of m divisions (the
-// factorisation) and none in the multisection.
+//     with row interchanges, thread 0); the reciprocals of the pivots are
+//     taken once, in parallel, so the solves are multiply-adds only.
 // Then the stopping decision: a non-finite Ritz value or residual; converged
 // (residual estimate <= tol, beta = 0, or the Krylov space is the whole
 // space); the step cap. Without a stop, J advances. With set_cond, the
 // decision is also the loop condition of the CUDA graph this kernel runs in
 // (1 = run another step), so a graph loop ends after at most max_iter steps:
 // J only advances below max_iter - 1.
-__global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int max_iter, double tol,
-                                                long long n, cudaGraphConditionalHandle cond,
-                                                int set_cond) {
+constexpr int TRI_THREADS = 128;
+
+// The first thread index whose flag is set (TRI_THREADS if none), for every
+// thread of the block; flags grow with the index (Sturm counts grow with x).
+__device__ __forceinline__ int first_set(bool flag, int* sh4) {
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sh4[warp] = m ? warp * 32 + __ffs(m) - 1 : TRI_THREADS;
+  __syncthreads();
+  int t = TRI_THREADS;
+  for (int w = 0; w < TRI_THREADS / 32; ++w) t = min(t, sh4[w]);
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(TRI_THREADS) k_tridiag(double* __restrict__ sc, int max_iter,
+                                                         double tol, long long n,
+                                                         cudaGraphConditionalHandle cond,
+                                                         int set_cond) {
   __shared__ double a[MAXIT], b[MAXIT], b2[MAXIT], x[MAXIT], dd[MAXIT], du[MAXIT], du2[MAXIT],
       ml[MAXIT], rd[MAXIT];
+  __shared__ float af[MAXIT], b2f[MAXIT];
   __shared__ unsigned char piv[MAXIT];
+  __shared__ double red[2][TRI_THREADS / 32];
+  __shared__ int sh4[TRI_THREADS / 32];
   int* st = lz_state(sc);
   const int j = st[ST_J];
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (j < 0 || j >= max_iter || j >= MAXIT) {  // not reachable from the drivers below
-    if (lane == 0) {
+    if (tid == 0) {
       st[ST_STOP] = STOP_NONFINITE;
       st[ST_M] = 1;
       if (set_cond) cudaGraphSetConditional(cond, 0u);
@@ -268,19 +288,19 @@ __global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int max
     return;
   }
   const int m = j + 1;
-  if (lane == 0) {
+  if (tid == 0) {
     sc[OFF_ALPHA + j] = sc[OFF_C1 + j] + sc[OFF_C2 + j];
     sc[OFF_BETA + j] = sqrt(sc[OFF_MISC + 3]);
   }
-  __syncwarp();
-  for (int i = lane; i < m; i += 32) {
+  __syncthreads();
+  for (int i = tid; i < m; i += TRI_THREADS) {
     a[i] = sc[OFF_ALPHA + i];
     b[i] = sc[OFF_BETA + i];  // b[i] couples i and i+1 (b[j] is the residual norm)
     b2[i] = b[i] * b[i];
   }
-  __syncwarp();
+  __syncthreads();
   double l = 1e300, h = -1e300;
-  for (int i = lane; i < m; i += 32) {
+  for (int i = tid; i < m; i += TRI_THREADS) {
     const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
     l = fmin(l, a[i] - r);
     h = fmax(h, a[i] + r);
@@ -289,30 +309,80 @@ __global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int max
     l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
     h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
   }
-  const double pad = 1e-12 * fmax(fabs(l), fabs(h)) + 1e-300;
-  double lo = l - pad, hi = h + pad;
-  for (int round = 0; round < 16; ++round) {
-    if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
-    const double step = (hi - lo) * (1.0 / 65.0);
-    const double xs[2] = {lo + step * (double)(2 * lane + 1), lo + step * (double)(2 * lane + 2)};
-    int c[2];
-    sturm_counts<2>(a, b2, m, xs, c);
-    // counts grow with x: the first point with a count >= 1 brackets the
-    // lowest eigenvalue from above, its predecessor from below
-    const unsigned h0 = __ballot_sync(0xffffffffu, c[0] >= 1);
-    const unsigned h1 = __ballot_sync(0xffffffffu, c[1] >= 1);
-    int t = 64;
-    if (h1) {
-      const int l1 = __ffs(h1) - 1;
-      t = 2 * l1 + (((h0 >> l1) & 1u) ? 0 : 1);
-    }
+  if (lane == 0) {
+    red[0][warp] = l;
+    red[1][warp] = h;
+  }
+  __syncthreads();
+  l = red[0][0];
+  h = red[1][0];
+  for (int w = 1; w < TRI_THREADS / 32; ++w) {
+    l = fmin(l, red[0][w]);
+    h = fmax(h, red[1][w]);
+  }
+  const double tn = fmax(fabs(l), fabs(h)) + 1e-300;
+  const double pad = 1e-12 * tn + 1e-300;
+  const double gl = l - pad, gh = h + pad;  // the Gershgorin interval
+  // float32 phase on T / tn
+  const double inv = 1.0 / tn;
+  for (int i = tid; i < m; i += TRI_THREADS) {
+    af[i] = (float)(a[i] * inv);
+    b2f[i] = (float)(b2[i] * inv * inv);
+  }
+  __syncthreads();
+  double lo = gl, hi = gh;
+  for (int round = 0; round < 8; ++round) {
+    if (!(hi - lo > 1e-5 * tn)) break;
+    const double step = (hi - lo) * (1.0 / (TRI_THREADS + 1));
+    const double xt = lo + step * (double)(tid + 1);
+    const bool hit = sturm_count_f32(af, b2f, m, (float)(xt * inv)) >= 1;
+    const int t = first_set(hit, sh4);
     const double nlo = lo + step * (double)t;
-    const double nhi = (t < 64) ? lo + step * (double)(t + 1) : hi;
+    const double nhi = (t < TRI_THREADS) ? lo + step * (double)(t + 1) : hi;
     lo = nlo;
     hi = nhi;
   }
+  // float64 phase: the padded bracket, its ends checked in the first round
+  {
+    const double fpad = 4e-5 * tn;
+    lo = fmax(gl, lo - fpad);
+    hi = fmin(gh, hi + fpad);
+  }
+  bool check = true;  // this round includes the bracket's ends
+  for (int round = 0; round < 40; ++round) {
+    if (!check && !(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
+    double xt, step;
+    if (check) {  // points lo, ..., hi (ends included)
+      step = (hi - lo) * (1.0 / (TRI_THREADS - 1));
+      xt = (tid == TRI_THREADS - 1) ? hi : lo + step * (double)tid;
+    } else {
+      step = (hi - lo) * (1.0 / (TRI_THREADS + 1));
+      xt = lo + step * (double)(tid + 1);
+    }
+    const double xs[1] = {xt};
+    int c[1];
+    sturm_counts<1>(a, b2, m, xs, c);
+    const int t = first_set(c[0] >= 1, sh4);
+    if (check) {
+      check = false;
+      if (t == 0 || t == TRI_THREADS) {  // the float32 bracket missed: the full interval
+        lo = gl;
+        hi = gh;
+        continue;
+      }
+      const double nlo = lo + step * (double)(t - 1);
+      const double nhi = (t == TRI_THREADS - 1) ? hi : lo + step * (double)t;
+      lo = nlo;
+      hi = nhi;
+    } else {
+      const double nlo = lo + step * (double)t;
+      const double nhi = (t < TRI_THREADS) ? lo + step * (double)(t + 1) : hi;
+      lo = nlo;
+      hi = nhi;
+    }
+  }
   const double e = 0.5 * (lo + hi);
-  if (lane == 0) {
+  if (tid == 0) {
     double tnorm = 0.0;
     for (int i = 0; i < m; ++i) tnorm = fmax(tnorm, fabs(a[i]) + 2.0 * fabs(b[i]));
     const double tiny = 1e-300 + 1e-18 * tnorm;
@@ -348,10 +418,10 @@ __global__ void __launch_bounds__(32) k_tridiag(double* __restrict__ sc, int max
     }
     if (dd[m - 1] == 0.0) dd[m - 1] = tiny;
   }
-  __syncwarp();
-  for (int i = lane; i < m; i += 32) rd[i] = 1.0 / dd[i];
-  __syncwarp();
-  if (lane == 0) {
+  __syncthreads();
+  for (int i = tid; i < m; i += TRI_THREADS) rd[i] = 1.0 / dd[i];
+  __syncthreads();
+  if (tid == 0) {
     const double x0 = 1.0 / sqrt((double)m);
     for (int i = 0; i < m; ++i) x[i] = x0;
     for (int iter = 0; iter < 3; ++iter) {
@@ -624,7 +694,7 @@ osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter
     OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C1, q, state));
     OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C2, q, state));
     OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, q));
-    { k_tridiag<<<1, 32, 0, q>>>(sc, max_iter, tol, (long long)n, cond, set_cond); note_launch(); }
+    { k_tridiag<<<1, TRI_THREADS, 0, q>>>(sc, max_iter, tol, (long long)n, cond, set_cond); note_launch(); }
     OSMPS_LAUNCH_CHECK();
     { k_next_vector<<<ew_blocks(n), 256, 0, q>>>(V, ld, w, n, sc); note_launch(); }
     OSMPS_LAUNCH_CHECK();

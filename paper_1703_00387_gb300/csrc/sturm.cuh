@@ -54,4 +54,34 @@ __device__ __forceinline__ void sturm_counts(const double* __restrict__ d,
   }
 }
 
+// The same count in float32 (d, e2, x as floats), for narrowing a bracket
+// before the float64 count resolves it: the count is exact for a tridiagonal
+// within a few float32 ulps of T (entrywise), so it can misplace an
+// eigenvalue by a few ulps of ||T||, no more. float32 has an 8-bit exponent:
+// the minors are rescaled every 4 rows, and out of range at 2^+-60.
+__device__ __forceinline__ int sturm_count_f32(const float* __restrict__ d,
+                                               const float* __restrict__ e2, int n, float x) {
+  float pm = 0.0f, p = 1.0f;
+  int c = 0;
+  for (int i = 0; i < n; ++i) {
+    const float ei = i > 0 ? e2[i - 1] : 0.0f;
+    float pn = fmaf(d[i] - x, p, -ei * pm);
+    const bool prev_neg = __float_as_int(p) < 0;
+    if ((__float_as_int(pn) << 1) == 0) pn = prev_neg ? FLT_MIN : -FLT_MIN;
+    c += (__float_as_int(pn) < 0) != prev_neg;
+    pm = p;
+    p = pn;
+    if ((i & 3) == 3) {
+      const int bp = (__float_as_int(p) >> 23) & 0xFF, bq = (__float_as_int(pm) >> 23) & 0xFF;
+      const int e = bp > bq ? bp : bq;  // biased exponent of the larger
+      if (e < 127 - 60 || e > 127 + 60) {
+        const float f = __int_as_float((254 - e) << 23);  // 2^(127 - e)
+        p *= f;
+        pm *= f;
+      }
+    }
+  }
+  return c;
+}
+
 }  // namespace osmps
