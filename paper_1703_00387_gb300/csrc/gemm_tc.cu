@@ -16,7 +16,8 @@
 //                      commits each stage back to the producer and each
 //                      16-MMA partial sum to the epilogue
 //   warps 2..17      : epilogue, TMEM partial sums -> float32 registers
-//                      (round-to-nearest adds) -> global (f32 or f64)
+//                      (round-to-nearest adds) -> shared-memory staging ->
+//                      row-contiguous global stores (f32 or f64)
 // Every mbarrier wait is bounded by %globaltimer (2 s); on expiry the kernel
 // records bit 0 in the context's error flag, drains its own copies (bounded),
 // frees TMEM and returns.
@@ -46,35 +47,46 @@ constexpr int EPI_COLS = BN / 4;             // columns per epilogue thread
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int CHUNK = 4;                     // K slices (x 4 MMAs) per TMEM partial sum
 constexpr uint32_t TMEM_COLS = 512;          // two 256-column accumulator buffers
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+// epilogue staging: per epilogue warp 32 rows x 16 columns of float32
+constexpr int STG_COLS = 16;
+constexpr int STG_BYTES = EPI_WARPS * 32 * STG_COLS * 4;  // 32 KB
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + STG_BYTES;
 
+// One epilogue warp's 32 x 64 results (lane = row, acc = its 64 columns) to
+// global memory, through its 32 x 16 float32 staging block in 4 passes: the
+// lanes write their rows (float4 groups XOR-swizzled by row), then each
+// half-warp stores 16 consecutive columns of one row, so a store instruction
+// covers 2 rows x 16 columns (4 full sectors for float32, 8 for float64)
+// instead of touching 32 rows.
 template <int OUT>
-__device__ __forceinline__ void store_row(void* C, int64_t row, int64_t col0, int64_t N,
-                                          int64_t ldc, const float (&acc)[EPI_COLS]) {
-  if (OUT == TC_OUT_F32) {
-    float* dst = reinterpret_cast<float*>(C) + row * ldc + col0;
-    if (col0 + EPI_COLS <= N && (ldc & 3) == 0 && ((reinterpret_cast<uintptr_t>(C) & 15) == 0)) {
+__device__ __forceinline__ void store_tile_rows(void* C, int64_t row0, int64_t col0, int64_t M,
+                                                int64_t N, int64_t ldc, const float (&acc)[EPI_COLS],
+                                                float* __restrict__ stg, int lane) {
 #pragma unroll
-      for (int j = 0; j < EPI_COLS; j += 4)
-        *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
-    } else {
+  for (int pass = 0; pass < EPI_COLS / STG_COLS; ++pass) {
 #pragma unroll
-      for (int j = 0; j < EPI_COLS; ++j)
-        if (col0 + j < N) dst[j] = acc[j];
+    for (int v = 0; v < STG_COLS / 4; ++v) {
+      const int g = v ^ (lane & 3);
+      reinterpret_cast<float4*>(stg + lane * STG_COLS)[g] =
+          make_float4(acc[STG_COLS * pass + 4 * v], acc[STG_COLS * pass + 4 * v + 1],
+                      acc[STG_COLS * pass + 4 * v + 2], acc[STG_COLS * pass + 4 * v + 3]);
     }
-  } else {
-    double* dst = reinterpret_cast<double*>(C) + row * ldc + col0;
-    const bool vec = col0 + EPI_COLS <= N && (ldc & 1) == 0 &&
-                     ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
-#pragma unroll
-    for (int j = 0; j < EPI_COLS; j += 2) {
-      if (vec) {
-        *reinterpret_cast<double2*>(dst + j) = make_double2((double)acc[j], (double)acc[j + 1]);
-      } else {
-        if (col0 + j < N) dst[j] = (double)acc[j];
-        if (col0 + j + 1 < N) dst[j + 1] = (double)acc[j + 1];
+    __syncwarp();
+    const int cc = lane & 15;
+    const int64_t col = col0 + STG_COLS * pass + cc;
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+      const int rr = 2 * i + (lane >> 4);
+      const float val = stg[rr * STG_COLS + (((cc >> 2) ^ (rr & 3)) << 2) + (cc & 3)];
+      const int64_t row = row0 + rr;
+      if (row < M && col < N) {
+        if (OUT == TC_OUT_F32)
+          reinterpret_cast<float*>(C)[row * ldc + col] = val;
+        else
+          reinterpret_cast<double*>(C)[row * ldc + col] = (double)val;
       }
     }
+    __syncwarp();  // the next pass overwrites the staging block
   }
 }
 
@@ -268,8 +280,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!ok) break;
       // decoded again after the K loop so its fields are not live during it
       const TileJob job = tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob);
-      const int64_t row = job.row0 + q * 32 + lane;
-      if (row < job.M) store_row<OUT>(job.C, row, job.col0 + part * EPI_COLS, job.N, job.ldc, acc);
+      float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * 32 * STG_COLS;
+      store_tile_rows<OUT>(job.C, job.row0 + q * 32, job.col0 + part * EPI_COLS, job.M, job.N,
+                           job.ldc, acc, stg, lane);
     }
     if (!ok) atomicOr(err, 1);
   }
