@@ -1,9 +1,19 @@
-"""Small driver for profiler runs: repeated H_eff.theta products (and
-optionally one full two-site step) at a given bond dimension, with seeded
-inputs and under 2 GB of device memory.
+"""Small driver for profiler runs, with seeded inputs and under 2 GB of
+device memory:
+
+* repeated H_eff.theta products (and optionally one full two-site step) at a
+  given bond dimension;
+* --lanczos-solve: one 20-step Lanczos solve on a symmetric operator, after 3
+  untimed solves, between the profiler's start and stop (for
+  `ncu --profile-from-start off`);
+* --u1: 3 products of the U(1) block-sparse H_eff.theta of the Bose-Hubbard
+  workload (L=64, N=64, d=5, w=4, chi=512 per bond, sites 31 and 32), after
+  3 untimed ones, between the profiler's start and stop.
 
     python -m paper_1703_00387_gb300.profile_heff --chi 1024 --prec bf16x3 --reps 3
     python -m paper_1703_00387_gb300.profile_heff --chi 1024 --step
+    python -m paper_1703_00387_gb300.profile_heff --lanczos-solve --chi 32 --lanczos-mode host
+    python -m paper_1703_00387_gb300.profile_heff --u1
 """
 import argparse
 import time
@@ -20,7 +30,14 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--step", action="store_true",
                     help="also run theta formation + Lanczos + split + env update once")
+    ap.add_argument("--lanczos-solve", action="store_true")
+    ap.add_argument("--lanczos-mode", default="auto", choices=["auto", "host", "graph"])
+    ap.add_argument("--u1", action="store_true")
     args = ap.parse_args()
+    if args.lanczos_solve:
+        return lanczos_solve(args)
+    if args.u1:
+        return u1_products(args)
 
     import torch
     from paper_1703_00387_gb300 import binding as B
@@ -56,6 +73,65 @@ def main():
                            Lo.view(chn, w, chn), precision=args.prec)
         torch.cuda.synchronize()
         print("step done, chi_new", chn)
+    ctx.close()
+
+
+def lanczos_solve(args):
+    import torch
+    from paper_1703_00387_gb300 import binding as B
+    from paper_1703_00387_gb300 import inputs
+
+    chi = args.chi
+    Lh, W1, W2, Rh, th = inputs.random_heff_operands(chi, 2, 2, chi, 5, 5, 5, seed=1)
+    # symmetric H_eff: environments symmetric in (bra, ket), MPO tensors in (t, s)
+    Lh = 0.5 * (Lh + Lh.transpose(2, 1, 0))
+    Rh = 0.5 * (Rh + Rh.transpose(2, 1, 0))
+    W1 = 0.5 * (W1 + W1.transpose(0, 2, 1, 3))
+    W2 = 0.5 * (W2 + W2.transpose(0, 2, 1, 3))
+    ctx = B.Context(0)
+    ctx.set_lanczos_mode(args.lanczos_mode)
+    ops = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (Lh, W1, W2, Rh)]
+    t0 = torch.from_numpy(th).cuda()
+    for _ in range(3):
+        B.osmps_lanczos_ground(ctx, *ops, t0.clone(), max_iter=20, tol=1e-15, precision=args.prec)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    r = B.osmps_lanczos_ground(ctx, *ops, t0.clone(), max_iter=20, tol=1e-15, precision=args.prec)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print("lanczos solve", r)
+    ctx.close()
+
+
+def u1_products(args):
+    import torch
+    from paper_1703_00387_gb300 import binding as B
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+    from paper_1703_00387_gb300 import u1 as pu1
+
+    ctx = B.Context(0)
+    dev = torch.device("cuda:0")
+    W = hamiltonians.bose_hubbard(64, 1.0, 4.0, 4)
+    q = pu1.channel_charges(W)
+    left = inputs.u1_sector_profile(31.0, total=512, width=8.0)
+    right = inputs.u1_sector_profile(33.0, total=512, width=8.0)
+    op = pu1.U1Operator(ctx, left, right, 5, 5, W[31], W[32], q[31], q[33])
+    pl = op.plan
+    t = [torch.from_numpy(inputs.random_dense((n,), seed)).to(dev)
+         for n, seed in ((pl.n_L, 1), (pl.n_R, 2), (pl.n_theta, 3))]
+    W1, W2 = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (W[31], W[32]))
+    y = torch.empty_like(t[2])
+    B.osmps_u1_heff_prepare(ctx, pl, t[0], W1, W2, t[1], precision=args.prec)
+    for _ in range(3):
+        B.osmps_u1_heff_apply(ctx, pl, t[2], y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(3):
+        B.osmps_u1_heff_apply(ctx, pl, t[2], y)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print("u1 products done, n_theta", pl.n_theta)
+    op.close()
     ctx.close()
 
 
