@@ -7,8 +7,7 @@
 // Gram-Schmidt, two passes: full reorthogonalisation), normalises, and
 // solves the small tridiagonal problem for the lowest Ritz pair:
 //   * the eigenvalue by Sturm-count multisection (128 points per round),
-//   * its eigenvector by inverse iteration with a partially pivoted
-//     tridiagonal LU (Gaussian elimination with row interchanges).
+//   * its eigenvector from the twisted factorisation of T - e I.
 // The stopping test (residual estimate beta_j |s_j| <= tol, the iteration
 // cap, an exhausted Krylov space) is taken on the device, by the kernel that
 // solves the tridiagonal problem, and kept with the index of the current
@@ -241,10 +240,10 @@ __global__ void k_combine_scalar(const double* __restrict__ V, int64_t ld,
 //     is padded, checked with float64 counts at its ends (the full interval
 //     again if the check fails), and narrowed to 4e-16 relative width on
 //     division-free float64 counts (sturm.cuh).
-//   * Eigenvector: inverse iteration, three solves from a flat start with one
-//     partially pivoted LU factorisation of T - e I (Gaussian elimination
-//     with row interchanges, thread 0); the reciprocals of the pivots are
-//     taken once, in parallel, so the solves are multiply-adds only.
+//   * Eigenvector: the twisted factorisation of T - e I (top-down and
+//     bottom-up pivot chains on two warps, twist index where |gamma| is
+//     least, the vector by two product chains from it), normalised in
+//     parallel.
 // Then the stopping decision: a non-finite Ritz value or residual; converged
 // (residual estimate <= tol, beta = 0, or the Krylov space is the whole
 // space); the step cap. Without a stop, J advances. With set_cond, the
@@ -270,10 +269,9 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag(double* __restrict__ sc
                                                          double tol, long long n,
                                                          cudaGraphConditionalHandle cond,
                                                          int set_cond) {
-  __shared__ double a[MAXIT], b[MAXIT], b2[MAXIT], x[MAXIT], dd[MAXIT], du[MAXIT], du2[MAXIT],
-      ml[MAXIT], rd[MAXIT];
+  __shared__ double a[MAXIT], b[MAXIT], b2[MAXIT], x[MAXIT], dd[MAXIT], du[MAXIT], ml[MAXIT],
+      rd[MAXIT];
   __shared__ float af[MAXIT], b2f[MAXIT];
-  __shared__ unsigned char piv[MAXIT];
   __shared__ double red[2][TRI_THREADS / 32];
   __shared__ int sh4[TRI_THREADS / 32];
   int* st = lz_state(sc);
@@ -382,72 +380,93 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag(double* __restrict__ sc
     }
   }
   const double e = 0.5 * (lo + hi);
+  // Eigenvector of T - e I by the twisted factorisation: the top-down pivots
+  // dp (T - e I = L D+ L^T, multipliers lq) and the bottom-up pivots dm
+  // (= U D- U^T, multipliers uq) on two warps at once; the twist index r
+  // minimises |gamma_k| = |dp_k + dm_k - (a_k - e)| (gamma_k^-1 is the k-th
+  // diagonal entry of (T - e I)^-1, largest where the eigenvector is); then
+  // z_r = 1, z_i = -lq_i z_(i+1) above r and z_(i+1) = -uq_i z_i below it, the
+  // two product chains again on two warps. A zero pivot becomes a tiny one of
+  // the same sign.
+  const double tiny = 1e-300 + 1e-18 * tn;
   if (tid == 0) {
-    double tnorm = 0.0;
-    for (int i = 0; i < m; ++i) tnorm = fmax(tnorm, fabs(a[i]) + 2.0 * fabs(b[i]));
-    const double tiny = 1e-300 + 1e-18 * tnorm;
-    for (int i = 0; i < m; ++i) {
-      dd[i] = a[i] - e;
-      du[i] = (i < m - 1) ? b[i] : 0.0;
-      du2[i] = 0.0;
-    }
-    // P (T - e I) = L U: row i+1 enters with sub-diagonal b[i]; piv[i] marks
-    // an interchange of rows i and i+1, ml[i] the multiplier, du2[i] the
-    // fill-in on the second superdiagonal.
+    double d = a[0] - e;
     for (int i = 0; i + 1 < m; ++i) {
-      const double sub = b[i];
-      if (fabs(dd[i]) >= fabs(sub)) {
-        if (dd[i] == 0.0) dd[i] = tiny;
-        const double f = sub / dd[i];
-        dd[i + 1] -= f * du[i];
-        ml[i] = f;
-        piv[i] = 0;
-      } else {
-        const double f = dd[i] / sub;
-        const double t = dd[i + 1];
-        dd[i] = sub;
-        dd[i + 1] = du[i] - f * t;
-        du[i] = t;
-        if (i + 2 < m) {
-          du2[i] = du[i + 1];
-          du[i + 1] = -f * du2[i];
-        }
-        ml[i] = f;
-        piv[i] = 1;
-      }
+      if (fabs(d) < tiny) d = d < 0.0 ? -tiny : tiny;
+      dd[i] = d;
+      const double l = b[i] / d;
+      ml[i] = l;
+      d = (a[i + 1] - e) - l * b[i];
     }
-    if (dd[m - 1] == 0.0) dd[m - 1] = tiny;
+    if (fabs(d) < tiny) d = d < 0.0 ? -tiny : tiny;
+    dd[m - 1] = d;
+  } else if (tid == 32) {
+    double d = a[m - 1] - e;
+    for (int i = m - 2; i >= 0; --i) {
+      if (fabs(d) < tiny) d = d < 0.0 ? -tiny : tiny;
+      du[i + 1] = d;
+      const double u = b[i] / d;
+      rd[i] = u;
+      d = (a[i] - e) - u * b[i];
+    }
+    if (fabs(d) < tiny) d = d < 0.0 ? -tiny : tiny;
+    du[0] = d;
   }
   __syncthreads();
-  for (int i = tid; i < m; i += TRI_THREADS) rd[i] = 1.0 / dd[i];
+  // twist index: smallest |gamma|, ties to the smallest index
+  double gbest = 1e308;
+  int rbest = 0;
+  for (int k = tid; k < m; k += TRI_THREADS) {
+    const double g = fabs(dd[k] + du[k] - (a[k] - e));
+    if (g < gbest) {
+      gbest = g;
+      rbest = k;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double go = __shfl_xor_sync(0xffffffffu, gbest, o);
+    const int ro = __shfl_xor_sync(0xffffffffu, rbest, o);
+    if (go < gbest || (go == gbest && ro < rbest)) {
+      gbest = go;
+      rbest = ro;
+    }
+  }
+  if (lane == 0) {
+    red[0][warp] = gbest;
+    sh4[warp] = rbest;
+  }
+  __syncthreads();
+  int r = sh4[0];
+  double gr = red[0][0];
+  for (int w = 1; w < TRI_THREADS / 32; ++w)
+    if (red[0][w] < gr || (red[0][w] == gr && sh4[w] < r)) {
+      gr = red[0][w];
+      r = sh4[w];
+    }
+  __syncthreads();  // red / sh4 are reused below
+  if (tid == 0) {
+    x[r] = 1.0;
+    for (int i = r - 1; i >= 0; --i) x[i] = -ml[i] * x[i + 1];
+  } else if (tid == 32) {
+    for (int i = r; i + 1 < m; ++i) x[i + 1] = -rd[i] * (i == r ? 1.0 : x[i]);
+  }
+  __syncthreads();
+  // normalise (fixed-order block sum)
+  double ss = 0.0;
+  for (int i = tid; i < m; i += TRI_THREADS) ss = fma(x[i], x[i], ss);
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) red[1][warp] = ss;
+  __syncthreads();
+  double nrm2 = 0.0;
+  for (int w = 0; w < TRI_THREADS / 32; ++w) nrm2 += red[1][w];
+  const bool vec_ok = nrm2 > 0.0 && isfinite(nrm2);
+  const double inv_nrm = vec_ok ? 1.0 / sqrt(nrm2) : 0.0;
+  for (int i = tid; i < m; i += TRI_THREADS) {
+    x[i] = vec_ok ? x[i] * inv_nrm : (i == 0 ? 1.0 : 0.0);
+    sc[OFF_S + i] = x[i];
+  }
   __syncthreads();
   if (tid == 0) {
-    const double x0 = 1.0 / sqrt((double)m);
-    for (int i = 0; i < m; ++i) x[i] = x0;
-    for (int iter = 0; iter < 3; ++iter) {
-      for (int i = 0; i + 1 < m; ++i) {  // x <- L^-1 P x
-        if (piv[i]) {
-          const double t = x[i];
-          x[i] = x[i + 1];
-          x[i + 1] = t;
-        }
-        x[i + 1] -= ml[i] * x[i];
-      }
-      x[m - 1] *= rd[m - 1];  // x <- U^-1 x
-      if (m > 1) x[m - 2] = (x[m - 2] - du[m - 2] * x[m - 1]) * rd[m - 2];
-      for (int i = m - 3; i >= 0; --i)
-        x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) * rd[i];
-      double nrm = 0.0;
-      for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
-      nrm = sqrt(nrm);
-      if (!(nrm > 0.0) || !isfinite(nrm)) {
-        for (int i = 0; i < m; ++i) x[i] = (i == 0) ? 1.0 : 0.0;
-        break;
-      }
-      const double inv = 1.0 / nrm;
-      for (int i = 0; i < m; ++i) x[i] *= inv;
-    }
-    for (int i = 0; i < m; ++i) sc[OFF_S + i] = x[i];
     const double res = b[j] * fabs(x[m - 1]);
     sc[OFF_MISC + 0] = e;
     sc[OFF_MISC + 1] = res;
