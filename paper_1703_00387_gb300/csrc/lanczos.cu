@@ -486,27 +486,21 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag(double* __restrict__ sc
 }
 
 // Next Krylov vector V[J] = w / beta_{J-1} after a step that did not stop
-// (the same arithmetic as vec_scale_by_inv).
+// (the same arithmetic as vec_scale_by_inv), also into x when it is set: the
+// fixed input buffer of the matrix-vector product recorded in the step graph.
 __global__ void k_next_vector(double* __restrict__ V, int64_t ld, const double* __restrict__ w,
-                              int64_t n, const double* __restrict__ sc) {
+                              int64_t n, const double* __restrict__ sc, double* __restrict__ x) {
   const int* st = lz_state(sc);
   if (st[ST_STOP] != STOP_NONE) return;
   const int jn = st[ST_J];
   const double f = 1.0 / sc[OFF_BETA + jn - 1];
   double* y = V + (int64_t)jn * ld;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = w[i] * f;
-}
-
-// x = V[J]: the fixed input buffer of the matrix-vector product recorded in
-// the step graph.
-__global__ void k_copy_current(const double* __restrict__ V, int64_t ld, double* __restrict__ x,
-                               int64_t n, const double* __restrict__ sc) {
-  const double* v = V + (int64_t)lz_state(sc)[ST_J] * ld;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = v[i];
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[i] * f;
+    y[i] = v;
+    if (x) x[i] = v;
+  }
 }
 
 // First node of the step graph: enter the loop only if the step run before
@@ -696,15 +690,12 @@ osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter
   OSMPS_CUDA(cudaMemsetAsync(state, 0, 4 * sizeof(int), s));
 
   // One step on stream q: w = H_eff V[J] (x is V[J] itself, or the buffer X
-  // that k_copy_current fills), projected out of the projector rows and
-  // twice out of V[0..J], its norm, the tridiagonal solve with the stopping
-  // decision, and V[J+1]. final_blocks bounds J + 1.
+  // that the previous step's k_next_vector filled), projected out of the
+  // projector rows and twice out of V[0..J], its norm, the tridiagonal solve
+  // with the stopping decision, and V[J+1] (and its copy in X, when there is
+  // one). final_blocks bounds J + 1.
   auto step = [&](cudaStream_t q, const double* x, int final_blocks,
                   cudaGraphConditionalHandle cond, int set_cond) -> osmps_status {
-    if (x == X) {
-      { k_copy_current<<<ew_blocks(n), 256, 0, q>>>(V, ld, X, n, sc); note_launch(); }
-      OSMPS_LAUNCH_CHECK();
-    }
     OSMPS_TRY(matvec(x, w, q));
     if (kp > 0) {  // the operator restricted to the complement: w <- (1 - P^T P) H v_j
       OSMPS_TRY(project(ctx, P, ldp, n, kp, w, part, sc + OFF_PROJ, q));
@@ -715,7 +706,7 @@ osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter
     OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, q));
     { k_tridiag<<<1, TRI_THREADS, 0, q>>>(sc, max_iter, tol, (long long)n, cond, set_cond); note_launch(); }
     OSMPS_LAUNCH_CHECK();
-    { k_next_vector<<<ew_blocks(n), 256, 0, q>>>(V, ld, w, n, sc); note_launch(); }
+    { k_next_vector<<<ew_blocks(n), 256, 0, q>>>(V, ld, w, n, sc, X); note_launch(); }
     OSMPS_LAUNCH_CHECK();
     return OSMPS_OK;
   };
