@@ -22,6 +22,10 @@ following the paper's steps in order:
 * ``grad``   -- gradients for the differentiation workload: the vector-Jacobian
                 product of H_eff.theta and dE/dW_k of the MPO energy at a
                 fixed state, with the chain rule to XXZ couplings.
+* ``tdvp``   -- real-time evolution (Sec. 5.4, two-site TDVP) in complex128:
+                complex environments, one- and two-site H_eff, the Krylov
+                propagator of Eq. krylov:approx, the complex SVD split and the
+                symmetric second-order time step.
 
 Parity status: every function is pinned by a test in ``tests/test_oracle_*.py``
 against exact diagonalisation, a closed form, the paper's worked example, or a
