@@ -219,6 +219,32 @@ osmps_status osmps_lanczos_ground(osmps_ctx* ctx, const double* L, const double*
                                   int precision, double* energy_out, int* iters_out,
                                   double* resid_out, void* stream);
 
+/* Krylov propagator theta <- exp(-i tau H_eff) theta (Sec. 5.2, Eq. propSE
+ * and Eq. krylov:approx), the local step of the two-site TDVP (Sec. 5.4).
+ * L (chi_l, wl, chi_l), R (chi_r, wr, chi_r) and theta_inout
+ * (chi_l, d1, d2, chi_r) are COMPLEX: interleaved (re, im) float64 pairs,
+ * the layout of C99 double complex / complex128; W1, W2 are real, as in
+ * osmps_heff_apply. H_eff is the same contraction as in osmps_heff_apply;
+ * the environments' first index is the conjugated (bra) one, so a Hermitian
+ * MPO gives a Hermitian H_eff. A one-site H_eff is the case d2 = 1 with
+ * W2[w,0,0,w2] = delta(w, w2).
+ * The Krylov basis starts from theta / ||theta|| with full float64
+ * reorthogonalisation; with m vectors the result is
+ * ||theta|| V exp(-i tau T_m) e_1. It stops when the weight leaving the
+ * space, beta_m |[exp(-i tau T_m) e_1]_m|, is <= tol, when the space is
+ * exhausted, or at max_iter vectors (1 <= max_iter <= 128). The norm is kept
+ * (the propagator is unitary). iters_out, err_out (may be NULL): host
+ * pointers to the vector count and the last estimate. Returns ENOCONV at
+ * max_iter above tol (the result is still written), ENAN on non-finite
+ * Krylov data (theta_inout unchanged). Uses the same workspace as
+ * osmps_lanczos_ground, plus three slots for the real embedding of L, R and
+ * theta (16 chi^2 w and 32 chi_l d1 d2 chi_r bytes). Synchronises `stream`. */
+osmps_status osmps_heff_expm(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
+                             const double* R, double* theta_inout, int64_t chi_l, int64_t d1,
+                             int64_t d2, int64_t chi_r, int64_t wl, int64_t wm, int64_t wr,
+                             double tau, int max_iter, double tol, int precision, int* iters_out,
+                             double* err_out, void* stream);
+
 /* Two-site tensor (Sec. 2, "Contractions"): theta[a,s1,s2,c] = sum_b A1[a,s1,b] A2[b,s2,c].
  * A1: (chi_l, d1, chi_m), A2: (chi_m, d2, chi_r), theta: (chi_l, d1, d2, chi_r). */
 osmps_status osmps_theta_form(osmps_ctx* ctx, const double* A1, const double* A2, double* theta,

@@ -82,6 +82,9 @@ _SIGS = {
     "osmps_lanczos_ground_projected": (_c.c_int, [_vp] * 7 + [_c.c_int] + [_i64] * 7 +
                                        [_c.c_int, _c.c_double, _c.c_int, _dp, _c.POINTER(_c.c_int),
                                         _dp, _vp]),
+    "osmps_heff_expm": (_c.c_int, [_vp] * 6 + [_i64] * 7 +
+                        [_c.c_double, _c.c_int, _c.c_double, _c.c_int, _c.POINTER(_c.c_int), _dp,
+                         _vp]),
     "osmps_overlap_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_vp]),
     "osmps_projected_state": (_c.c_int, [_vp] * 6 + [_i64] * 7 + [_vp]),
     "osmps_theta_form": (_c.c_int, [_vp, _vp, _vp, _vp] + [_i64] * 5 + [_vp]),
@@ -153,6 +156,15 @@ def _dev(t, name):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
         raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return _vp(t.data_ptr())
+
+
+def _devc(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be a complex128 CUDA tensor")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return _vp(t.data_ptr())
@@ -278,6 +290,23 @@ def osmps_lanczos_ground(ctx, L, W1, W2, R, theta, max_iter=100, tol=1e-12, prec
                                     _c.byref(e), _c.byref(it), _c.byref(res), _stream(stream))
     _check(st, allow=(ENOCONV,) if allow_noconv else ())
     return e.value, it.value, res.value, st == 0
+
+
+def osmps_heff_expm(ctx, L, W1, W2, R, theta, tau, max_iter=40, tol=1e-12, precision="fp64",
+                    stream=None, allow_noconv=True):
+    """theta <- exp(-i tau H_eff) theta in place by the Krylov propagator.
+    L, R, theta are complex128 tensors (L[a2,w,a], R[c2,w,c], theta[a,s1,s2,c]),
+    W1, W2 float64. Returns (Krylov vectors used, error estimate, converged)."""
+    chi_l, d1, d2, chi_r = theta.shape
+    wl, wm, wr = W1.shape[0], W1.shape[3], W2.shape[3]
+    it = _c.c_int()
+    err = _c.c_double()
+    st = lib().osmps_heff_expm(ctx.ptr, _devc(L, "L"), _dev(W1, "W1"), _dev(W2, "W2"),
+                               _devc(R, "R"), _devc(theta, "theta"), chi_l, d1, d2, chi_r, wl,
+                               wm, wr, float(tau), int(max_iter), float(tol), _prec(precision),
+                               _c.byref(it), _c.byref(err), _stream(stream))
+    _check(st, allow=(ENOCONV,) if allow_noconv else ())
+    return it.value, err.value, st == 0
 
 
 def osmps_theta_form(ctx, A1, A2, theta, stream=None):

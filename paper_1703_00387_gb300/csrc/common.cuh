@@ -109,6 +109,9 @@ enum Slot {
   SLOT_GRAD_T,
   SLOT_GRAD_PART,
   SLOT_GRAD_ENVS,
+  SLOT_CX_L,
+  SLOT_CX_R,
+  SLOT_CX_THETA,
   SLOT_COUNT
 };
 

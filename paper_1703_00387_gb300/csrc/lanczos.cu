@@ -40,7 +40,9 @@ constexpr int OFF_MISC = 5 * MAXIT;  // [0] e, [1] resid, [2] beta, [3] ||w||^2,
 constexpr int OFF_STATE = OFF_MISC + 8;  // 4 ints in two double slots, below
 constexpr int OFF_PROJ = 5 * MAXIT + 16;  // coefficients against the projector rows
 constexpr int MAX_PROJ = 64;
-constexpr int SCAL_COUNT = 5 * MAXIT + 16 + 2 * MAX_PROJ;
+constexpr int OFF_URE = 5 * MAXIT + 16 + 2 * MAX_PROJ;  // exp(-i tau T) e_1 (Krylov propagator)
+constexpr int OFF_UIM = OFF_URE + MAXIT;
+constexpr int SCAL_COUNT = OFF_UIM + MAXIT;
 constexpr int MISC_READ = 10;  // doubles of OFF_MISC the host reads (the state included)
 
 // Iteration state (ints at OFF_STATE): the index J of the Krylov vector the
@@ -905,3 +907,342 @@ extern "C" osmps_status osmps_lanczos_ground_projected(
                       Q, ld, k, key, 9);
 }
 
+
+// ---------------------------------------------------------------------------
+// Krylov propagator exp(-i tau H_eff) theta (Sec. 5.2, Eq. propSE and
+// Eq. krylov:approx), the local step of the two-site TDVP (Sec. 5.4).
+//
+// Complex tensors enter as interleaved (re, im) float64 pairs and are worked
+// on in the real 2x2 embedding z = x + iy -> [[x, -y], [y, x]] applied to
+// every bond index pair: a complex tensor X[r, w, c] becomes the real
+// X~[(p, r), w, (q, c)] with the (p, q) block of each element. The embedding
+// turns products into products, so the real H_eff.theta of the ground-state
+// search, given L~ = emb(L), R~ = emb(conj R) and theta~ = emb(theta) at
+// bond dimensions 2 chi_l, 2 chi_r, computes emb(H_eff theta) exactly. Real
+// Lanczos on embedded vectors reproduces the complex Lanczos recurrence (its
+// alpha and beta are real for a Hermitian H_eff), so the Krylov basis, the
+// reorthogonalisation and the tridiagonal T are the ground-state path's
+// kernels. Multiplying by i is the map J(B) = B [[0, -1], [1, 0]] on the q
+// blocks, used once in the final combination.
+// ---------------------------------------------------------------------------
+namespace osmps {
+namespace {
+
+constexpr int EXPM_THREADS = 128;
+constexpr int EXPM_MAXIT = EXPM_THREADS;  // one thread per Krylov coordinate
+constexpr int EXPM_TAYLOR = 18;  // terms per substep with |h| ||T|| <= 1: remainder below 1/19!
+constexpr int EXPM_MAX_SUBSTEPS = 1 << 16;
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = red[0];
+  for (int k = 1; k < EXPM_THREADS / 32; ++k) r = fmax(r, red[k]);
+  return r;
+}
+
+// Step j = state J of the propagator: record alpha_j and beta_j as the
+// ground-state kernel does, then u = exp(-i tau T_m) e_1 for the leading
+// m = j + 1 rows of T. u comes from the Taylor series applied to e_1 in s
+// substeps of length h = tau / s, s the smallest count with |h| g <= 1 for
+// the Gershgorin bound g of T_m, EXPM_TAYLOR terms each; one thread per
+// coordinate, each term one tridiagonal product. (The float64 eigensolver
+// chains are long on this GPU: a dependent float64 operation takes 64
+// cycles, a division 628.) The weight leaving the space is estimated as
+// beta_j |u_{m-1}|; the space counts as exhausted when beta_j <= 1e-14 times
+// max|alpha| + max|beta| of T_m. u goes to OFF_URE / OFF_UIM, the estimate
+// to OFF_MISC + 1, and the stop decision to the state.
+__global__ void __launch_bounds__(EXPM_THREADS) k_expm_tridiag(double* __restrict__ sc,
+                                                               int max_iter, double tol,
+                                                               double tau, long long n) {
+  __shared__ double a[EXPM_MAXIT], b[EXPM_MAXIT], tr[EXPM_MAXIT], ti[EXPM_MAXIT];
+  __shared__ double red[EXPM_THREADS / 32];
+  int* st = lz_state(sc);
+  const int j = st[ST_J];
+  const int i = threadIdx.x;
+  if (j < 0 || j >= max_iter || j >= EXPM_MAXIT) {  // not reachable from the driver below
+    if (i == 0) {
+      st[ST_STOP] = STOP_NONFINITE;
+      st[ST_M] = 1;
+    }
+    return;
+  }
+  const int m = j + 1;
+  if (i == 0) {
+    sc[OFF_ALPHA + j] = sc[OFF_C1 + j] + sc[OFF_C2 + j];
+    sc[OFF_BETA + j] = sqrt(sc[OFF_MISC + 3]);
+  }
+  __syncthreads();
+  const bool act = i < m;
+  if (act) {
+    a[i] = sc[OFF_ALPHA + i];
+    b[i] = sc[OFF_BETA + i];  // b[i] couples i and i+1; b[m-1] = beta_j is the residual
+  }
+  __syncthreads();
+  double gi = 0.0, ai = 0.0, bi = 0.0;
+  if (act) {
+    ai = fabs(a[i]);
+    bi = (i < m - 1) ? fabs(b[i]) : 0.0;
+    gi = ai + bi + (i > 0 ? fabs(b[i - 1]) : 0.0);
+  }
+  const double g = block_max(gi, red);
+  const double amax = block_max(ai, red);
+  const double bmax = block_max(bi, red);
+  const double bj = b[m - 1];
+  const double steps = ceil(fabs(tau) * g);
+  if (!isfinite(g) || !isfinite(bj) || !(steps <= (double)EXPM_MAX_SUBSTEPS)) {
+    if (i == 0) {
+      st[ST_STOP] = STOP_NONFINITE;
+      st[ST_M] = m;
+    }
+    return;
+  }
+  const int nsub = steps < 1.0 ? 1 : (int)steps;
+  const double h = tau / nsub;
+  // u = e_1, then nsub times u <- sum_k (-i h T)^k u / k!
+  double yr = (i == 0) ? 1.0 : 0.0, yi = 0.0;
+  const double al = act ? a[i] : 0.0;
+  const double bl = (act && i > 0) ? b[i - 1] : 0.0;
+  const double br = (act && i < m - 1) ? b[i] : 0.0;
+  for (int sub = 0; sub < nsub; ++sub) {
+    if (act) {
+      tr[i] = yr;
+      ti[i] = yi;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 1; k <= EXPM_TAYLOR; ++k) {
+      double pr = 0.0, pi = 0.0;  // (T t)_i
+      if (act) {
+        pr = al * tr[i];
+        pi = al * ti[i];
+        if (i > 0) {
+          pr = fma(bl, tr[i - 1], pr);
+          pi = fma(bl, ti[i - 1], pi);
+        }
+        if (i < m - 1) {
+          pr = fma(br, tr[i + 1], pr);
+          pi = fma(br, ti[i + 1], pi);
+        }
+      }
+      __syncthreads();
+      // (-i h T)(t_r + i t_i) / k = (h T t_i - i h T t_r) / k
+      const double hk = h * (1.0 / (double)k);
+      if (act) {
+        const double nr = hk * pi, ni = -hk * pr;
+        tr[i] = nr;
+        ti[i] = ni;
+        yr += nr;
+        yi += ni;
+      }
+      __syncthreads();
+    }
+  }
+  if (act) {
+    sc[OFF_URE + i] = yr;
+    sc[OFF_UIM + i] = yi;
+    tr[i] = yr;
+    ti[i] = yi;
+  }
+  __syncthreads();
+  if (i == 0) {
+    const double ul = sqrt(tr[m - 1] * tr[m - 1] + ti[m - 1] * ti[m - 1]);
+    const bool exhausted = bj <= 1e-14 * fmax(amax + bmax, 1e-300);
+    const double err = exhausted ? 0.0 : bj * ul;
+    sc[OFF_MISC + 1] = err;
+    sc[OFF_MISC + 2] = bj;
+    int stop = STOP_NONE;
+    if (!isfinite(err) || !isfinite(tr[0]) || !isfinite(ti[0]))
+      stop = STOP_NONFINITE;
+    else if (exhausted || err <= tol || (long long)m == n)
+      stop = STOP_CONVERGED;
+    else if (m >= max_iter)
+      stop = STOP_CAP;
+    st[ST_M] = m;
+    st[ST_STOP] = stop;
+    if (stop == STOP_NONE) st[ST_J] = j + 1;
+  }
+}
+
+// out = ||theta~|| sum_i u_i v_i, read back from the embedding: with B the
+// (p, q) blocks of the real basis vector v_i at one complex element,
+// sum_i Re(u_i) B + Im(u_i) J(B) averaged over its duplicate blocks. out is
+// interleaved complex [chi_l, D, chi_r]; the embedded vectors are
+// [(p, a), D, (q, c)]. Nothing is written when the iteration stopped on a
+// non-finite value.
+__global__ void k_expm_combine(const double* __restrict__ V, int64_t ld,
+                               const double* __restrict__ sc, double* __restrict__ out,
+                               int64_t chi_l, int64_t D, int64_t chi_r) {
+  __shared__ double ur[EXPM_MAXIT], ui[EXPM_MAXIT];
+  const int* st = lz_state(sc);
+  if (st[ST_STOP] == STOP_NONFINITE) return;
+  const int m = st[ST_M];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    ur[i] = sc[OFF_URE + i];
+    ui[i] = sc[OFF_UIM + i];
+  }
+  __syncthreads();
+  const double scale = 0.5 * sqrt(sc[OFF_MISC + 4]);
+  const int64_t dc = D * chi_r, nc = chi_l * dc, row = 2 * chi_r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nc;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / dc, rem = e - a * dc, s = rem / chi_r, c = rem - s * chi_r;
+    const int64_t o00 = (a * D + s) * row + c, o10 = ((chi_l + a) * D + s) * row + c;
+    double xr = 0.0, xi = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double* v = V + (int64_t)i * ld;
+      const double b00 = v[o00], b01 = v[o00 + chi_r], b10 = v[o10], b11 = v[o10 + chi_r];
+      xr = fma(ur[i], b00 + b11, fma(ui[i], b01 - b10, xr));
+      xi = fma(ur[i], b10 - b01, fma(ui[i], b00 + b11, xi));
+    }
+    out[2 * e] = scale * xr;
+    out[2 * e + 1] = scale * xi;
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// out[((p r + i) w + k) 2c + q c + j] = (p, q) block of z[i, k, j] (or of
+// its conjugate): blocks (0,0) = (1,1) = Re, (1,0) = Im, (0,1) = -Im.
+__global__ void k_embed3(const double* __restrict__ z, double* __restrict__ out, int64_t r,
+                         int64_t w, int64_t c, int conj) {
+  const int64_t wc = w * c, n = r * wc, row = 2 * c, plane = r * w * row;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / wc, rem = e - i * wc, k = rem / c, jj = rem - k * c;
+    const double re = z[2 * e], im = conj ? -z[2 * e + 1] : z[2 * e + 1];
+    const int64_t o = (i * w + k) * row + jj;
+    out[o] = re;
+    out[o + c] = -im;
+    out[plane + o] = im;
+    out[plane + o + c] = re;
+  }
+}
+
+}  // namespace
+
+osmps_status embed_complex(const double* z, double* out, int64_t r, int64_t w, int64_t c,
+                           bool conj, cudaStream_t s) {
+  { k_embed3<<<ew_blocks(r * w * c), 256, 0, s>>>(z, out, r, w, c, conj ? 1 : 0); note_launch(); }
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+// theta_out (interleaved complex, may alias nothing the basis uses) =
+// exp(-i tau H) theta~ read back from the embedding; theta_emb is the
+// embedded start vector of length n4 = 4 n_c, matvec the embedded operator.
+osmps_status expm_core(osmps_ctx* ctx, int64_t n_c, const double* theta_emb, double* theta_out,
+                       int64_t chi_l, int64_t D, int64_t chi_r, double tau, int max_iter,
+                       double tol, const Matvec& matvec, int* iters, double* err, cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  const int64_t n = 4 * n_c;
+  const int64_t ld = n;  // a multiple of 4: 16-byte aligned rows
+  if (max_iter > n_c) max_iter = (int)n_c;
+  double* V = (double*)ws_get(ctx, SLOT_LZ_BASIS, (size_t)max_iter * ld * 8, s, &st);
+  if (!V) return st;
+  double* w = (double*)ws_get(ctx, SLOT_LZ_W, (size_t)n * 8, s, &st);
+  if (!w) return st;
+  double* sc = (double*)ws_get(ctx, SLOT_LZ_SCAL, SCAL_COUNT * 8, s, &st);
+  if (!sc) return st;
+  double* part = (double*)ws_get(ctx, SLOT_LZ_PART, (size_t)MAXIT * DOT_MAX_BLOCKS * 8, s, &st);
+  if (!part) return st;
+  OSMPS_TRY(pinned_reserve(ctx, 16));
+  int* state = lz_state(sc);
+
+  OSMPS_TRY(vec_norm2(ctx, theta_emb, n, sc + OFF_MISC + 4, s));
+  OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC + 4, 8, cudaMemcpyDeviceToHost, s));
+  OSMPS_CUDA(cudaStreamSynchronize(s));
+  if (!(ctx->host_pinned[0] > 0.0) || !std::isfinite(ctx->host_pinned[0]))
+    return set_error(ctx->host_pinned[0] == 0.0 ? OSMPS_EINVAL : OSMPS_ENAN,
+                     "heff_expm: start vector has norm^2 %g", ctx->host_pinned[0] / 2);
+  OSMPS_CUDA(cudaMemcpyAsync(V, theta_emb, n * 8, cudaMemcpyDeviceToDevice, s));
+  OSMPS_TRY(vec_scale_by_inv_sqrt(V, n, sc + OFF_MISC + 4, s));
+  OSMPS_CUDA(cudaMemsetAsync(state, 0, 4 * sizeof(int), s));
+  for (int j = 0; j < max_iter; ++j) {
+    OSMPS_TRY(matvec(V + (int64_t)j * ld, w, s));
+    OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C1, s, state));
+    OSMPS_TRY(project(ctx, V, ld, n, j + 1, w, part, sc + OFF_C2, s, state));
+    OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, s));
+    { k_expm_tridiag<<<1, EXPM_THREADS, 0, s>>>(sc, max_iter, tol, tau, (long long)n_c); note_launch(); }
+    OSMPS_LAUNCH_CHECK();
+    { k_next_vector<<<ew_blocks(n), 256, 0, s>>>(V, ld, w, n, sc, nullptr); note_launch(); }
+    OSMPS_LAUNCH_CHECK();
+    OSMPS_CUDA(cudaMemcpyAsync(ctx->host_pinned, sc + OFF_MISC, MISC_READ * 8,
+                               cudaMemcpyDeviceToHost, s));
+    OSMPS_CUDA(cudaStreamSynchronize(s));
+    if (lz_state_in_misc(ctx->host_pinned)[ST_STOP] != STOP_NONE) break;
+  }
+  { k_expm_combine<<<ew_blocks(n_c), 256, 0, s>>>(V, ld, sc, theta_out, chi_l, D, chi_r); note_launch(); }
+  OSMPS_LAUNCH_CHECK();
+  OSMPS_CUDA(cudaStreamSynchronize(s));
+  const int* hs = lz_state_in_misc(ctx->host_pinned);
+  const int stop = hs[ST_STOP], m = hs[ST_M];
+  const double e = ctx->host_pinned[1];
+  if (stop == STOP_NONFINITE)
+    return set_error(OSMPS_ENAN, "heff_expm: non-finite Krylov data at step %d", m - 1);
+  *iters = m;
+  if (err) *err = e;
+  if (stop != STOP_CONVERGED)
+    return set_error(OSMPS_ENOCONV, "heff_expm: error estimate %.3e above tol %.3e after %d vectors",
+                     e, tol, m);
+  return OSMPS_OK;
+}
+
+// Embedded operands of a complex H_eff: L~ = emb(L), R~ = emb(conj R),
+// prepared for the real H_eff.theta at bond dimensions 2 chi_l, 2 chi_r.
+osmps_status heff_prepare_complex(osmps_ctx* ctx, const double* L, const double* W1,
+                                  const double* W2, const double* R, int64_t chi_l, int64_t d1,
+                                  int64_t d2, int64_t chi_r, int64_t wl, int64_t wm, int64_t wr,
+                                  int precision, cudaStream_t s) {
+  osmps_status st = OSMPS_OK;
+  double* Le = (double*)ws_get(ctx, SLOT_CX_L, (size_t)4 * chi_l * wl * chi_l * 8, s, &st);
+  if (!Le) return st;
+  double* Re = (double*)ws_get(ctx, SLOT_CX_R, (size_t)4 * chi_r * wr * chi_r * 8, s, &st);
+  if (!Re) return st;
+  OSMPS_TRY(embed_complex(L, Le, chi_l, wl, chi_l, false, s));
+  OSMPS_TRY(embed_complex(R, Re, chi_r, wr, chi_r, true, s));
+  return heff_prepare(ctx, Le, W1, W2, Re, 2 * chi_l, d1, d2, 2 * chi_r, wl, wm, wr, precision, s);
+}
+
+}  // namespace osmps
+
+extern "C" osmps_status osmps_heff_expm(osmps_ctx* ctx, const double* L, const double* W1,
+                                        const double* W2, const double* R, double* theta_inout,
+                                        int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r,
+                                        int64_t wl, int64_t wm, int64_t wr, double tau,
+                                        int max_iter, double tol, int precision, int* iters_out,
+                                        double* err_out, void* stream) {
+  clear_error();
+  if (!ctx || !L || !W1 || !W2 || !R || !theta_inout || !iters_out)
+    return set_error(OSMPS_EINVAL, "osmps_heff_expm: null argument");
+  if (max_iter < 1 || max_iter > EXPM_MAXIT)
+    return set_error(OSMPS_EINVAL, "osmps_heff_expm: max_iter %d outside [1, %d]", max_iter,
+                     EXPM_MAXIT);
+  if (!(tol >= 0.0)) return set_error(OSMPS_EINVAL, "osmps_heff_expm: tol %g", tol);
+  if (!std::isfinite(tau)) return set_error(OSMPS_EINVAL, "osmps_heff_expm: tau %g", tau);
+  if (!valid_precision(precision))
+    return set_error(OSMPS_EINVAL, "osmps_heff_expm: precision %d", precision);
+  for (int64_t x : {chi_l, d1, d2, chi_r, wl, wm, wr})
+    if (x <= 0 || x > ((int64_t)1 << 30))
+      return set_error(OSMPS_ESHAPE, "osmps_heff_expm: non-positive or oversized dimension");
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
+  cudaStream_t s = (cudaStream_t)stream;
+  osmps_status st = OSMPS_OK;
+  const int64_t n_c = chi_l * d1 * d2 * chi_r;
+  double* th = (double*)ws_get(ctx, SLOT_CX_THETA, (size_t)4 * n_c * 8, s, &st);
+  if (!th) return st;
+  OSMPS_TRY(heff_prepare_complex(ctx, L, W1, W2, R, chi_l, d1, d2, chi_r, wl, wm, wr, precision, s));
+  OSMPS_TRY(embed_complex(theta_inout, th, chi_l, d1 * d2, chi_r, false, s));
+  const Matvec mv = [&](const double* x, double* y, cudaStream_t q) {
+    return heff_apply_impl(ctx, nullptr, nullptr, nullptr, nullptr, x, y, 2 * chi_l, d1, d2,
+                           2 * chi_r, wl, wm, wr, precision, q, true);
+  };
+  return expm_core(ctx, n_c, th, theta_inout, chi_l, d1 * d2, chi_r, tau, max_iter, tol, mv,
+                   iters_out, err_out, s);
+}

@@ -1,0 +1,147 @@
+"""GPU Krylov propagator exp(-i tau H_eff) theta (the local step of the
+two-site TDVP) against the complex128 oracle, element by element."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mpo
+from oracle import tdvp as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1703_00387_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _operator(L, k, chi, seed, model="xxz"):
+    """Complex environments around the pair (k, k+1) of a random complex MPS
+    (left part left-canonical, right part right-canonical), the MPO tensors
+    and the centre theta."""
+    W = mpo.xxz_mpo(L, 1.0, 0.8, 0.3) if model == "xxz" else mpo.ising_mpo(L, 1.0, 1.1)
+    rng = np.random.default_rng(seed)
+    dims = [min(2 ** j, 2 ** (L - j), chi) for j in range(L + 1)]
+    mps = [rng.standard_normal((dims[j], 2, dims[j + 1]))
+           + 1j * rng.standard_normal((dims[j], 2, dims[j + 1])) for j in range(L)]
+    mps = T.right_canonicalize_c(mps)
+    Renv = T.build_right_envs_c(W, mps)
+    Lenv = np.ones((1, 1, 1), dtype=np.complex128)
+    for j in range(k):
+        chl, d, chr_ = mps[j].shape
+        Q, Rm = np.linalg.qr(mps[j].reshape(chl * d, chr_))
+        mps[j] = Q.reshape(chl, d, Q.shape[1])
+        mps[j + 1] = np.tensordot(Rm, mps[j + 1], axes=([1], [0]))
+        Lenv = T.env_left_c(Lenv, mps[j], W[j])
+    theta = np.tensordot(mps[k], mps[k + 1], axes=([2], [0]))
+    return Lenv, W[k], W[k + 1], Renv[k + 2], theta
+
+
+# (L, k, chi, seed): theta 1x2x2x2, 16x2x2x16 and 24x2x2x24 (ragged tiles)
+CASES = [(3, 0, 8, 1), (10, 4, 24, 2), (12, 5, 24, 3)]
+
+
+@pytest.mark.parametrize("prec,bar", [("fp64", 1e-11), ("fp64emu", 1e-11), ("bf16x3", 3e-5)])
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("tau", [0.05, -0.2])
+def test_heff_expm_matches_oracle(B, ctx, prec, bar, case, tau):
+    Lh, W1, W2, Rh, theta = _operator(*case)
+    mv = lambda x: T.heff2_apply(Lh, W1, W2, Rh, x)
+    ref, m_ref, _ = T.krylov_expm(mv, theta, tau, max_iter=40, tol=1e-12)
+    th = dev(theta)
+    m, err, ok = B.osmps_heff_expm(ctx, dev(Lh), dev(W1), dev(W2), dev(Rh), th, tau,
+                                   max_iter=40, tol=1e-12, precision=prec)
+    got = th.cpu().numpy()
+    assert ok
+    assert np.linalg.norm(got - ref) <= bar * np.linalg.norm(ref)
+    assert np.max(np.abs(got - ref)) <= bar * np.max(np.abs(ref)) * 4
+    if prec != "bf16x3":
+        assert abs(m - m_ref) <= 1
+    # unitary: the norm is kept
+    assert abs(np.linalg.norm(got) - np.linalg.norm(theta)) <= max(bar, 1e-12) * np.linalg.norm(theta)
+
+
+def test_heff_expm_equals_matrix_exponential(B, ctx):
+    # the dense matrix exponential of the explicit H_eff, not the oracle's Krylov loop
+    Lh, W1, W2, Rh, theta = _operator(10, 4, 24, 7)
+    n = theta.size
+    H = np.einsum("xwa,wtsv,vuqz,yzc->xtuyasqc", Lh, W1, W2, Rh).reshape(n, n)
+    assert np.abs(H - H.conj().T).max() <= 1e-12 * np.abs(H).max()
+    tau = 0.1
+    ref = (__import__("scipy.linalg").linalg.expm(-1j * tau * H) @ theta.reshape(-1)).reshape(theta.shape)
+    th = dev(theta)
+    m, err, ok = B.osmps_heff_expm(ctx, dev(Lh), dev(W1), dev(W2), dev(Rh), th, tau,
+                                   max_iter=60, tol=1e-13, precision="fp64")
+    assert ok and err <= 1e-13
+    assert np.linalg.norm(th.cpu().numpy() - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_heff_expm_exhausted_space_is_exact(B, ctx):
+    # n_c = 8 at the left end of an L = 3 chain: the Krylov space runs out
+    Lh, W1, W2, Rh, theta = _operator(3, 0, 8, 4)
+    n = theta.size
+    H = np.einsum("xwa,wtsv,vuqz,yzc->xtuyasqc", Lh, W1, W2, Rh).reshape(n, n)
+    import scipy.linalg
+    ref = (scipy.linalg.expm(-0.7j * H) @ theta.reshape(-1)).reshape(theta.shape)
+    th = dev(theta)
+    m, err, ok = B.osmps_heff_expm(ctx, dev(Lh), dev(W1), dev(W2), dev(Rh), th, 0.7,
+                                   max_iter=40, tol=0.0, precision="fp64")
+    assert ok and m <= n and err <= 1e-13
+    assert np.linalg.norm(th.cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec,bar", [("fp64", 1e-11), ("bf16x3", 3e-5)])
+def test_one_site_backward_step_matches_oracle(B, ctx, prec, bar):
+    # the one-site H_eff as d2 = 1 with an identity second MPO tensor,
+    # evolved backwards as in the TDVP sweep
+    Lh, W1, _, _, _ = _operator(10, 4, 24, 5)
+    Rh2 = _operator(10, 3, 24, 5)[3]  # R environment of sites 5..9 of the same state
+    rng = np.random.default_rng(11)
+    chl, chr_ = Lh.shape[0], Rh2.shape[0]
+    wr = W1.shape[3]
+    assert Rh2.shape[1] == wr
+    C = rng.standard_normal((chl, 2, chr_)) + 1j * rng.standard_normal((chl, 2, chr_))
+    mv = lambda x: T.heff1_apply(Lh, W1, Rh2, x)
+    ref, _, _ = T.krylov_expm(mv, C, -0.05, max_iter=40, tol=1e-12)
+    Wid = np.zeros((wr, 1, 1, wr))
+    for w in range(wr):
+        Wid[w, 0, 0, w] = 1.0
+    th = dev(C.reshape(chl, 2, 1, chr_))
+    m, err, ok = B.osmps_heff_expm(ctx, dev(Lh), dev(W1), dev(Wid), dev(Rh2), th, -0.05,
+                                   max_iter=40, tol=1e-12, precision=prec)
+    assert ok
+    got = th.cpu().numpy().reshape(C.shape)
+    assert np.linalg.norm(got - ref) <= bar * np.linalg.norm(ref)
+
+
+def test_heff_expm_cap_and_validation(B, ctx):
+    Lh, W1, W2, Rh, theta = _operator(10, 4, 24, 2)
+    ops = [dev(x) for x in (Lh, W1, W2, Rh)]
+    th = dev(theta)
+    m, err, ok = B.osmps_heff_expm(ctx, *ops, th, 3.0, max_iter=3, tol=1e-14, precision="fp64")
+    assert not ok and m == 3 and err > 1e-14
+    # the capped result is still the 3-vector Krylov approximation of the oracle
+    mv = lambda x: T.heff2_apply(Lh, W1, W2, Rh, x)
+    ref, m_ref, _ = T.krylov_expm(mv, theta, 3.0, max_iter=3, tol=1e-14)
+    assert m_ref == 3
+    assert np.linalg.norm(th.cpu().numpy() - ref) <= 1e-11 * np.linalg.norm(ref)
+    for kw in (dict(max_iter=0), dict(max_iter=129)):
+        with pytest.raises(B.OsmpsError):
+            B.osmps_heff_expm(ctx, *ops, dev(theta), 0.1, precision="fp64", **kw)
+    with pytest.raises(B.OsmpsError):
+        B.osmps_heff_expm(ctx, *ops, dev(theta), float("nan"), precision="fp64")
+    with pytest.raises(B.OsmpsError):
+        B.osmps_heff_expm(ctx, *ops, dev(np.zeros_like(theta)), 0.1, precision="fp64")
