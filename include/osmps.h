@@ -571,6 +571,80 @@ osmps_status osmps_coupling_grad(osmps_ctx* ctx, int64_t n_par, const int64_t* r
                                  const int64_t* col, const double* val, int64_t nnz,
                                  const double* gW, int64_t n_w, double* g_par, void* stream);
 
+/* ---- Real-time evolution: two-site TDVP (Sec. 5.4) ------------------------
+ * Complex tensors are interleaved (re, im) float64 pairs (C99 double complex
+ * / complex128 layout). */
+
+/* Split of a complex two-site tensor with truncation, the eigendecomposition
+ * route of osmps_split (Sec. 2, Eq. AAD_ULLUD) for M = theta as the complex
+ * (chi_l d1) x (d2 chi_r) matrix:
+ *   move_right = 1: G = M M^dagger; A1 = kept eigenvectors (left-canonical),
+ *                   A2 = U^dagger M renormalised to unit norm;
+ *   move_right = 0: G = M^dagger M; A2 = V^dagger (right-canonical),
+ *                   A1 = M V renormalised.
+ * The Hermitian eigenproblem is solved by cuSOLVER zheevd in float64; the
+ * Gram matrix and the projection run on float64 GEMMs (DMMA for
+ * OSMPS_PREC_FP64, the emulated float64 GEMM otherwise). The kept number and
+ * the discarded weight follow osmps_split's rule. theta (device, complex,
+ * chi_l x d1 x d2 x chi_r); A1, A2 (device, complex) with room for
+ * chi_l d1 min(chi_max, rank) and min(chi_max, rank) d2 chi_r elements;
+ * chi_new_out, discarded_out, entropy_out, lam2_out (min(chi_l d1, d2 chi_r)
+ * values, may be NULL): host. Synchronises `stream`.                       */
+osmps_status osmps_split_complex(osmps_ctx* ctx, const double* theta, double* A1, double* A2,
+                                 int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r,
+                                 int move_right, int64_t chi_max, double eps_local,
+                                 int64_t* chi_new_out, double* discarded_out,
+                                 double* entropy_out, double* lam2_out, int precision,
+                                 void* stream);
+
+typedef struct {
+  double dt;            /* time step: each step applies exp(-i H dt) (Eq. propSE)         */
+  int n_steps;          /* number of steps                                                 */
+  int64_t chi_max;      /* maximal bond dimension                                          */
+  double eps_local;     /* truncation tolerance of each split (0: chi_max only)            */
+  double krylov_tol;    /* error estimate at which a local propagator stops                */
+  int krylov_max_iter;  /* Krylov vectors per local propagator, 1..128                     */
+  int precision;        /* osmps_precision of the contractions                             */
+} osmps_tdvp_params;
+
+typedef struct {
+  double* energy;          /* in: NULL or host array of n_steps; out: <H> after each step   */
+  double* norm;            /* in: NULL or host array of n_steps; out: <psi|psi> after each  */
+  int64_t max_chi;         /* largest bond dimension reached                                */
+  int max_krylov;          /* most Krylov vectors one local propagator used                 */
+  int64_t krylov_calls;    /* local propagators applied (two-site and one-site)             */
+  int64_t krylov_vectors;  /* Krylov vectors over all of them (= H_eff products)            */
+  int64_t nonconverged;    /* propagators that stopped at krylov_max_iter above tolerance   */
+  double max_discarded;    /* largest discarded weight of a split                           */
+  double seconds;          /* wall time of the call                                         */
+} osmps_tdvp_stats;
+
+/* Real-time evolution of a complex MPS by n_steps of the symmetric
+ * second-order two-site TDVP (Sec. 5.4; Haegeman et al.'s two-site scheme,
+ * which lets the bond dimension grow): each step is a left-to-right half
+ * sweep with dt/2 then a right-to-left one with dt/2. At the pair (k, k+1)
+ * theta = A_k A_{k+1} is propagated by exp(-i H_eff dt/2) with the Krylov
+ * method of osmps_heff_expm (Sec. 5.2, Eq. krylov:approx), split and
+ * truncated as in osmps_split_complex (chi <= chi_max and the exact bound
+ * min(prod d left, prod d right)), the environment on the side the centre
+ * leaves is grown, and the new centre tensor is propagated backwards by
+ * exp(+i H1_eff dt/2) with the one-site H_eff (not at the chain ends).
+ * Input: chi_in (L + 1 bond dimensions, chi_in[0] = chi_in[L] = 1, each at
+ * most chi_max), host_in[k] (HOST, complex, chi_in[k] x d_k x chi_in[k+1]).
+ * The input must have sites 1..L-1 right-canonical (sum_{s,b} A[a,s,b]
+ * conj(A[a2,s,b]) = delta(a, a2)), the centre at site 0 (any norm: it is
+ * normalised); a product state qualifies. The same gauge holds on return.
+ * Output: chi_out (L + 1), host_out[k] (HOST, room for
+ * chi_max d_k chi_max complex elements, or for the exact bound), stats (may
+ * be NULL). The MPO must be Hermitian (real W as for osmps_sweep). All
+ * tensors stay on the device during the call; the context's workspace holds
+ * the Krylov basis (4 chi_l d^2 chi_r krylov_max_iter doubles at the largest
+ * bond). Synchronises `stream`.                                             */
+osmps_status osmps_tdvp_evolve(osmps_ctx* ctx, const osmps_mpo* mpo, const int64_t* chi_in,
+                               const double* const* host_in, const osmps_tdvp_params* p,
+                               int64_t* chi_out, double* const* host_out,
+                               osmps_tdvp_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,18 @@ class StepStats(_c.Structure):
                 ("converged", _c.c_int)]
 
 
+class TdvpParams(_c.Structure):
+    _fields_ = [("dt", _c.c_double), ("n_steps", _c.c_int), ("chi_max", _i64),
+                ("eps_local", _c.c_double), ("krylov_tol", _c.c_double),
+                ("krylov_max_iter", _c.c_int), ("precision", _c.c_int)]
+
+
+class TdvpStats(_c.Structure):
+    _fields_ = [("energy", _dp), ("norm", _dp), ("max_chi", _i64), ("max_krylov", _c.c_int),
+                ("krylov_calls", _i64), ("krylov_vectors", _i64), ("nonconverged", _i64),
+                ("max_discarded", _c.c_double), ("seconds", _c.c_double)]
+
+
 class U1Desc(_c.Structure):
     _fields_ = [("n_left", _i64), ("q_left", _c.POINTER(_i64)), ("chi_left", _c.POINTER(_i64)),
                 ("n_right", _i64), ("q_right", _c.POINTER(_i64)), ("chi_right", _c.POINTER(_i64)),
@@ -85,6 +97,11 @@ _SIGS = {
     "osmps_heff_expm": (_c.c_int, [_vp] * 6 + [_i64] * 7 +
                         [_c.c_double, _c.c_int, _c.c_double, _c.c_int, _c.POINTER(_c.c_int), _dp,
                          _vp]),
+    "osmps_split_complex": (_c.c_int, [_vp, _vp, _vp, _vp] + [_i64] * 4 +
+                            [_c.c_int, _i64, _c.c_double, _c.POINTER(_i64), _dp, _dp, _dp,
+                             _c.c_int, _vp]),
+    "osmps_tdvp_evolve": (_c.c_int, [_vp, _vp, _c.POINTER(_i64), _c.POINTER(_dp), _vp,
+                                     _c.POINTER(_i64), _c.POINTER(_dp), _vp, _vp]),
     "osmps_overlap_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_vp]),
     "osmps_projected_state": (_c.c_int, [_vp] * 6 + [_i64] * 7 + [_vp]),
     "osmps_theta_form": (_c.c_int, [_vp, _vp, _vp, _vp] + [_i64] * 5 + [_vp]),
@@ -307,6 +324,59 @@ def osmps_heff_expm(ctx, L, W1, W2, R, theta, tau, max_iter=40, tol=1e-12, preci
                                _c.byref(it), _c.byref(err), _stream(stream))
     _check(st, allow=(ENOCONV,) if allow_noconv else ())
     return it.value, err.value, st == 0
+
+
+def osmps_split_complex(ctx, theta, A1, A2, move_right, chi_max, eps_local, precision="fp64",
+                        stream=None):
+    """Complex split (complex128 CUDA tensors). Returns (chi_new, discarded,
+    entropy, lam2 numpy array); A1/A2 are flat buffers as for osmps_split."""
+    chi_l, d1, d2, chi_r = theta.shape
+    n = min(chi_l * d1, d2 * chi_r)
+    lam2 = np.zeros(n)
+    chn = _i64()
+    disc = _c.c_double()
+    ent = _c.c_double()
+    _check(lib().osmps_split_complex(ctx.ptr, _devc(theta, "theta"), _devc(A1, "A1"),
+                                     _devc(A2, "A2"), chi_l, d1, d2, chi_r, int(move_right),
+                                     int(chi_max), float(eps_local), _c.byref(chn),
+                                     _c.byref(disc), _c.byref(ent),
+                                     lam2.ctypes.data_as(_dp), _prec(precision), _stream(stream)))
+    return chn.value, disc.value, ent.value, lam2
+
+
+def osmps_tdvp_evolve(ctx, mpo, tensors, dt, n_steps, chi_max, eps_local=0.0, krylov_tol=1e-12,
+                      krylov_max_iter=40, precision="fp64", stream=None):
+    """Two-site TDVP real-time evolution of a complex MPS given as host arrays
+    tensors[k] (chi_k, d_k, chi_{k+1}) with sites 1..L-1 right-canonical.
+    Returns (evolved tensors as complex128 numpy arrays, energies, norms, stats)."""
+    L = len(tensors)
+    ts = [np.ascontiguousarray(t, dtype=np.complex128) for t in tensors]
+    chi_in = (_i64 * (L + 1))(*([t.shape[0] for t in ts] + [ts[-1].shape[2]]))
+    ins = (_dp * L)(*[t.ctypes.data_as(_dp) for t in ts])
+    d = [t.shape[1] for t in ts]
+    left = [1]
+    for k in range(L):
+        left.append(min(left[-1] * d[k], 1 << 30))
+    right = [1] * (L + 1)
+    for k in range(L - 1, -1, -1):
+        right[k] = min(right[k + 1] * d[k], 1 << 30)
+    cap = [min(chi_max, left[k], right[k]) for k in range(L + 1)]
+    outs = [np.zeros(cap[k] * d[k] * cap[k + 1], dtype=np.complex128) for k in range(L)]
+    outp = (_dp * L)(*[o.ctypes.data_as(_dp) for o in outs])
+    chi_out = (_i64 * (L + 1))()
+    energy = np.zeros(max(n_steps, 1))
+    norm = np.zeros(max(n_steps, 1))
+    st = TdvpStats()
+    st.energy = energy.ctypes.data_as(_dp)
+    st.norm = norm.ctypes.data_as(_dp)
+    prm = TdvpParams(float(dt), int(n_steps), int(chi_max), float(eps_local), float(krylov_tol),
+                     int(krylov_max_iter), _prec(precision))
+    _check(lib().osmps_tdvp_evolve(ctx.ptr, mpo.ptr, chi_in, ins, _c.byref(prm), chi_out, outp,
+                                   _c.byref(st), _stream(stream)))
+    res = [outs[k][: chi_out[k] * d[k] * chi_out[k + 1]].reshape(chi_out[k], d[k], chi_out[k + 1])
+           for k in range(L)]
+    stats = {f: getattr(st, f) for f, _ in TdvpStats._fields_ if f not in ("energy", "norm")}
+    return res, energy[:n_steps], norm[:n_steps], stats
 
 
 def osmps_theta_form(ctx, A1, A2, theta, stream=None):

@@ -390,6 +390,29 @@ osmps_status sytrd_tc(osmps_ctx* ctx, double* A, int64_t n, double* d, double* e
 // eigenvalues ascending in ev, eigenvectors as the rows of Y (nev x n).
 osmps_status eig_top(osmps_ctx* ctx, double* G, int64_t n, int64_t nev, double* ev, double* Y,
                      cudaStream_t s);
+// Krylov propagator (lanczos.cu) on the real 2x2 embedding of complex
+// tensors: X[r, w, c] (interleaved complex) -> X~[(p, r), w, (q, c)], with
+// conj applied first when set.
+osmps_status embed_complex(const double* z, double* out, int64_t r, int64_t w, int64_t c,
+                           bool conj, cudaStream_t s);
+// exp(-i tau H) theta~ for the embedded start vector theta_emb (length
+// 4 n_c, n_c = chi_l D chi_r complex elements) and the embedded operator
+// matvec; the result goes to theta_out as interleaved complex, or embedded
+// (may alias theta_emb) with out_embedded.
+osmps_status expm_core(osmps_ctx* ctx, int64_t n_c, const double* theta_emb, double* theta_out,
+                       int64_t chi_l, int64_t D, int64_t chi_r, double tau, int max_iter,
+                       double tol, const Matvec& matvec, int* iters, double* err, cudaStream_t s,
+                       bool out_embedded);
+// Truncation of a Gram spectrum (split.cu): ev (any order, nev values) with
+// tr = ||theta||^2; keeps min(chi_max, rank, the local-tolerance count).
+struct Trunc {
+  int64_t keep = 0;
+  double discarded = 0.0, entropy = 0.0;
+  std::vector<int> order;   // indices of the kept values, descending
+  std::vector<double> lam2;  // all values / tr, descending
+};
+osmps_status truncate_spectrum(const double* ev, int64_t nev, double tr, int64_t rank,
+                               int64_t chi_max, double eps_local, Trunc* t);
 osmps_status split_impl(osmps_ctx* ctx, const double* theta, double* A1, double* A2,
                         int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r, int move_right,
                         int64_t chi_max, double eps_local, int64_t* chi_new, double* discarded,

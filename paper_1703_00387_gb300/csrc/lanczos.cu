@@ -1070,12 +1070,12 @@ __global__ void __launch_bounds__(EXPM_THREADS) k_expm_tridiag(double* __restric
 // out = ||theta~|| sum_i u_i v_i, read back from the embedding: with B the
 // (p, q) blocks of the real basis vector v_i at one complex element,
 // sum_i Re(u_i) B + Im(u_i) J(B) averaged over its duplicate blocks. out is
-// interleaved complex [chi_l, D, chi_r]; the embedded vectors are
-// [(p, a), D, (q, c)]. Nothing is written when the iteration stopped on a
-// non-finite value.
+// interleaved complex [chi_l, D, chi_r], or with emb set the embedded
+// [(p, a), D, (q, c)] form of the vectors themselves. Nothing is written
+// when the iteration stopped on a non-finite value.
 __global__ void k_expm_combine(const double* __restrict__ V, int64_t ld,
                                const double* __restrict__ sc, double* __restrict__ out,
-                               int64_t chi_l, int64_t D, int64_t chi_r) {
+                               int64_t chi_l, int64_t D, int64_t chi_r, int emb) {
   __shared__ double ur[EXPM_MAXIT], ui[EXPM_MAXIT];
   const int* st = lz_state(sc);
   if (st[ST_STOP] == STOP_NONFINITE) return;
@@ -1098,8 +1098,15 @@ __global__ void k_expm_combine(const double* __restrict__ V, int64_t ld,
       xr = fma(ur[i], b00 + b11, fma(ui[i], b01 - b10, xr));
       xi = fma(ur[i], b10 - b01, fma(ui[i], b00 + b11, xi));
     }
-    out[2 * e] = scale * xr;
-    out[2 * e + 1] = scale * xi;
+    if (emb) {
+      out[o00] = scale * xr;
+      out[o00 + chi_r] = -scale * xi;
+      out[o10] = scale * xi;
+      out[o10 + chi_r] = scale * xr;
+    } else {
+      out[2 * e] = scale * xr;
+      out[2 * e + 1] = scale * xi;
+    }
   }
 }
 
@@ -1133,12 +1140,13 @@ osmps_status embed_complex(const double* z, double* out, int64_t r, int64_t w, i
   return OSMPS_OK;
 }
 
-// theta_out (interleaved complex, may alias nothing the basis uses) =
-// exp(-i tau H) theta~ read back from the embedding; theta_emb is the
-// embedded start vector of length n4 = 4 n_c, matvec the embedded operator.
+// theta_out = exp(-i tau H) theta~, interleaved complex, or embedded (and
+// then free to alias theta_emb) with out_embedded; theta_emb is the embedded
+// start vector of length 4 n_c, matvec the embedded operator.
 osmps_status expm_core(osmps_ctx* ctx, int64_t n_c, const double* theta_emb, double* theta_out,
                        int64_t chi_l, int64_t D, int64_t chi_r, double tau, int max_iter,
-                       double tol, const Matvec& matvec, int* iters, double* err, cudaStream_t s) {
+                       double tol, const Matvec& matvec, int* iters, double* err, cudaStream_t s,
+                       bool out_embedded) {
   osmps_status st = OSMPS_OK;
   const int64_t n = 4 * n_c;
   const int64_t ld = n;  // a multiple of 4: 16-byte aligned rows
@@ -1177,7 +1185,7 @@ osmps_status expm_core(osmps_ctx* ctx, int64_t n_c, const double* theta_emb, dou
     OSMPS_CUDA(cudaStreamSynchronize(s));
     if (lz_state_in_misc(ctx->host_pinned)[ST_STOP] != STOP_NONE) break;
   }
-  { k_expm_combine<<<ew_blocks(n_c), 256, 0, s>>>(V, ld, sc, theta_out, chi_l, D, chi_r); note_launch(); }
+  { k_expm_combine<<<ew_blocks(n_c), 256, 0, s>>>(V, ld, sc, theta_out, chi_l, D, chi_r, out_embedded ? 1 : 0); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   OSMPS_CUDA(cudaStreamSynchronize(s));
   const int* hs = lz_state_in_misc(ctx->host_pinned);
@@ -1244,5 +1252,5 @@ extern "C" osmps_status osmps_heff_expm(osmps_ctx* ctx, const double* L, const d
                            2 * chi_r, wl, wm, wr, precision, q, true);
   };
   return expm_core(ctx, n_c, th, theta_inout, chi_l, d1 * d2, chi_r, tau, max_iter, tol, mv,
-                   iters_out, err_out, s);
+                   iters_out, err_out, s, false);
 }

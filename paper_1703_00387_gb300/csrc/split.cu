@@ -49,6 +49,15 @@ __global__ void k_transpose_keep(const double* __restrict__ Yk, int64_t n, int64
   }
 }
 
+int blocks_for(int64_t n) {
+  int64_t b = cdiv(n, 256 * 4);
+  if (b < 1) b = 1;
+  if (b > 16384) b = 16384;
+  return (int)b;
+}
+
+}  // namespace
+
 // Truncation from the computed (largest) eigenvalues of the Gram matrix, in
 // any order: returns the indices of the kept values (descending) and fills
 // chi', the discarded weight and the entropy. The Gram route squares the
@@ -56,14 +65,7 @@ __global__ void k_transpose_keep(const double* __restrict__ Yk, int64_t n, int64
 // noise; the discarded weight is therefore taken as 1 - (kept sum) / tr with
 // tr = ||theta||^2 computed directly, the kept sum accumulated with
 // compensated summation, instead of as a sum over the noisy tail.
-struct Trunc {
-  int64_t keep = 0;
-  double discarded = 0.0, entropy = 0.0;
-  std::vector<int> order;
-  std::vector<double> lam2;
-};
-
-static osmps_status truncate_spectrum(const double* ev, int64_t n, double tr, int64_t rank,
+osmps_status truncate_spectrum(const double* ev, int64_t n, double tr, int64_t rank,
                                       int64_t chi_max, double eps_local, Trunc* t) {
   t->order.resize(n);
   for (int64_t i = 0; i < n; ++i) t->order[i] = (int)i;
@@ -92,15 +94,6 @@ static osmps_status truncate_spectrum(const double* ev, int64_t n, double tr, in
   t->entropy = S;
   return OSMPS_OK;
 }
-
-int blocks_for(int64_t n) {
-  int64_t b = cdiv(n, 256 * 4);
-  if (b < 1) b = 1;
-  if (b > 16384) b = 16384;
-  return (int)b;
-}
-
-}  // namespace
 
 // Truncate from the eigenpairs (Y: eigenvectors as rows, ev: eigenvalues on
 // the host, any order), then form the two site tensors:

@@ -145,3 +145,113 @@ def test_heff_expm_cap_and_validation(B, ctx):
         B.osmps_heff_expm(ctx, *ops, dev(theta), float("nan"), precision="fp64")
     with pytest.raises(B.OsmpsError):
         B.osmps_heff_expm(ctx, *ops, dev(np.zeros_like(theta)), 0.1, precision="fp64")
+
+
+# ---------------------------------------------------------------------------
+# Complex split and the whole TDVP evolution
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("move_right", [1, 0])
+@pytest.mark.parametrize("chi_max", [5, 64])
+def test_split_complex_matches_oracle(B, ctx, prec, move_right, chi_max):
+    # precision only selects the float64 GEMM (DMMA or emulated): both exact
+    rng = np.random.default_rng(21 + move_right)
+    chl, d1, d2, chr_ = 6, 2, 2, 7
+    theta = rng.standard_normal((chl, d1, d2, chr_)) + 1j * rng.standard_normal((chl, d1, d2, chr_))
+    m, n = chl * d1, d2 * chr_
+    kmax = min(chi_max, m, n)
+    A1 = torch.zeros(m * kmax, dtype=torch.complex128, device="cuda")
+    A2 = torch.zeros(kmax * n, dtype=torch.complex128, device="cuda")
+    keep, disc, ent, lam2 = B.osmps_split_complex(ctx, dev(theta), A1, A2, move_right, chi_max,
+                                                  0.0, precision=prec)
+    a1, a2, info = T.split_svd_c(theta, chi_max, 0.0, move_right=bool(move_right))
+    assert keep == info["keep"]
+    big = info["lam2"] > 1e-6
+    assert np.allclose(lam2[big], info["lam2"][big], rtol=1e-11, atol=0)
+    assert abs(disc - info["discarded"]) <= 1e-12
+    assert abs(ent - info["entropy"]) <= 1e-11
+    g1 = A1.cpu().numpy()[: m * keep].reshape(chl, d1, keep)
+    g2 = A2.cpu().numpy()[: keep * n].reshape(keep, d2, chr_)
+    # the product is gauge free (the kept singular vectors carry phases)
+    rec = np.tensordot(g1, g2, axes=([2], [0]))
+    ref = np.tensordot(a1, a2, axes=([2], [0]))
+    assert np.linalg.norm(rec - ref) <= 1e-11 * np.linalg.norm(ref)
+    if move_right:
+        M = g1.reshape(m, keep)
+        assert np.abs(M.conj().T @ M - np.eye(keep)).max() <= 1e-12
+    else:
+        M = g2.reshape(keep, n)
+        assert np.abs(M @ M.conj().T - np.eye(keep)).max() <= 1e-12
+
+
+def _rc_state(L, chi, seed):
+    return T.right_canonicalize_c(_random_complex_mps_(L, chi, seed))
+
+
+def _random_complex_mps_(L, chi, seed):
+    rng = np.random.default_rng(seed)
+    dims = [min(2 ** j, 2 ** (L - j), chi) for j in range(L + 1)]
+    return [rng.standard_normal((dims[j], 2, dims[j + 1]))
+            + 1j * rng.standard_normal((dims[j], 2, dims[j + 1])) for j in range(L)]
+
+
+@pytest.mark.parametrize("model", ["xxz", "ising"])
+def test_tdvp_full_bond_dimension_is_exact_evolution(B, ctx, model):
+    import scipy.linalg
+    L = 6
+    W = mpo.xxz_mpo(L, 1.0, 0.5, 0.2) if model == "xxz" else mpo.ising_mpo(L, 1.0, 1.2)
+    H = mpo.mpo_to_dense(W)
+    mps0 = _rc_state(L, 64, 1)
+    psi0 = T.mps_to_vector_c(mps0)
+    dt, n = 0.1, 4
+    h = B.MPO(ctx, W)
+    out, energy, norm, stats = B.osmps_tdvp_evolve(ctx, h, mps0, dt, n, chi_max=64,
+                                                   krylov_tol=1e-13, precision="fp64")
+    ref = scipy.linalg.expm(-1j * H * dt * n) @ psi0
+    assert np.linalg.norm(T.mps_to_vector_c(out) - ref) <= 1e-9
+    e0 = np.vdot(psi0, H @ psi0).real
+    assert np.all(np.abs(energy - e0) <= 1e-10 * max(1.0, abs(e0)))
+    assert np.all(np.abs(norm - 1.0) <= 1e-12)
+    assert stats["nonconverged"] == 0 and stats["krylov_calls"] == n * (2 * (L - 1) + 2 * (L - 2))
+
+
+@pytest.mark.parametrize("prec,bar", [("fp64", 1e-9), ("fp64emu", 1e-9), ("bf16x3", 1e-4)])
+def test_tdvp_truncated_matches_oracle(B, ctx, prec, bar):
+    # L = 10 XXZ with a field (no Schmidt multiplets at the cut), complex random
+    # start with bond dimension 2, chi_max = 6: both sides truncate the same way
+    L = 10
+    W = mpo.xxz_mpo(L, 1.0, 0.7, 0.35)
+    mps0 = _rc_state(L, 2, 5)
+    dt, n, chi = 0.05, 6, 6
+    ref_mps, ref_hist = T.tdvp2_evolve(W, mps0, dt, n, chi_max=chi, krylov_tol=1e-13)
+    h = B.MPO(ctx, W)
+    out, energy, norm, stats = B.osmps_tdvp_evolve(ctx, h, mps0, dt, n, chi_max=chi,
+                                                   krylov_tol=1e-13, precision=prec)
+    assert [A.shape for A in out] == [A.shape for A in ref_mps]
+    psi, ref = T.mps_to_vector_c(out), T.mps_to_vector_c(ref_mps)
+    assert np.linalg.norm(psi - ref) <= bar
+    assert np.allclose(energy, [e for _, e, _ in ref_hist], rtol=0, atol=bar * 10)
+    assert stats["max_chi"] == chi
+
+
+def test_tdvp_ground_state_gains_only_a_phase(B, ctx):
+    # a GPU DMRG ground state evolved on the GPU: psi(t) = exp(-i E0 t) psi0
+    L = 10
+    W = mpo.ising_mpo(L, 1.0, 1.0)
+    rng = np.random.default_rng(0)
+    from oracle import dmrg as od
+    dims = od.initial_bond_dims(L, 2, 16)
+    start = [rng.standard_normal((dims[k], 2, dims[k + 1])) for k in range(L)]
+    E0, gs, _ = od.dmrg(W, start, chi_max=16, n_sweeps=4)
+    gs_c = T.right_canonicalize_c(gs)
+    psi0 = T.mps_to_vector_c(gs_c)
+    dt, n = 0.05, 4
+    h = B.MPO(ctx, W)
+    out, energy, norm, _ = B.osmps_tdvp_evolve(ctx, h, gs_c, dt, n, chi_max=16, eps_local=1e-14,
+                                               krylov_tol=1e-13, precision="fp64")
+    ov = np.vdot(psi0, T.mps_to_vector_c(out))
+    assert abs(abs(ov) - 1.0) <= 1e-8
+    assert abs(np.angle(ov * np.exp(1j * E0 * dt * n))) <= 1e-8
+    assert np.all(np.abs(energy - E0) <= 1e-9 * abs(E0))
