@@ -303,6 +303,7 @@ def run_ours(args, ws, rank, local):
         line["u1_heff"] = u1_leg(B, ctx, args)
         line["long_range_sweep"] = long_range_leg(B, ctx, args)
         line["excited_state"] = excited_leg(B, ctx, args)
+        line["tdvp"] = tdvp_leg(B, ctx, args)
         line["gradients"] = grad_leg(B, ctx, args)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"], line["matvec_rel_err"] = cpu_leg(B, ctx, Wh)
@@ -566,6 +567,38 @@ def excited_leg(B, ctx, args):
     return {"workload": "long-range TFI J=1 g=4 alpha=1.5 (3 exponentials, w=5), L=32, chi_max=64",
             "ground_energy": st["energy"], "excited_energy": r["energy"],
             "overlap": r["overlaps"][0], "ground_seconds": t_ground, "excited_seconds": t_exc}
+
+
+def tdvp_leg(B, ctx, args):
+    """Two-site TDVP real-time evolution (Sec. 5.4) of the XXZ chain (J=1,
+    Delta=1), L=64, at saturated bond dimension chi=128: a seeded random MPS
+    right-canonicalised on the GPU (osmps_mps_canonicalize), then one untimed
+    and two timed steps of dt=0.05 (Krylov tolerance 1e-10, at most 40
+    vectors), split-precision contractions, float64 Krylov and split."""
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+    L, chi, dt = 64, 128, 0.05
+    W = hamiltonians.xxz(L, 1.0, 1.0, 0.0)
+    mpo = B.MPO(ctx, W)
+    mps = B.MPS(ctx, inputs.random_mps(L, D, chi, seed=21), chi_cap=chi)
+    B.osmps_mps_canonicalize(ctx, mps, mpo, 0, precision="fp64")
+    start = [t.astype(np.complex128) for t in mps.tensors()]
+    mps.close()
+    warm, _, _, _ = B.osmps_tdvp_evolve(ctx, mpo, start, dt, 1, chi_max=chi, krylov_tol=1e-10,
+                                        krylov_max_iter=40, precision=args.precision)
+    out, energy, norm, st = B.osmps_tdvp_evolve(ctx, mpo, warm, dt, 2, chi_max=chi,
+                                                krylov_tol=1e-10, krylov_max_iter=40,
+                                                precision=args.precision)
+    mpo.close()
+    steps = 2
+    return {"workload": "XXZ J=1 Delta=1, L=64, d=2, w=5, chi=128 (saturated), dt=0.05, "
+                        "two-site TDVP second-order steps from a random right-canonical MPS",
+            "seconds_per_step": st["seconds"] / steps, "steps": steps,
+            "krylov_vectors_per_step": st["krylov_vectors"] / steps,
+            "krylov_calls_per_step": st["krylov_calls"] / steps, "max_krylov": st["max_krylov"],
+            "nonconverged": st["nonconverged"], "max_chi": st["max_chi"],
+            "max_discarded": st["max_discarded"],
+            "energy_drift": float(abs(energy[-1] - energy[0])), "norm_last": float(norm[-1]),
+            "precision": args.precision}
 
 
 def grad_leg(B, ctx, args):

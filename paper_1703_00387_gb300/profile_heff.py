@@ -8,12 +8,16 @@ device memory:
   `ncu --profile-from-start off`);
 * --u1: 3 products of the U(1) block-sparse H_eff.theta of the Bose-Hubbard
   workload (L=64, N=64, d=5, w=4, chi=512 per bond, sites 31 and 32), after
-  3 untimed ones, between the profiler's start and stop.
+  3 untimed ones, between the profiler's start and stop;
+* --tdvp: one two-site TDVP step (XXZ, L --tdvp-L, chi --chi, dt 0.05) from a
+  random MPS right-canonicalised on the GPU, after one untimed step, between
+  the profiler's start and stop.
 
     python -m paper_1703_00387_gb300.profile_heff --chi 1024 --prec bf16x3 --reps 3
     python -m paper_1703_00387_gb300.profile_heff --chi 1024 --step
     python -m paper_1703_00387_gb300.profile_heff --lanczos-solve --chi 32 --lanczos-mode host
     python -m paper_1703_00387_gb300.profile_heff --u1
+    python -m paper_1703_00387_gb300.profile_heff --tdvp --tdvp-L 32 --chi 64
 """
 import argparse
 import time
@@ -33,11 +37,15 @@ def main():
     ap.add_argument("--lanczos-solve", action="store_true")
     ap.add_argument("--lanczos-mode", default="auto", choices=["auto", "host", "graph"])
     ap.add_argument("--u1", action="store_true")
+    ap.add_argument("--tdvp", action="store_true")
+    ap.add_argument("--tdvp-L", type=int, default=32)
     args = ap.parse_args()
     if args.lanczos_solve:
         return lanczos_solve(args)
     if args.u1:
         return u1_products(args)
+    if args.tdvp:
+        return tdvp_step(args)
 
     import torch
     from paper_1703_00387_gb300 import binding as B
@@ -132,6 +140,31 @@ def u1_products(args):
     torch.cuda.profiler.stop()
     print("u1 products done, n_theta", pl.n_theta)
     op.close()
+    ctx.close()
+
+
+def tdvp_step(args):
+    import torch
+    from paper_1703_00387_gb300 import binding as B
+    from paper_1703_00387_gb300 import hamiltonians, inputs
+
+    ctx = B.Context(0)
+    L, chi = args.tdvp_L, args.chi
+    mpo = B.MPO(ctx, hamiltonians.xxz(L, 1.0, 1.0, 0.0))
+    mps = B.MPS(ctx, inputs.random_mps(L, 2, chi, seed=21), chi_cap=chi)
+    B.osmps_mps_canonicalize(ctx, mps, mpo, 0, precision="fp64")
+    start = [t.astype(np.complex128) for t in mps.tensors()]
+    mps.close()
+    warm, _, _, _ = B.osmps_tdvp_evolve(ctx, mpo, start, 0.05, 1, chi_max=chi, krylov_tol=1e-10,
+                                        precision=args.prec)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    _, e, _, st = B.osmps_tdvp_evolve(ctx, mpo, warm, 0.05, 1, chi_max=chi, krylov_tol=1e-10,
+                                      precision=args.prec)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print("tdvp step", st, e)
+    mpo.close()
     ctx.close()
 
 
