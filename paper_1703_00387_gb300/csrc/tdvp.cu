@@ -164,7 +164,8 @@ int grid_for(int64_t n) {
 // A1~ (2 chi_l, d1, 2 keep) and A2~ (2 keep, d2, 2 chi_r) are written
 // embedded. The Gram matrix and the projection are float64 GEMMs on the
 // embedded tensors (DMMA for OSMPS_PREC_FP64, the emulated float64 GEMM
-// otherwise); the eigenpairs come from cuSOLVER zheevd; chi' and the
+// otherwise); the eigenpairs come from cuSOLVER (zheevdx for the largest
+// min(chi_max, rank) only, zheevd when that is all of them); chi' and the
 // discarded weight follow truncate_spectrum with tr = ||theta||^2.
 osmps_status split_embedded(osmps_ctx* ctx, const double* th, double* A1, double* A2,
                             int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r, int move_right,
@@ -206,15 +207,31 @@ osmps_status split_embedded(osmps_ctx* ctx, const double* th, double* A1, double
   }
   { k_gram_to_complex<<<grid_for(nz * nz), 256, 0, s>>>(Gt, Z, nz, move_right ? m : chi_r); note_launch(); }
   OSMPS_LAUNCH_CHECK();
+  // Only the largest min(chi_max, rank) eigenpairs can be kept: compute just
+  // those when that is fewer than all (zheevdx, range by index).
+  const int64_t nev = std::min<int64_t>(nz, std::min<int64_t>(chi_max, std::min(m, n)));
   OSMPS_SOLVER(cusolverDnSetStream(ctx->solver, s));
-  int lwork = 0;
-  OSMPS_SOLVER(cusolverDnZheevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
-                                           CUBLAS_FILL_MODE_LOWER, (int)nz, Z, (int)nz, ev, &lwork));
-  cuDoubleComplex* work =
-      (cuDoubleComplex*)ws_get(ctx, SLOT_SPLIT_WORK, (size_t)std::max(lwork, 1) * 16, s, &st);
-  if (!work) return st;
-  OSMPS_SOLVER(cusolverDnZheevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                (int)nz, Z, (int)nz, ev, work, lwork, ctx->dev_info));
+  int lwork = 0, found = (int)nz;
+  if (nev == nz) {
+    OSMPS_SOLVER(cusolverDnZheevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                             CUBLAS_FILL_MODE_LOWER, (int)nz, Z, (int)nz, ev, &lwork));
+    cuDoubleComplex* work =
+        (cuDoubleComplex*)ws_get(ctx, SLOT_SPLIT_WORK, (size_t)std::max(lwork, 1) * 16, s, &st);
+    if (!work) return st;
+    OSMPS_SOLVER(cusolverDnZheevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                  (int)nz, Z, (int)nz, ev, work, lwork, ctx->dev_info));
+  } else {
+    const int il = (int)(nz - nev + 1), iu = (int)nz;
+    OSMPS_SOLVER(cusolverDnZheevdx_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                              CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, (int)nz,
+                                              Z, (int)nz, 0.0, 0.0, il, iu, &found, ev, &lwork));
+    cuDoubleComplex* work =
+        (cuDoubleComplex*)ws_get(ctx, SLOT_SPLIT_WORK, (size_t)std::max(lwork, 1) * 16, s, &st);
+    if (!work) return st;
+    OSMPS_SOLVER(cusolverDnZheevdx(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                   CUBLAS_FILL_MODE_LOWER, (int)nz, Z, (int)nz, 0.0, 0.0, il, iu,
+                                   &found, ev, work, lwork, ctx->dev_info));
+  }
   OSMPS_TRY(pinned_reserve(ctx, (size_t)nz + 16));
   double* h = ctx->host_pinned;
   int info = 0;
@@ -222,13 +239,15 @@ osmps_status split_embedded(osmps_ctx* ctx, const double* th, double* A1, double
   OSMPS_CUDA(cudaMemcpyAsync(&info, ctx->dev_info, sizeof(int), cudaMemcpyDeviceToHost, s));
   OSMPS_CUDA(cudaStreamSynchronize(s));
   if (info != 0) return set_error(OSMPS_ECUDA, "split: zheevd info %d", info);
+  if (found < 1 || found > nz) return set_error(OSMPS_ECUDA, "split: zheevdx found %d eigenpairs", found);
   const double trace = 0.5 * h[nz];
-  std::vector<double> ev_host(h, h + nz);
+  // the selected eigenvectors occupy the first `found` columns of Z
+  std::vector<double> ev_host(h, h + found);
   Trunc t;
-  OSMPS_TRY(truncate_spectrum(ev_host.data(), nz, trace, std::min(m, n), chi_max, eps_local, &t));
+  OSMPS_TRY(truncate_spectrum(ev_host.data(), found, trace, std::min(m, n), chi_max, eps_local, &t));
   const int64_t keep = t.keep;
   if (lam2_out)
-    for (int64_t i = 0; i < std::min(m, n); ++i) lam2_out[i] = i < nz ? t.lam2[i] : 0.0;
+    for (int64_t i = 0; i < std::min(m, n); ++i) lam2_out[i] = i < found ? t.lam2[i] : 0.0;
   *chi_new = keep;
   *discarded = t.discarded;
   *entropy = t.entropy;
