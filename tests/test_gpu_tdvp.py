@@ -256,3 +256,79 @@ def test_tdvp_ground_state_gains_only_a_phase(B, ctx):
     assert abs(abs(ov) - 1.0) <= 1e-8
     assert abs(np.angle(ov * np.exp(1j * E0 * dt * n))) <= 1e-8
     assert np.all(np.abs(energy - E0) <= 1e-9 * abs(E0))
+
+
+# ---------------------------------------------------------------------------
+# Edge cases of the evolution
+# ---------------------------------------------------------------------------
+
+
+def _random_rc(L, d, chi, seed):
+    rng = np.random.default_rng(seed)
+    dims = [min(d ** j, d ** (L - j), chi) for j in range(L + 1)]
+    return T.right_canonicalize_c([rng.standard_normal((dims[j], d, dims[j + 1]))
+                                   + 1j * rng.standard_normal((dims[j], d, dims[j + 1]))
+                                   for j in range(L)])
+
+
+@pytest.mark.parametrize("L,model", [(2, "xxz"), (4, "aklt")])
+def test_tdvp_short_chains_and_spin_one_are_exact(B, ctx, L, model):
+    # L = 2: one pair, no one-site steps; spin-1 AKLT (d = 3, w = 14) at L = 4
+    import scipy.linalg
+    W = mpo.xxz_mpo(L, 1.0, 0.6, 0.4) if model == "xxz" else mpo.aklt_mpo(L)
+    d = W[0].shape[1]
+    H = mpo.mpo_to_dense(W)
+    mps0 = _random_rc(L, d, 64, seed=8)
+    psi0 = T.mps_to_vector_c(mps0)
+    dt, n = 0.07, 3
+    out, energy, norm, stats = B.osmps_tdvp_evolve(ctx, B.MPO(ctx, W), mps0, dt, n, chi_max=64,
+                                                   krylov_tol=1e-13, precision="fp64")
+    ref = scipy.linalg.expm(-1j * H * dt * n) @ psi0
+    assert np.linalg.norm(T.mps_to_vector_c(out) - ref) <= 1e-9
+    assert stats["krylov_calls"] == n * (2 * (L - 1) + 2 * max(L - 2, 0))
+
+
+def test_tdvp_product_manifold_chi1_matches_oracle(B, ctx):
+    # chi_max = 1: both sides keep the leading Schmidt vector at every split
+    L = 6
+    W = mpo.xxz_mpo(L, 1.0, 0.5, 0.8)
+    rng = np.random.default_rng(4)
+    mps0 = T.right_canonicalize_c([rng.standard_normal((1, 2, 1)) + 1j * rng.standard_normal((1, 2, 1))
+                                   for _ in range(L)])
+    ref_mps, _ = T.tdvp2_evolve(W, mps0, 0.05, 3, chi_max=1, krylov_tol=1e-13)
+    out, _, norm, stats = B.osmps_tdvp_evolve(ctx, B.MPO(ctx, W), mps0, 0.05, 3, chi_max=1,
+                                              krylov_tol=1e-13, precision="fp64")
+    assert stats["max_chi"] == 1
+    assert np.linalg.norm(T.mps_to_vector_c(out) - T.mps_to_vector_c(ref_mps)) <= 1e-9
+    assert np.all(np.abs(norm - 1.0) <= 1e-12)
+
+
+def test_tdvp_krylov_cap_matches_oracle(B, ctx):
+    # a cap of 3 Krylov vectors stops most propagators early; the capped
+    # approximation is still the same on both sides
+    L = 8
+    W = mpo.ising_mpo(L, 1.0, 1.3)
+    mps0 = _random_rc(L, 2, 8, seed=12)
+    ref_mps, _ = T.tdvp2_evolve(W, mps0, 0.2, 2, chi_max=8, krylov_tol=1e-14, krylov_max_iter=3)
+    out, _, _, stats = B.osmps_tdvp_evolve(ctx, B.MPO(ctx, W), mps0, 0.2, 2, chi_max=8,
+                                           krylov_tol=1e-14, krylov_max_iter=3, precision="fp64")
+    assert stats["nonconverged"] > 0 and stats["max_krylov"] == 3
+    assert np.linalg.norm(T.mps_to_vector_c(out) - T.mps_to_vector_c(ref_mps)) <= 1e-9
+
+
+def test_tdvp_zero_steps_and_validation(B, ctx):
+    L = 5
+    W = mpo.ising_mpo(L, 1.0, 1.0)
+    h = B.MPO(ctx, W)
+    mps0 = _random_rc(L, 2, 4, seed=2)
+    scaled = [A.copy() for A in mps0]
+    scaled[0] = 3.0 * scaled[0]  # the centre is normalised on entry
+    out, e, nrm, stats = B.osmps_tdvp_evolve(ctx, h, scaled, 0.1, 0, chi_max=4, precision="fp64")
+    assert len(e) == 0 and stats["krylov_calls"] == 0
+    assert np.linalg.norm(T.mps_to_vector_c(out) - T.mps_to_vector_c(mps0)) <= 1e-13
+    with pytest.raises(B.OsmpsError):  # a bond above chi_max
+        B.osmps_tdvp_evolve(ctx, h, mps0, 0.1, 1, chi_max=2, precision="fp64")
+    with pytest.raises(B.OsmpsError):
+        B.osmps_tdvp_evolve(ctx, h, mps0, float("nan"), 1, chi_max=4, precision="fp64")
+    with pytest.raises(B.OsmpsError):
+        B.osmps_tdvp_evolve(ctx, h, mps0, 0.1, 1, chi_max=4, krylov_max_iter=200, precision="fp64")
