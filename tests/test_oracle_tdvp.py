@@ -153,3 +153,32 @@ def test_tdvp_truncated_converges_with_bond_dimension():
         errs.append(np.linalg.norm(T.mps_to_vector_c(mps) - ref))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] <= 1e-10
+
+
+@pytest.mark.parametrize("mistake", ["backward_sign", "no_backward", "full_dt", "no_conj"])
+def test_exactness_pin_catches_planted_mistakes(monkeypatch, mistake):
+    # each plausible slip in the step, planted in the oracle, breaks the
+    # full-bond-dimension exactness pin by far more than its 1e-10 bar
+    L = 6
+    W = mpo.xxz_mpo(L, 1.0, 0.5, 0.2)
+    H = mpo.mpo_to_dense(W)
+    mps0 = _random_complex_mps(L, 2, 64, seed=1)
+    psi0 = T.mps_to_vector_c(T.right_canonicalize_c(mps0))
+    real_expm = T.krylov_expm
+    if mistake == "backward_sign":
+        monkeypatch.setattr(T, "krylov_expm", lambda mv, v, tau, *a: real_expm(mv, v, abs(tau), *a))
+    elif mistake == "no_backward":
+        monkeypatch.setattr(T, "krylov_expm",
+                            lambda mv, v, tau, *a: (v, 1, 0.0) if tau < 0 else real_expm(mv, v, tau, *a))
+    elif mistake == "full_dt":
+        monkeypatch.setattr(T, "krylov_expm",
+                            lambda mv, v, tau, *a: real_expm(mv, v, 2 * tau if tau > 0 else tau, *a))
+    else:
+        def env_left_noconj(Lenv, A, Wk):
+            X = np.tensordot(Lenv, A, axes=([2], [0]))
+            Y = np.tensordot(X, Wk, axes=([1, 2], [0, 2]))
+            return np.ascontiguousarray(np.tensordot(A, Y, axes=([0, 1], [0, 2])).transpose(0, 2, 1))
+        monkeypatch.setattr(T, "env_left_c", env_left_noconj)
+    mps, _ = T.tdvp2_evolve(W, mps0, 0.1, 4, chi_max=64)
+    ref = scipy.linalg.expm(-1j * H * 0.4) @ psi0
+    assert np.linalg.norm(T.mps_to_vector_c(mps) - ref) > 1e-4
