@@ -237,8 +237,10 @@ osmps_status osmps_lanczos_ground(osmps_ctx* ctx, const double* L, const double*
  * pointers to the vector count and the last estimate. Returns ENOCONV at
  * max_iter above tol (the result is still written), ENAN on non-finite
  * Krylov data (theta_inout unchanged). Uses the same workspace as
- * osmps_lanczos_ground, plus three slots for the real embedding of L, R and
- * theta (16 chi^2 w and 32 chi_l d1 d2 chi_r bytes). Synchronises `stream`. */
+ * osmps_lanczos_ground (the Krylov basis holds 4 chi_l d1 d2 chi_r doubles
+ * per vector), plus three slots for the real embedding of L, R and theta
+ * (32 chi_l^2 wl, 32 chi_r^2 wr and 32 chi_l d1 d2 chi_r bytes).
+ * Synchronises `stream`.                                                    */
 osmps_status osmps_heff_expm(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
                              const double* R, double* theta_inout, int64_t chi_l, int64_t d1,
                              int64_t d2, int64_t chi_r, int64_t wl, int64_t wm, int64_t wr,
