@@ -5,9 +5,11 @@
  * the effective Hamiltonian of Sec. 3.4 (Fig. LanczosMPS), its lowest
  * eigenpair by Lanczos, the eigendecomposition split of Sec. 2
  * (Eq. AAD_ULLUD, Eq. ThetaAL) with the truncation rule of Eq. elocal, and the
- * sweeps of Sec. 3.4.
+ * sweeps of Sec. 3.4; and real-time evolution by the two-site TDVP of
+ * Sec. 5.4 with the Krylov propagator of Sec. 5.2.
  *
- * Conventions (all tensors real float64, row-major, contiguous):
+ * Conventions (tensors real float64 unless a call says complex, which means
+ * interleaved (re, im) float64 pairs; row-major, contiguous):
  *   MPS site tensor      A[a, s, b]        (chi_l, d, chi_r)            Eq. mps
  *   MPO site tensor      W[w, t, s, w2]    (w_left, d, d, w_right)      Eq. mpo / Eq. MPOdef
  *                        t = outgoing (bra) physical index, s = incoming (ket);
