@@ -182,3 +182,31 @@ def test_exactness_pin_catches_planted_mistakes(monkeypatch, mistake):
     mps, _ = T.tdvp2_evolve(W, mps0, 0.1, 4, chi_max=64)
     ref = scipy.linalg.expm(-1j * H * 0.4) @ psi0
     assert np.linalg.norm(T.mps_to_vector_c(mps) - ref) > 1e-4
+
+
+@pytest.mark.parametrize("move_right", [True, False])
+def test_complex_split_is_the_best_rank_k_approximation(move_right):
+    # Eckart-Young: the truncated split reproduces theta up to exactly the
+    # discarded singular values; the isometric factor is orthonormal and the
+    # other one carries the renormalised Schmidt values
+    rng = np.random.default_rng(7)
+    chl, d1, d2, chr_ = 5, 2, 3, 4
+    theta = rng.standard_normal((chl, d1, d2, chr_)) + 1j * rng.standard_normal((chl, d1, d2, chr_))
+    M = theta.reshape(chl * d1, d2 * chr_)
+    S = np.linalg.svd(M, compute_uv=False)
+    k = 4
+    A1, A2, info = T.split_svd_c(theta, k, 0.0, move_right=move_right)
+    assert info["keep"] == k
+    kept = np.sqrt(np.sum(S[:k] ** 2))
+    approx = np.tensordot(A1, A2, axes=([2], [0])).reshape(M.shape) * kept
+    assert abs(np.linalg.norm(M - approx) ** 2 - np.sum(S[k:] ** 2)) <= 1e-12 * np.sum(S ** 2)
+    assert abs(info["discarded"] - np.sum(S[k:] ** 2) / np.sum(S ** 2)) <= 1e-14
+    if move_right:
+        U = A1.reshape(chl * d1, k)
+        assert np.abs(U.conj().T @ U - np.eye(k)).max() <= 1e-13
+        sv = np.linalg.svd(A2.reshape(k, d2 * chr_), compute_uv=False)
+    else:
+        V = A2.reshape(k, d2 * chr_)
+        assert np.abs(V @ V.conj().T - np.eye(k)).max() <= 1e-13
+        sv = np.linalg.svd(A1.reshape(chl * d1, k), compute_uv=False)
+    assert np.allclose(sv, S[:k] / kept, rtol=1e-12, atol=0)
