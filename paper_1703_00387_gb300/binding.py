@@ -350,7 +350,15 @@ def osmps_tdvp_evolve(ctx, mpo, tensors, dt, n_steps, chi_max, eps_local=0.0, kr
     tensors[k] (chi_k, d_k, chi_{k+1}) with sites 1..L-1 right-canonical.
     Returns (evolved tensors as complex128 numpy arrays, energies, norms, stats)."""
     L = len(tensors)
+    if L != mpo.L:
+        raise ValueError(f"osmps_tdvp_evolve: {L} site tensors for an MPO of {mpo.L} sites")
     ts = [np.ascontiguousarray(t, dtype=np.complex128) for t in tensors]
+    for k, t in enumerate(ts):
+        if t.ndim != 3 or t.shape[1] != mpo.shapes[k][1]:
+            raise ValueError(f"osmps_tdvp_evolve: site {k} has shape {t.shape}, physical "
+                             f"dimension {mpo.shapes[k][1]} expected")
+        if k + 1 < L and t.shape[2] != ts[k + 1].shape[0]:
+            raise ValueError(f"osmps_tdvp_evolve: bond {k + 1} differs between sites {k} and {k + 1}")
     chi_in = (_i64 * (L + 1))(*([t.shape[0] for t in ts] + [ts[-1].shape[2]]))
     ins = (_dp * L)(*[t.ctypes.data_as(_dp) for t in ts])
     d = [t.shape[1] for t in ts]

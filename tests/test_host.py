@@ -103,3 +103,23 @@ def test_xxz_coupling_basis_rebuilds_oracle_mpo():
     for j in range(2 * L - 1):
         k = j if j < L - 1 else j - (L - 1)
         assert set(site_of[row_ptr[j]:row_ptr[j + 1]]) == {k}
+
+
+def test_tdvp_binding_rejects_mismatched_states_on_the_host():
+    # shape checks run before any device work: a wrong site count would make
+    # the library read past the bond-dimension array
+    import numpy as np
+    from paper_1703_00387_gb300 import binding as B
+
+    class FakeMPO:
+        L = 3
+        shapes = [(1, 2, 2, 5), (5, 2, 2, 5), (5, 2, 2, 1)]
+        ptr = None
+
+    good = [np.zeros((1, 2, 2)), np.zeros((2, 2, 2)), np.zeros((2, 2, 1))]
+    with pytest.raises(ValueError):
+        B.osmps_tdvp_evolve(None, FakeMPO(), good[:2], 0.1, 1, chi_max=4)
+    with pytest.raises(ValueError):
+        B.osmps_tdvp_evolve(None, FakeMPO(), [good[0], np.zeros((2, 3, 2)), good[2]], 0.1, 1, chi_max=4)
+    with pytest.raises(ValueError):
+        B.osmps_tdvp_evolve(None, FakeMPO(), [good[0], np.zeros((2, 2, 3)), good[2]], 0.1, 1, chi_max=4)
