@@ -160,6 +160,10 @@ osmps_status osmps_heff_apply(osmps_ctx* ctx, const double* L, const double* W1,
  * message gives the bytes needed); use osmps_heff_apply for those.
  * The first call on each device looks up the array's device address with
  * that device current; make that first call before any stream capture.
+ * The address is kept per device ordinal for the life of the process: after
+ * cudaDeviceReset (or any release and re-creation of the device's primary
+ * context) it is stale, so do not call this entry point again in a process
+ * that has reset the device.
  * Every call shares the one array and it keeps the previous call's
  * contents (nothing in it is read before the call writes it), so calls
  * that can overlap on the GPU (other streams or threads) race: serialise

@@ -262,9 +262,24 @@ def osmps_heff_apply(ctx, L, W1, W2, R, theta, y, precision="bf16x3", stream=Non
 
 def osmps_heff_apply_noalloc(L, W1, W2, R, theta, y, stream=None):
     """Float64 H_eff.theta through the allocation-free entry point (no context;
-    fixed 32 MiB scratch inside the library, shared by all calls)."""
+    fixed 32 MiB scratch inside the library, shared by all calls).
+
+    The library runs on the device current on the calling thread and reads
+    every operand with the dimensions taken from theta, W1 and W2, so the
+    operands are checked here first: all on the current device, and L, R,
+    W1, W2 and y of the shapes those dimensions imply."""
+    import torch
     chi_l, d1, d2, chi_r = theta.shape
     wl, wm, wr = W1.shape[0], W1.shape[3], W2.shape[3]
+    cur = torch.cuda.current_device()
+    for name, t in (("L", L), ("W1", W1), ("W2", W2), ("R", R), ("theta", theta), ("y", y)):
+        if not t.is_cuda or t.device.index != cur:
+            raise ValueError(f"{name} is on {t.device}, not on the current device cuda:{cur}")
+    want = {"L": (chi_l, wl, chi_l), "R": (chi_r, wr, chi_r), "W1": (wl, d1, d1, wm),
+            "W2": (wm, d2, d2, wr), "y": (chi_l, d1, d2, chi_r)}
+    for name, t in (("L", L), ("R", R), ("W1", W1), ("W2", W2), ("y", y)):
+        if tuple(t.shape) != want[name]:
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {want[name]}")
     _check(lib().osmps_heff_apply_noalloc(_dev(L, "L"), _dev(W1, "W1"), _dev(W2, "W2"),
                                           _dev(R, "R"), _dev(theta, "theta"), _dev(y, "y"), chi_l,
                                           d1, d2, chi_r, wl, wm, wr, _stream(stream)))

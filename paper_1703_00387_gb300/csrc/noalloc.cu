@@ -5,6 +5,7 @@
 // a context workspace, so the call needs no osmps_ctx and never calls
 // cudaMalloc/cudaFree. The array costs NOALLOC_SCRATCH_BYTES of device memory
 // on every GPU where the library is used, held until the process exits.
+#include <initializer_list>
 #include <mutex>
 
 #include "common.cuh"
@@ -46,6 +47,20 @@ osmps_status scratch_address(void** out) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Bytes of a float64 array with the given extents, 256-byte aligned, or
+// false when the product overflows or alone exceeds the fixed scratch (each
+// factor is at most 2^31, so a product of five or six of them can wrap).
+bool region_bytes(std::initializer_list<int64_t> dims, size_t* out) {
+  uint64_t b = 8;
+  for (int64_t x : dims) {
+    uint64_t r = 0;
+    if (__builtin_mul_overflow(b, (uint64_t)x, &r) || r > NOALLOC_SCRATCH_BYTES) return false;
+    b = r;
+  }
+  *out = align256((size_t)b);
+  return true;
+}
+
 }  // namespace
 
 }  // namespace osmps
@@ -65,13 +80,19 @@ extern "C" osmps_status osmps_heff_apply_noalloc(const double* L, const double* 
   for (int64_t x : {chi_l, d1, d2, chi_r, wl, wm, wr})
     if (x <= 0 || x > ((int64_t)1 << 31))
       return set_error(OSMPS_ESHAPE, "osmps_heff_apply_noalloc: non-positive or oversized dimension");
+  size_t b_mat1 = 0, b_mat2 = 0, b_t1 = 0, b_t2 = 0, b_t3 = 0;
+  const bool fits = region_bytes({wl, d1, d1, wm}, &b_mat1) && region_bytes({wm, d2, d2, wr}, &b_mat2) &&
+                    region_bytes({chi_l, wl, d1, d2, chi_r}, &b_t1) &&
+                    region_bytes({chi_l, d1, wm, d2, chi_r}, &b_t2) &&
+                    region_bytes({chi_l, d1, d2, wr, chi_r}, &b_t3);
+  if (!fits)
+    return set_error(OSMPS_ESHAPE,
+                     "osmps_heff_apply_noalloc: an intermediate of these dimensions alone exceeds "
+                     "the fixed scratch of %zu bytes (use osmps_heff_apply with a context instead)",
+                     NOALLOC_SCRATCH_BYTES);
   const int64_t N1 = d1 * d2 * chi_r;
   const int64_t P1 = wl * d1, Q1 = d1 * wm, P2 = wm * d2, Q2 = d2 * wr;
-  const size_t b_mat1 = align256((size_t)P1 * Q1 * 8), b_mat2 = align256((size_t)P2 * Q2 * 8);
-  const size_t b_t1 = align256((size_t)chi_l * wl * N1 * 8);
-  const size_t b_t2 = align256((size_t)chi_l * d1 * wm * d2 * chi_r * 8);
-  const size_t b_t3 = align256((size_t)chi_l * d1 * d2 * wr * chi_r * 8);
-  const size_t need = b_mat1 + b_mat2 + b_t1 + b_t2 + b_t3;
+  const size_t need = b_mat1 + b_mat2 + b_t1 + b_t2 + b_t3;  // each term <= 32 MiB + 255
   if (need > NOALLOC_SCRATCH_BYTES)
     return set_error(OSMPS_ESHAPE,
                      "osmps_heff_apply_noalloc: these dimensions need %zu bytes of scratch; the "
