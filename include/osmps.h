@@ -77,12 +77,15 @@ const char* osmps_status_string(osmps_status s);
 osmps_status osmps_ctx_create(int device, size_t ws_bytes, osmps_ctx** out);
 osmps_status osmps_ctx_destroy(osmps_ctx* ctx);
 /* Eigensolver used by the split (osmps_split and the sweeps):
- *   OSMPS_EIG_AUTO     (default) the faster of the two as measured at
- *                      chi = 1024 on GB300: currently cuSOLVER;
+ *   OSMPS_EIG_AUTO     (default) the faster of the two as measured on
+ *                      GB300: this library's route for Gram dimension
+ *                      n >= 64, cuSOLVER below;
  *   OSMPS_EIG_CUSOLVER cuSOLVER dsyevd / dsyevdx (largest pairs) always;
  *   OSMPS_EIG_TRIDIAG  this library's Householder reduction (osmps_sytrd;
- *                      cuSOLVER dsytrd above n = 8192), bisection, inverse
- *                      iteration, Cholesky QR and blocked back-transformation
+ *                      cuSOLVER dsytrd above n = 8192), multisection on
+ *                      Sturm counts, inverse iteration, Cholesky QR (cuSOLVER
+ *                      dpotrf for the factor, this library's triangular
+ *                      inverse) and blocked back-transformation
  *                      (float64-accurate emulated GEMMs) for every Gram
  *                      dimension >= 2.
  * Both are float64-accurate. EINVAL for another value.                      */
@@ -191,8 +194,9 @@ osmps_status osmps_dgemm_emu(osmps_ctx* ctx, const double* A, const double* B, d
  * A[j+2.., j]) stored below the subdiagonal of column j (column-major view;
  * the layout of LAPACK's dsytrd with uplo = L). A: n x n device array
  * holding the full symmetric matrix (both triangles), overwritten. Panels of
- * 32 columns on a cooperative kernel, the trailing updates on the
- * float64-accurate emulated tensor-core GEMM. 2 <= n <= 8192, else ESHAPE. */
+ * 32 columns on a cooperative kernel with two grid barriers per column, the
+ * trailing updates on the float64-accurate emulated tensor-core GEMM.
+ * 2 <= n <= 8192, else ESHAPE; ETIMEOUT if a bounded barrier wait gave up. */
 osmps_status osmps_sytrd(osmps_ctx* ctx, double* A, int64_t n, double* d, double* e, double* tau,
                          void* stream);
 

@@ -5,12 +5,17 @@
 //   1. T = Q^T G Q, tridiagonal, by Householder reflections (sytrd.cu: panels
 //      on a cooperative kernel, trailing updates on the emulated GEMM; cuSOLVER
 //      dsytrd above n = 8192).
-//   2. The wanted eigenvalues of T by bisection on Sturm counts (one thread
-//      per eigenvalue; a count is the number of negative pivots of the LDL^T
-//      factorisation of T - x I, with the usual tiny-pivot guard).
+//   2. The wanted eigenvalues of T by multisection on Sturm counts (sign
+//      changes of the leading principal minors of T - x I), eight points per
+//      eigenvalue on eight lanes: float32 counts on T / ||T|| narrow the
+//      bracket to ~1e-5 ||T||; the padded bracket is checked at both ends
+//      with float64 counts (the Gershgorin interval again if the check
+//      fails) and narrowed to eps ||T|| with float64 counts.
 //   3. One eigenvector per eigenvalue by inverse iteration: two solves with
 //      T - lambda I (Gaussian elimination with partial pivoting on the
-//      tridiagonal) from a pseudo-random start, one thread per eigenvalue.
+//      tridiagonal) from a pseudo-random start, one thread per eigenvalue;
+//      the elimination keeps its running row in registers and the back
+//      substitution multiplies by pivot reciprocals formed off the chain.
 //   4. Orthonormalisation of the vectors by Cholesky QR applied twice: the
 //      Gram matrix and the products on the float64-accurate emulated GEMM.
 //      Vectors of nearly equal eigenvalues come out of step 3 as independent
@@ -18,11 +23,14 @@
 //      orthonormal basis of it, so the kept space is right even where the
 //      individual vectors of a cluster are not determined.
 //   5. The back-transformation U = Q Z by blocks of reflectors in compact WY
-//      form, Q_b = I - V T V^T (T from the Schreiber-Van Loan recurrence), each
-//      block two emulated-float64 GEMMs.
+//      form, Q_b = I - V T V^T, T the inverse of triu(V^T V, 1) + diag(1/tau),
+//      each block three emulated-float64 GEMMs.
+// The triangular inverses (of the Cholesky factor in step 4 and of T^-1 in
+// step 5) are this file's column-parallel back substitution.
 // Output: eigenvalues ascending, eigenvectors as rows (the layout the split uses).
 #include <cfloat>
 #include <cmath>
+#include <cstring>
 
 #include "common.cuh"
 #include "sturm.cuh"
@@ -80,29 +88,88 @@ __global__ void k_scale_t(const double* __restrict__ d, const double* __restrict
   }
 }
 
-// ev[j] = eigenvalue n - nev + j of T (ascending), by bisection on T / ||T||
-// (one Sturm chain per thread: on this GPU's float64 pipe, several chains per
-// thread with multisection measured slower than plain bisection).
-__global__ void k_bisect(const double* __restrict__ ds, const double* __restrict__ e2s, int n,
-                         int nev, const double* __restrict__ bounds, double* __restrict__ ev) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nev) return;
-  const int idx = n - nev + j;
-  const double tn = bounds[3];
-  double lo = bounds[0] / tn, hi = bounds[1] / tn;
-  // absolute tolerance eps ||T||: the eigenvalues of a Gram matrix carry that
-  // much rounding anyway, and it bounds the count of halvings (~53)
-  const double tol = DBL_EPSILON;
-  for (int it = 0; it < 160; ++it) {
-    if (hi - lo <= tol) break;
-    const double mid[1] = {0.5 * (lo + hi)};
-    if (!(mid[0] > lo && mid[0] < hi)) break;
-    int c[1];
-    sturm_counts<1>(ds, e2s, n, mid, c);
-    if (c[0] > idx) hi = mid[0];
-    else lo = mid[0];
+// float32 copies of T / ||T|| for the first multisection rounds
+__global__ void k_t_to_f32(const double* __restrict__ ds, const double* __restrict__ e2s, int n,
+                           float* __restrict__ d32, float* __restrict__ e232) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    d32[i] = (float)ds[i];
+    if (i < n - 1) e232[i] = (float)e2s[i];
   }
-  ev[j] = 0.5 * (lo + hi) * tn;
+}
+
+constexpr int MS_PTS = 8;  // multisection points (lanes) per eigenvalue
+
+// ev[j] = eigenvalue n - nev + j of T (ascending). A group of MS_PTS lanes
+// works on one eigenvalue: each round every lane counts the eigenvalues of
+// T / ||T|| below its point, and the group keeps the subinterval that holds
+// the wanted one (the points with count <= idx form a prefix).
+__global__ void __launch_bounds__(32) k_multisect(const double* __restrict__ ds,
+                                                  const double* __restrict__ e2s,
+                                                  const float* __restrict__ d32,
+                                                  const float* __restrict__ e232, int n, int nev,
+                                                  const double* __restrict__ bounds,
+                                                  double* __restrict__ ev) {
+  const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / MS_PTS;
+  const int p = threadIdx.x % MS_PTS;
+  const int lane = threadIdx.x & 31;
+  const int g0 = lane - p;  // first lane of the group
+  const unsigned gmask = ((1u << MS_PTS) - 1u) << g0;
+  if (gid >= nev) return;  // whole groups leave together
+  const int idx = n - nev + gid;
+  const double tn = bounds[3];
+  const double glo = bounds[0] / tn, ghi = bounds[1] / tn;
+  // float32 rounds to a bracket of ~1e-5
+  float flo = (float)glo, fhi = (float)ghi;
+  flo = nextafterf(flo, -INFINITY);
+  fhi = nextafterf(fhi, INFINITY);
+  for (int it = 0; it < 24 && fhi - flo > 1e-5f; ++it) {
+    const float x = flo + (fhi - flo) * (float)(p + 1) / (float)(MS_PTS + 1);
+    const int c = sturm_count_f32(d32, e232, n, x);
+    const int k = __popc(__ballot_sync(gmask, c <= idx) & gmask);
+    const float xl = __shfl_sync(gmask, x, g0 + (k > 0 ? k - 1 : 0));
+    const float xh = __shfl_sync(gmask, x, g0 + (k < MS_PTS ? k : MS_PTS - 1));
+    if (k > 0) flo = xl;
+    if (k < MS_PTS) fhi = xh;
+  }
+  // float64: check the padded bracket at both ends on the first round
+  double lo = (double)flo - 1e-6, hi = (double)fhi + 1e-6;
+  lo = fmax(lo, glo);
+  hi = fmin(hi, ghi);
+  {
+    const double x = p == 0 ? lo : (p == MS_PTS - 1 ? hi : lo + (hi - lo) * p / (MS_PTS - 1));
+    const double xs[1] = {x};
+    int c[1];
+    sturm_counts<1>(ds, e2s, n, xs, c);
+    const unsigned below = __ballot_sync(gmask, c[0] <= idx) & gmask;
+    const int k = __popc(below);
+    const bool valid = ((below >> g0) & 1u) && !((below >> (g0 + MS_PTS - 1)) & 1u);
+    const double xl = __shfl_sync(gmask, x, g0 + (k > 0 ? k - 1 : 0));
+    const double xh = __shfl_sync(gmask, x, g0 + (k < MS_PTS ? k : MS_PTS - 1));
+    if (valid) {
+      lo = xl;
+      hi = xh;
+    } else {
+      lo = glo;
+      hi = ghi;
+    }
+  }
+  // absolute tolerance eps ||T||: the eigenvalues of a Gram matrix carry that
+  // much rounding anyway
+  const double tol = DBL_EPSILON;
+  for (int it = 0; it < 80 && hi - lo > tol; ++it) {
+    const double x = lo + (hi - lo) * (p + 1) / (MS_PTS + 1);
+    const bool inside = x > lo && x < hi;
+    if (!__all_sync(gmask, inside)) break;  // no representable point left between
+    const double xs[1] = {x};
+    int c[1];
+    sturm_counts<1>(ds, e2s, n, xs, c);
+    const int k = __popc(__ballot_sync(gmask, c[0] <= idx) & gmask);
+    const double xl = __shfl_sync(gmask, x, g0 + (k > 0 ? k - 1 : 0));
+    const double xh = __shfl_sync(gmask, x, g0 + (k < MS_PTS ? k : MS_PTS - 1));
+    if (k > 0) lo = xl;
+    if (k < MS_PTS) hi = xh;
+  }
+  if (p == 0) ev[gid] = 0.5 * (lo + hi) * tn;
 }
 
 __device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t a, uint64_t b) {
@@ -119,13 +186,18 @@ __device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t a, uint64
 // or below `noise` (the resolution of the Gram route, n eps ||T||) are not
 // determined by the data; their columns get the normalised pseudo-random
 // start instead, and the orthonormalisation that follows (columns in order)
-// turns them into an orthonormal completion of the resolved ones. Work arrays
-// are interleaved across eigenvalues (W[(k n + i) nev + j]) so that
+// turns them into an orthonormal completion of the resolved ones.
+// The elimination with partial pivoting runs down the rows with the current
+// row in registers (only the pivot division is on the dependence chain) and
+// stores, per row, the reciprocal of the final pivot, the first
+// superdiagonal of U, the multiplier and whether rows i, i+1 were swapped (a
+// swap puts e[i+1] on the second superdiagonal, so that needs no storage).
+// Work arrays are interleaved across eigenvalues (W[i * nev + j]) so that
 // neighbouring threads touch neighbouring addresses.
 __global__ void k_inviter(const double* __restrict__ d, const double* __restrict__ e, int n,
                           int nev, const double* __restrict__ ev,
                           const double* __restrict__ bounds, double* __restrict__ W,
-                          double* __restrict__ Z, uint64_t seed) {
+                          unsigned char* __restrict__ piv, double* __restrict__ Z, uint64_t seed) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nev) return;
   const double lam = ev[j];
@@ -142,76 +214,73 @@ __global__ void k_inviter(const double* __restrict__ d, const double* __restrict
     return;
   }
   const int64_t ld = nev;
-  double* md = W;                              // U diagonal
-  double* mu = W + (int64_t)n * ld;            // U first superdiagonal
-  double* mu2 = W + 2 * (int64_t)n * ld;       // U second superdiagonal
-  double* ml = W + 3 * (int64_t)n * ld;        // multipliers
-  double* mp = W + 4 * (int64_t)n * ld;        // 1 where rows i, i+1 were swapped
-  double* x = W + 5 * (int64_t)n * ld;         // right-hand side / solution
+  double* rcp = W;                        // 1 / pivot of row i (tiny pivots replaced)
+  double* mu = W + (int64_t)n * ld;       // first superdiagonal of U
+  double* ml = W + 2 * (int64_t)n * ld;   // multipliers
+  double* x = W + 3 * (int64_t)n * ld;    // right-hand side / solution
 #define AT(a, i) a[(int64_t)(i) * ld + j]
-  for (int i = 0; i < n; ++i) {
-    AT(md, i) = d[i] - lam;
-    AT(mu, i) = i < n - 1 ? e[i] : 0.0;
-    AT(mu2, i) = 0.0;
-    AT(x, i) = hash_uniform(seed, (uint64_t)j, (uint64_t)i);
-  }
-  // LU with partial pivoting of the tridiagonal (subdiagonal e)
-  for (int i = 0; i < n - 1; ++i) {
-    const double di = AT(md, i), li = e[i];
+  auto store_pivot = [&](int i, double p) {
+    if (fabs(p) < tiny) p = p < 0.0 ? -tiny : tiny;  // a zero (or tiny) pivot becomes a tiny one
+    AT(rcp, i) = 1.0 / p;
+  };
+  // LU with partial pivoting of the tridiagonal (subdiagonal e): the running
+  // row i is (di at column i, ui at column i+1)
+  double di = d[0] - lam, ui = n > 1 ? e[0] : 0.0;
+  for (int i = 0; i + 1 < n; ++i) {
+    const double li = e[i], dn = d[i + 1] - lam, un = i + 2 < n ? e[i + 1] : 0.0;
     if (fabs(di) >= fabs(li)) {
       const double f = di != 0.0 ? li / di : 0.0;
+      store_pivot(i, di);
+      AT(mu, i) = ui;
       AT(ml, i) = f;
-      AT(mp, i) = 0.0;
-      AT(md, i + 1) -= f * AT(mu, i);
+      AT(piv, i) = 0;
+      di = fma(-f, ui, dn);
+      ui = un;
     } else {
       const double f = di / li;
-      AT(md, i) = li;
+      store_pivot(i, li);
+      AT(mu, i) = dn;
       AT(ml, i) = f;
-      AT(mp, i) = 1.0;
-      const double t = AT(mu, i);
-      AT(mu, i) = AT(md, i + 1);
-      AT(md, i + 1) = t - f * AT(md, i + 1);
-      if (i < n - 2) {
-        AT(mu2, i) = AT(mu, i + 1);
-        AT(mu, i + 1) = -f * AT(mu, i + 1);
-      }
+      AT(piv, i) = 1;
+      di = fma(-f, dn, ui);
+      ui = -f * un;
     }
   }
-  for (int i = 0; i < n; ++i)  // a zero (or tiny) pivot is replaced by a tiny one
-    if (fabs(AT(md, i)) < tiny) AT(md, i) = AT(md, i) < 0.0 ? -tiny : tiny;
+  store_pivot(n - 1, di);
   for (int pass = 0; pass < 2; ++pass) {
-    for (int i = 0; i < n - 1; ++i) {  // forward: apply the row swaps and multipliers
-      if (AT(mp, i) == 0.0) {
-        AT(x, i + 1) -= AT(ml, i) * AT(x, i);
+    // forward: the row swaps and multipliers applied to the right-hand side
+    double xi = pass == 0 ? hash_uniform(seed, (uint64_t)j, 0) : AT(x, 0);
+    for (int i = 0; i + 1 < n; ++i) {
+      const double xn = pass == 0 ? hash_uniform(seed, (uint64_t)j, (uint64_t)(i + 1)) : AT(x, i + 1);
+      const double f = AT(ml, i);
+      if (AT(piv, i) == 0) {
+        AT(x, i) = xi;
+        xi = fma(-f, xi, xn);
       } else {
-        const double t = AT(x, i);
-        AT(x, i) = AT(x, i + 1);
-        AT(x, i + 1) = t - AT(ml, i) * AT(x, i + 1);
+        AT(x, i) = xn;
+        xi = fma(-f, xn, xi);
       }
     }
-    double nrm = 0.0;
-    for (int i = n - 1; i >= 0; --i) {  // back substitution with U
+    AT(x, n - 1) = xi;
+    // back substitution with U (second superdiagonal e[i+1] where rows swapped)
+    double x1 = 0.0, x2 = 0.0, nrm = 0.0;
+    for (int i = n - 1; i >= 0; --i) {
       double v = AT(x, i);
-      if (i + 1 < n) v -= AT(mu, i) * AT(x, i + 1);
-      if (i + 2 < n) v -= AT(mu2, i) * AT(x, i + 2);
-      v /= AT(md, i);
+      if (i + 1 < n) v = fma(-AT(mu, i), x1, v);
+      if (i + 2 < n && AT(piv, i)) v = fma(-e[i + 1], x2, v);
+      v *= AT(rcp, i);
       AT(x, i) = v;
       nrm = fma(v, v, nrm);
+      x2 = x1;
+      x1 = v;
     }
     const double sc = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
-    for (int i = 0; i < n; ++i) AT(x, i) *= sc;
+    if (pass == 0)
+      for (int i = 0; i < n; ++i) AT(x, i) *= sc;
+    else
+      for (int i = 0; i < n; ++i) Z[(int64_t)i * nev + col] = AT(x, i) * sc;
   }
-  for (int i = 0; i < n; ++i) Z[(int64_t)i * nev + col] = AT(x, i);
 #undef AT
-}
-
-// Zero the strictly lower part of a column-major m x m matrix.
-__global__ void k_zero_strict_lower(double* __restrict__ A, int64_t m) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m * m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = e / m, r = e - c * m;
-    if (r > c) A[e] = 0.0;
-  }
 }
 
 // Reflectors i0 .. i0+mb-1 of dsytrd (lower) as a dense n x mb row-major V:
@@ -250,12 +319,6 @@ __global__ void k_add_diag(double* __restrict__ S, int64_t k, double v) {
     S[i * k + i] += v;
 }
 
-__global__ void k_sub_inplace(double* __restrict__ Z, const double* __restrict__ D, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    Z[e] -= D[e];
-}
-
 // Y[j * n + i] = U[i * nev + (nev - 1 - j)] (U's columns by decreasing eigenvalue)
 __global__ void k_transpose_nk(const double* __restrict__ U, int64_t n, int64_t nev,
                                double* __restrict__ Y) {
@@ -274,23 +337,117 @@ __global__ void k_transpose_nk(const double* __restrict__ U, int64_t n, int64_t 
 
 int grid1(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 16384)); }
 
+// *emax = max |S_ij - delta_ij| over the k x k matrix S, as the bits of a
+// non-negative double (which order like the double values)
+__global__ void k_identity_err(const double* __restrict__ S, int64_t k,
+                               unsigned long long* __restrict__ emax) {
+  unsigned long long m = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < k * k;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / k, c = e - r * k;
+    const double d = fabs(S[e] - (r == c ? 1.0 : 0.0));
+    const unsigned long long b = isfinite(d) ? (unsigned long long)__double_as_longlong(d)
+                                             : 0x7FF0000000000000ull;
+    m = b > m ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
+    m = x > m ? x : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(emax, m);
+}
+
+// rd[i] = 1 / U[i][i] (U column-major with leading dimension m)
+__global__ void k_diag_rcp(const double* __restrict__ U, int64_t m, double* __restrict__ rd) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    rd[i] = 1.0 / U[i * m + i];
+}
+
+// X = U^-1 for an upper-triangular m x m U (column-major, leading dimension
+// m; the strict lower part is not read), X column-major with zeros below the
+// diagonal. One block per column c of X solves U x = e_c by back
+// substitution in column (axpy) order: x_i = x_i / U_ii, then x_r -= U_ri x_i
+// for r < i, down to i = 0. Thread t holds rows t, t + NT, ... in registers;
+// the finished x_i goes through a two-slot shared broadcast (one barrier
+// per step); the next column of U is loaded one step ahead and the diagonal
+// reciprocals (rd) come precomputed, so a step's dependence chain is one FMA
+// and one multiplication.
+template <int NT, int RPT>
+__global__ void __launch_bounds__(NT) k_trtri_upper(const double* __restrict__ U,
+                                                    const double* __restrict__ rd,
+                                                    double* __restrict__ X, int m) {
+  const int c = blockIdx.x, t = threadIdx.x;
+  __shared__ double sx[2];
+  double xr[RPT], ucur[RPT];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int r = t + NT * k;
+    xr[k] = r == c ? rd[c] : 0.0;
+    ucur[k] = r < c ? U[(int64_t)c * m + r] : 0.0;
+    if (r == c) sx[c & 1] = xr[k];
+  }
+  __syncthreads();
+  for (int i = c; i >= 1; --i) {
+    const double xi = sx[i & 1];
+    double unext[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int r = t + NT * k;
+      unext[k] = r < i - 1 ? U[(int64_t)(i - 1) * m + r] : 0.0;
+    }
+    const double rnext = rd[i - 1];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int r = t + NT * k;
+      if (r < i) xr[k] = fma(-ucur[k], xi, xr[k]);
+      if (r == i - 1) {
+        xr[k] *= rnext;
+        sx[(i - 1) & 1] = xr[k];
+      }
+      ucur[k] = unext[k];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int r = t + NT * k;
+    if (r < m) X[(int64_t)c * m + r] = r <= c ? xr[k] : 0.0;
+  }
+}
+
+// X = U^-1 (upper triangular, column-major, m <= 8192); rd: m doubles of scratch.
+osmps_status trtri_upper(const double* U, double* X, double* rd, int64_t m, cudaStream_t s) {
+  if (m < 1 || m > 8192) return set_error(OSMPS_ESHAPE, "triangular inverse: m=%lld", (long long)m);
+  { k_diag_rcp<<<grid1(m), 256, 0, s>>>(U, m, rd); note_launch(); }
+  const int mi = (int)m;
+  if (m <= 256) { k_trtri_upper<256, 1><<<mi, 256, 0, s>>>(U, rd, X, mi); }
+  else if (m <= 512) { k_trtri_upper<256, 2><<<mi, 256, 0, s>>>(U, rd, X, mi); }
+  else if (m <= 1024) { k_trtri_upper<256, 4><<<mi, 256, 0, s>>>(U, rd, X, mi); }
+  else if (m <= 2048) { k_trtri_upper<256, 8><<<mi, 256, 0, s>>>(U, rd, X, mi); }
+  else if (m <= 4096) { k_trtri_upper<512, 8><<<mi, 512, 0, s>>>(U, rd, X, mi); }
+  else { k_trtri_upper<512, 16><<<mi, 512, 0, s>>>(U, rd, X, mi); }
+  note_launch();
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
 // One Cholesky QR pass: dst = src R^-1 with R^T R = src^T src + shift I
 // (src, dst n x k row-major; S k x k scratch). Returns false in *ok when the
 // Cholesky factorisation breaks down (the columns are numerically dependent).
 osmps_status cholqr_pass(osmps_ctx* ctx, const double* src, double* dst, int64_t n, int64_t k,
-                         double* S, double shift, cudaStream_t s, bool* ok) {
+                         double* S, double shift, cudaStream_t s, bool* ok,
+                         bool have_gram = false) {
   osmps_status st = OSMPS_OK;
   SplitView zt; zt.src = src; zt.rows = k; zt.K = n; zt.s0 = 1; zt.sk = k;  // S = src^T src
-  OSMPS_TRY(gemm_emu(ctx, zt, zt, k, k, n, S, k, s));
+  if (!have_gram) OSMPS_TRY(gemm_emu(ctx, zt, zt, k, k, n, S, k, s));
   if (shift > 0.0) { k_add_diag<<<grid1(k), 256, 0, s>>>(S, k, shift); note_launch(); }
   int lw = 0;
   OSMPS_SOLVER(cusolverDnDpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, (int)k, S, (int)k, &lw));
-  size_t dbytes = 0, hbytes = 0;
-  OSMPS_SOLVER(cusolverDnXtrtri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT,
-                                           k, CUDA_R_64F, S, k, &dbytes, &hbytes));
-  const size_t wbytes = std::max<size_t>((size_t)std::max(lw, 1) * 8, dbytes) + 256;
-  double* work = (double*)ws_get(ctx, SLOT_SPLIT_WORK, wbytes, s, &st);
+  double* work = (double*)ws_get(ctx, SLOT_SPLIT_WORK, (size_t)std::max(lw, 1) * 8 + 256, s, &st);
   if (!work) return st;
+  double* Rinv = (double*)ws_get(ctx, SLOT_EIG_SCAL, (size_t)(k * k + k + 64) * 8, s, &st);
+  if (!Rinv) return st;
   OSMPS_SOLVER(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, (int)k, S, (int)k, work, lw,
                                 ctx->dev_info));
   int info = 0;
@@ -300,18 +457,11 @@ osmps_status cholqr_pass(osmps_ctx* ctx, const double* src, double* dst, int64_t
     *ok = false;
     return OSMPS_OK;
   }
-  std::vector<char> hbuf(std::max<size_t>(hbytes, 1));
-  OSMPS_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, k,
-                                CUDA_R_64F, S, k, work, dbytes, hbuf.data(), hbytes, ctx->dev_info));
-  { k_zero_strict_lower<<<grid1(k * k), 256, 0, s>>>(S, k); note_launch(); }
-  OSMPS_LAUNCH_CHECK();
+  OSMPS_TRY(trtri_upper(S, Rinv, Rinv + k * k, k, s));
   // dst[i][c] = sum_j src[i][j] Rinv(j, c), Rinv column-major (upper)
   SplitView a; a.src = src; a.rows = n; a.K = k; a.s0 = k; a.sk = 1;
-  SplitView b; b.src = S; b.rows = k; b.K = k; b.s0 = k; b.sk = 1;
+  SplitView b; b.src = Rinv; b.rows = k; b.K = k; b.s0 = k; b.sk = 1;
   OSMPS_TRY(gemm_emu(ctx, a, b, n, k, k, dst, k, s));
-  OSMPS_CUDA(cudaMemcpyAsync(&info, ctx->dev_info, sizeof(int), cudaMemcpyDeviceToHost, s));
-  OSMPS_CUDA(cudaStreamSynchronize(s));
-  if (info != 0) return set_error(OSMPS_ECUDA, "eigensolver: triangular inverse failed (%d)", info);
   *ok = true;
   return OSMPS_OK;
 }
@@ -323,7 +473,26 @@ osmps_status orthonormalize(osmps_ctx* ctx, double* Z, double* Z2, int64_t n, in
                             double* S, cudaStream_t s) {
   bool ok = true;
   OSMPS_TRY(cholqr_pass(ctx, Z, Z2, n, k, S, 0.0, s, &ok));
-  if (ok) OSMPS_TRY(cholqr_pass(ctx, Z2, Z, n, k, S, 0.0, s, &ok));
+  if (ok) {
+    // the second pass is skipped when the first already left the columns
+    // orthonormal to 32 eps (max |Z2^T Z2 - I|)
+    SplitView zt; zt.src = Z2; zt.rows = k; zt.K = n; zt.s0 = 1; zt.sk = k;
+    OSMPS_TRY(gemm_emu(ctx, zt, zt, k, k, n, S, k, s));
+    unsigned long long* dmax = reinterpret_cast<unsigned long long*>(ctx->dev_flags + 10);
+    OSMPS_CUDA(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s));
+    { k_identity_err<<<grid1(k * k), 256, 0, s>>>(S, k, dmax); note_launch(); }
+    OSMPS_LAUNCH_CHECK();
+    unsigned long long h = 0;
+    OSMPS_CUDA(cudaMemcpyAsync(&h, dmax, sizeof(h), cudaMemcpyDeviceToHost, s));
+    OSMPS_CUDA(cudaStreamSynchronize(s));
+    double err = 0.0;
+    memcpy(&err, &h, sizeof(err));
+    if (err <= 32.0 * DBL_EPSILON) {
+      OSMPS_CUDA(cudaMemcpyAsync(Z, Z2, (size_t)n * k * 8, cudaMemcpyDeviceToDevice, s));
+      return OSMPS_OK;
+    }
+    OSMPS_TRY(cholqr_pass(ctx, Z2, Z, n, k, S, 0.0, s, &ok, true));
+  }
   if (ok) return OSMPS_OK;
   // Z still holds the input (a failed pass writes nothing)
   const double shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * DBL_EPSILON * 0.5 * (double)k;
@@ -365,15 +534,24 @@ osmps_status eig_top(osmps_ctx* ctx, double* G, int64_t n, int64_t nev, double* 
   { k_gersh<<<1, 256, 0, s>>>(dvec, evec, (int)n, e2, bounds); note_launch(); }
   { k_scale_t<<<grid1(n), 256, 0, s>>>(dvec, e2, (int)n, bounds, ds, e2s); note_launch(); }
   // 8 eigenvalues per block: the multisections spread over the SMs
-  { k_bisect<<<(int)cdiv(nev, 8), 8, 0, s>>>(ds, e2s, (int)n, (int)nev, bounds, ev); note_launch(); }
+  float* d32 = (float*)ws_get(ctx, SLOT_EIG_F32, (size_t)(2 * n + 64) * 4, s, &st);
+  if (!d32) return st;
+  float* e232 = d32 + n;
+  { k_t_to_f32<<<grid1(n), 256, 0, s>>>(ds, e2s, (int)n, d32, e232); note_launch(); }
+  // MS_PTS lanes per eigenvalue, 4 eigenvalues per 32-thread block (spread over the SMs)
+  { k_multisect<<<(int)cdiv(nev * MS_PTS, 32), 32, 0, s>>>(ds, e2s, d32, e232, (int)n, (int)nev,
+                                                           bounds, ev); note_launch(); }
   OSMPS_LAUNCH_CHECK();
-  double* Wk = (double*)ws_get(ctx, SLOT_EIG_X, (size_t)6 * n * nev * 8, s, &st);
+  double* Wk = (double*)ws_get(ctx, SLOT_EIG_X, (size_t)4 * n * nev * 8 + (size_t)n * nev + 256,
+                              s, &st);
   if (!Wk) return st;
+  unsigned char* pivk = reinterpret_cast<unsigned char*>(Wk + 4 * n * nev);
   double* Z = (double*)ws_get(ctx, SLOT_EIG_R, (size_t)2 * n * nev * 8, s, &st);
   if (!Z) return st;
   double* Z2 = Z + n * nev;
-  { k_inviter<<<(int)cdiv(nev, 32), 32, 0, s>>>(dvec, evec, (int)n, (int)nev, ev, bounds, Wk, Z,
-                                                0x5DEECE66Dull); note_launch(); }
+  // 8 eigenvalues per block: the sequential chains spread over the SMs
+  { k_inviter<<<(int)cdiv(nev, 8), 8, 0, s>>>(dvec, evec, (int)n, (int)nev, ev, bounds, Wk, pivk,
+                                              Z, 0x5DEECE66Dull); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   const int64_t mbmax = std::min<int64_t>(WY, n - 1);
   double* S = (double*)ws_get(ctx, SLOT_EIG_S,
@@ -385,9 +563,10 @@ osmps_status eig_top(osmps_ctx* ctx, double* G, int64_t n, int64_t nev, double* 
   double* W1 = S + nev * nev;
   double* W2 = W1 + mbmax * nev;
   double* Tb = W2 + mbmax * nev;
-  double* V = (double*)ws_get(ctx, SLOT_EIG_P, (size_t)(n * mbmax + n * nev + 64) * 8, s, &st);
+  double* V = (double*)ws_get(ctx, SLOT_EIG_P, (size_t)(n * mbmax + 64) * 8, s, &st);
   if (!V) return st;
-  double* D = V + n * mbmax;
+  double* Tw = (double*)ws_get(ctx, SLOT_EIG_SCAL, (size_t)(mbmax * mbmax + mbmax + 64) * 8, s, &st);
+  if (!Tw) return st;
   const int64_t nref = n - 1;
   for (int64_t i0 = ((nref - 1) / WY) * WY; i0 >= 0; i0 -= WY) {
     const int64_t mb = std::min<int64_t>(WY, nref - i0);
@@ -397,31 +576,24 @@ osmps_status eig_top(osmps_ctx* ctx, double* G, int64_t n, int64_t nev, double* 
     OSMPS_TRY(gemm_emu(ctx, vt, vt, mb, mb, n, Tb, mb, s));                  // V^T V
     { k_tinv<<<grid1(mb * mb), 256, 0, s>>>(Tb, tau + i0, mb); note_launch(); }
     OSMPS_LAUNCH_CHECK();
-    size_t dbytes = 0, hbytes = 0;
-    OSMPS_SOLVER(cusolverDnXtrtri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT,
-                                             mb, CUDA_R_64F, Tb, mb, &dbytes, &hbytes));
-    double* work = (double*)ws_get(ctx, SLOT_SPLIT_WORK, dbytes + 256, s, &st);
-    if (!work) return st;
-    std::vector<char> hbuf(std::max<size_t>(hbytes, 1));
-    OSMPS_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, mb,
-                                  CUDA_R_64F, Tb, mb, work, dbytes, hbuf.data(), hbytes,
-                                  ctx->dev_info + 2));
+    OSMPS_TRY(trtri_upper(Tb, Tw, Tw + mb * mb, mb, s));                        // T = (T^-1)^-1
     SplitView zt; zt.src = Z; zt.rows = nev; zt.K = n; zt.s0 = 1; zt.sk = nev;  // Z^T rows
     OSMPS_TRY(gemm_emu(ctx, vt, zt, mb, nev, n, W1, nev, s));                  // W1 = V^T Z
-    SplitView ta; ta.src = Tb; ta.rows = mb; ta.K = mb; ta.s0 = 1; ta.sk = mb;  // T rows (col-major)
+    SplitView ta; ta.src = Tw; ta.rows = mb; ta.K = mb; ta.s0 = 1; ta.sk = mb;  // T rows (col-major)
     SplitView w1t; w1t.src = W1; w1t.rows = nev; w1t.K = mb; w1t.s0 = 1; w1t.sk = nev;
     OSMPS_TRY(gemm_emu(ctx, ta, w1t, mb, nev, mb, W2, nev, s));                // W2 = T W1
     SplitView vr; vr.src = V; vr.rows = n; vr.K = mb; vr.s0 = mb; vr.sk = 1;
     SplitView w2t; w2t.src = W2; w2t.rows = nev; w2t.K = mb; w2t.s0 = 1; w2t.sk = nev;
-    OSMPS_TRY(gemm_emu(ctx, vr, w2t, n, nev, mb, D, nev, s));                  // D = V W2
-    { k_sub_inplace<<<grid1(n * nev), 256, 0, s>>>(Z, D, n * nev); note_launch(); }
-    OSMPS_LAUNCH_CHECK();
+    OSMPS_TRY(gemm_emu(ctx, vr, w2t, n, nev, mb, Z, nev, s, true));            // Z -= V W2
   }
   {
-    int info = 0;
-    OSMPS_CUDA(cudaMemcpyAsync(&info, ctx->dev_info + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int flag = 0;
+    OSMPS_CUDA(cudaMemcpyAsync(&flag, ctx->dev_flags + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
     OSMPS_CUDA(cudaStreamSynchronize(s));
-    if (info != 0) return set_error(OSMPS_ECUDA, "eigensolver: WY factor inverse failed (%d)", info);
+    if (flag != 0) {
+      cudaMemsetAsync(ctx->dev_flags + 3, 0, sizeof(int), s);
+      return set_error(OSMPS_ETIMEOUT, "eigensolver: a grid barrier wait of the reduction gave up");
+    }
   }
   dim3 grid((unsigned)cdiv(n, 32), (unsigned)cdiv(nev, 32));
   { k_transpose_nk<<<grid, dim3(32, 8), 0, s>>>(Z, n, nev, Y); note_launch(); }

@@ -12,11 +12,20 @@
 //     a run of 256 of them sums to less than 2^22: exact in the float32 TMEM
 //     accumulator;
 //   * the epilogue adds those exact integers in int32 per slice diagonal
-//     i + j (same unit 2^(-7(i+j+2))) and moves each diagonal into float64
-//     once, over the 36 pairs with i + j <= 7 (the dropped pairs are below
-//     2^-56 of the row scales); the tile is scaled back by 2^(e_A + e_B).
-// GB300's float64 pipe is what limits this kind of kernel, so the float64
-// work is kept to ~10 operations per output element per tile.
+//     i + j (same unit 2^(-7(i+j+2))), over the 36 pairs with i + j <= 7
+//     (the dropped pairs are below 2^-56 of the row scales);
+//   * pairs on one diagonal share the unit, so a TMEM partial sum runs over
+//     up to 4 K blocks of 64 across the pairs of a diagonal (at K = 64 the
+//     36 pairs take 12 epilogue rounds, not 36);
+//   * the diagonals are combined exactly in int64, Horner fashion in steps
+//     of 2^7, within groups of consecutive diagonals (two groups of four
+//     while K <= 2^17, whose sums stay below 2^53); each group sum becomes
+//     a float64 by integer operations on the IEEE bits, the row and column
+//     scales 2^(e_A + e_B) folded into its exponent, and the group values
+//     are added in float64 in a second TMEM region. One float64 addition per
+//     output element and tile remains: GB300's float64 pipe is what limits
+//     this kind of kernel otherwise. The result is stored, or subtracted
+//     from C.
 // The kernel reuses the persistent, warp-specialised structure of gemm_tc:
 // 128 x 128 tiles, a 6-stage TMA ring, two 128-column TMEM buffers, 16
 // epilogue warps each holding 32 float64 accumulators per row.
@@ -44,8 +53,8 @@ constexpr int E_EPI_WARPS = 16;
 constexpr int E_EPI_COLS = EBN / 4;
 constexpr int E_THREADS = 64 + 32 * E_EPI_WARPS;
 constexpr int E_CHUNK = 4;  // 64-element K slices per exact partial sum (256 products)
-constexpr uint32_t E_TMEM_COLS = 256;
-constexpr int FLUSH_EVERY = 64;  // chunks per int32 run: 64 * 2^22 < 2^31
+constexpr uint32_t E_TMEM_COLS = 512;   // 2 x 128 accumulator columns, then the float64 sums
+constexpr uint32_t E_ACC_COL0 = 256;    // float64 group sums: two 32-bit columns per tile column
 constexpr size_t E_SMEM = (size_t)ESTAGES * E_STAGE + 1024 + 256;
 
 struct PairList {
@@ -53,11 +62,64 @@ struct PairList {
   unsigned char a[64], b[64];
 };
 
+// x 2^k as a float64 for an integer |x| < 2^53, built from the IEEE-754 bit
+// layout (sign, biased exponent, 52 fraction bits) with integer operations
+// only; exact whenever the result is a normal number, else left to scalbn.
+__device__ __forceinline__ double i64_ldexp(long long x, int k) {
+  if (x == 0) return 0.0;
+  const unsigned long long a = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+  const int e = 63 - __clzll((long long)a);  // a in [2^e, 2^(e+1)), e <= 52
+  const int E = e + k + 1023;
+  if (E <= 0 || E >= 2047) return scalbn((double)x, k);
+  const unsigned long long frac = (a << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(((unsigned long long)(x < 0) << 63) |
+                                          ((unsigned long long)E << 52) | frac));
+}
+
+// Close a diagonal group of the epilogue: its sums H (the last diagonal `cur`
+// at weight 1) become float64 with the scales folded in and are added to the
+// float64 sums of the earlier groups kept in TMEM (acc_t); after the last
+// group the total is stored to C (or subtracted from it). H is zeroed.
+__device__ __forceinline__ void close_group(long long (&H)[E_EPI_COLS], int& groups, bool last,
+                                            uint32_t acc_t, int cur, int ea,
+                                            const int* __restrict__ eB, int64_t col0, int64_t N,
+                                            int64_t row, int64_t M, double* __restrict__ C,
+                                            int64_t ldc, int subtract) {
+  const int k0 = -SLICE_BITS * (cur + 2) + ea;
+#pragma unroll
+  for (int h = 0; h < E_EPI_COLS / 8; ++h) {  // 8 values = 16 TMEM words at a time
+    uint32_t w[16];
+    if (groups > 0) tmem_ld16(acc_t + 16 * h, w);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = 8 * h + i;
+      const int eb = (col0 + j < N) ? eB[col0 + j] : 0;
+      double v = i64_ldexp(H[j], k0 + eb);
+      if (groups > 0) v += __hiloint2double((int)w[2 * i + 1], (int)w[2 * i]);
+      if (last) {
+        if (row < M && col0 + j < N) {
+          double* dst = C + row * ldc + col0 + j;
+          if (subtract) *dst -= v;
+          else *dst = v;
+        }
+      } else {
+        w[2 * i] = (uint32_t)__double2loint(v);
+        w[2 * i + 1] = (uint32_t)__double2hiint(v);
+      }
+      H[j] = 0;
+    }
+    if (!last) tmem_st16(acc_t + 16 * h, w);
+  }
+  if (!last) tmem_st_wait();
+  ++groups;
+}
+
 __global__ void __launch_bounds__(E_THREADS, 1)
     k_gemm_emu(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                double* __restrict__ C, int64_t M, int64_t N, int64_t ldc, int nkb, int Kp,
                int tiles_n, int n_tiles, const int* __restrict__ eA, const int* __restrict__ eB,
-               const __grid_constant__ PairList pl, int* __restrict__ err) {
+               const __grid_constant__ PairList pl, int* __restrict__ err, int subtract,
+               int group_diags) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -92,7 +154,12 @@ __global__ void __launch_bounds__(E_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int npairs = pl.n;
-  const int cpp = (nkb + E_CHUNK - 1) / E_CHUNK;  // chunks per pair
+  // the K block kb of pair q is the last of its TMEM partial sum when the
+  // sum holds E_CHUNK blocks or the next block belongs to another diagonal
+  auto chunk_ends = [&](int q, int kb, int inchunk) {
+    return inchunk == E_CHUNK ||
+           (kb == nkb - 1 && (q == npairs - 1 || pl.a[q + 1] + pl.b[q + 1] != pl.a[q] + pl.b[q]));
+  };
 
   if (warp == 0 && lane == 0) {
     uint32_t g = 0, issued = 0;
@@ -122,9 +189,10 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     uint32_t g = 0, gc = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      int inchunk = 0;
       for (int q = 0; q < npairs && ok; ++q) {
         for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
-          const bool first = (kb % E_CHUNK) == 0;
+          const bool first = inchunk == 0;
           const uint32_t buf = gc & 1u;
           if (first) {
             if (!mbar_wait(&tempty[buf], ((gc >> 1) & 1u) ^ 1u)) {
@@ -146,9 +214,10 @@ __global__ void __launch_bounds__(E_THREADS, 1)
           for (int k = 0; k < 4; ++k)
             umma<TC_BF16>(dt, ad + 2u * k, bd + 2u * k, id, (!first || k > 0) ? 1u : 0u);
           umma_commit(&empty[s]);
-          if ((kb % E_CHUNK) == E_CHUNK - 1 || kb == nkb - 1) {
+          if (chunk_ends(q, kb, ++inchunk)) {
             umma_commit(&tfull[buf]);
             ++gc;
+            inchunk = 0;
           }
         }
       }
@@ -158,32 +227,35 @@ __global__ void __launch_bounds__(E_THREADS, 1)
   } else if (warp >= 2) {
     const int qd = warp & 3;
     const int part = (warp - 2) >> 2;
+    // this thread's float64 group sums: TMEM lane of its row, two columns per value
+    const uint32_t acc_t = tmem + ((uint32_t)(qd * 32) << 16) + E_ACC_COL0 + part * 2 * E_EPI_COLS;
     uint32_t gc = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const int m0 = (tile / tiles_n) * EBM, n0 = (tile % tiles_n) * EBN;
-      double acc[E_EPI_COLS];  // float64 sum of the flushed diagonals
-      int iacc[E_EPI_COLS];    // exact integer sum of the current diagonal
+      const int64_t row = (int64_t)m0 + qd * 32 + lane;
+      const int64_t col0 = (int64_t)n0 + part * E_EPI_COLS;
+      const int ea = row < M ? eA[row] : 0;
+      long long H[E_EPI_COLS];  // exact group sum, the current diagonal at weight 1
 #pragma unroll
-      for (int j = 0; j < E_EPI_COLS; ++j) {
-        acc[j] = 0.0;
-        iacc[j] = 0;
-      }
+      for (int j = 0; j < E_EPI_COLS; ++j) H[j] = 0;
       int cur = pl.a[0] + pl.b[0];
-      int run = 0;
+      int inchunk = 0, groups = 0;
       for (int q = 0; q < npairs && ok; ++q) {
         const int diag = pl.a[q] + pl.b[q];
-        for (int c = 0; c < cpp; ++c, ++gc) {
-          if (diag != cur || run == FLUSH_EVERY) {
-            // flush: sum(int) x 2^(-7 (cur + 2)) into float64, once per diagonal
-            const double unit = ldexp(1.0, -SLICE_BITS * (cur + 2));
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+          if (!chunk_ends(q, kb, ++inchunk)) continue;
+          inchunk = 0;
+          if (diag != cur) {
+            if (diag / group_diags != cur / group_diags) {
+              close_group(H, groups, false, acc_t, cur, ea, eB, col0, N, row, M, C, ldc,
+                          subtract);
+            } else {
+              const int sh = SLICE_BITS * (diag - cur);
 #pragma unroll
-            for (int j = 0; j < E_EPI_COLS; ++j) {
-              acc[j] = fma((double)iacc[j], unit, acc[j]);
-              iacc[j] = 0;
+              for (int j = 0; j < E_EPI_COLS; ++j) H[j] <<= sh;
             }
             cur = diag;
-            run = 0;
           }
           const uint32_t buf = gc & 1u;
           if (!mbar_wait(&tfull[buf], (gc >> 1) & 1u)) {
@@ -201,30 +273,17 @@ __global__ void __launch_bounds__(E_THREADS, 1)
             for (int i = 0; i < 16; ++i) {
               // exact integer (|v| < 2^22): v + 1.5*2^23 has v in its low mantissa bits
               const float v = __uint_as_float(r[i]) + 12582912.0f;
-              iacc[16 * j + i] += (int)(__float_as_uint(v) - 0x4B400000u);
+              H[16 * j + i] += (int)(__float_as_uint(v) - 0x4B400000u);
             }
           }
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty[buf]);
-          ++run;
+          ++gc;
         }
       }
       if (!ok) break;
-      {
-        const double unit = ldexp(1.0, -SLICE_BITS * (cur + 2));
-#pragma unroll
-        for (int j = 0; j < E_EPI_COLS; ++j) acc[j] = fma((double)iacc[j], unit, acc[j]);
-      }
-      const int64_t row = (int64_t)m0 + qd * 32 + lane;
-      const int64_t col0 = (int64_t)n0 + part * E_EPI_COLS;
-      if (row < M) {
-        const int ea = eA[row];
-        double* dst = C + row * ldc + col0;
-#pragma unroll
-        for (int j = 0; j < E_EPI_COLS; ++j)
-          if (col0 + j < N) dst[j] = scalbn(acc[j], ea + eB[col0 + j]);
-      }
+      close_group(H, groups, true, acc_t, cur, ea, eB, col0, N, row, M, C, ldc, subtract);
     }
     if (!ok) atomicOr(err, 1);
   }
@@ -405,7 +464,8 @@ PairList make_pairs() {
 }  // namespace
 
 osmps_status gemm_emu(osmps_ctx* ctx, const SplitView& a, const SplitView& b, int64_t M,
-                      int64_t N, int64_t K, double* C, int64_t ldc, cudaStream_t s) {
+                      int64_t N, int64_t K, double* C, int64_t ldc, cudaStream_t s,
+                      bool subtract) {
   if (M <= 0 || N <= 0) return OSMPS_OK;
   if (K <= 0 || a.rows != M || b.rows != N || a.K != K || b.K != K)
     return set_error(OSMPS_ESHAPE, "gemm_emu: inconsistent operand views");
@@ -435,10 +495,14 @@ osmps_status gemm_emu(osmps_ctx* ctx, const SplitView& a, const SplitView& b, in
   const int n_tiles = tiles_n * (int)cdiv(M, EBM);
   const int grid = std::min(n_tiles, ctx->sm_count);
   const int nkb = (int)(Kp / 64);
+  // diagonals per exact int64 group: four while a group sum stays below 2^53
+  // (|I_d| < (d + 1) K 2^14 with slice digits of at most 2^7 and 2^6), else two
+  const int group_diags = Kp <= ((int64_t)1 << 17) ? 4 : 2;
   const int ph = prof_begin(s);
   {
     k_gemm_emu<<<grid, E_THREADS, E_SMEM, s>>>(ma, mb, C, M, N, ldc, nkb, (int)Kp, tiles_n,
-                                               n_tiles, eA, eB, pl, ctx->dev_flags);
+                                               n_tiles, eA, eB, pl, ctx->dev_flags,
+                                               subtract ? 1 : 0, group_diags);
     note_launch();
   }
   OSMPS_LAUNCH_CHECK();

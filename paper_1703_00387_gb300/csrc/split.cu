@@ -1,19 +1,20 @@
 // Two-site split with truncation by the eigendecomposition route (Sec. 2,
 // Eq. AAD_ULLUD and Eq. ThetaAL), entirely in float64:
-//   left-to-right: G = M M^T (Gram on the DMMA GEMM), G = U lambda^2 U^T
-//                  (cuSOLVER syevd), A1 = U_kept, A2 = U_kept^T M / ||.||
+//   left-to-right: G = M M^T (Gram matrix), G = U lambda^2 U^T (float64
+//                  eigenpairs), A1 = U_kept, A2 = U_kept^T M / ||.||
 //   right-to-left: G = M^T M, A2 = V_kept^T, A1 = M V_kept / ||.||
 // with M = theta viewed as (chi_l d1) x (d2 chi_r). The number kept follows
 // the local tolerance (Eq. elocal, Sec. 3.4): chi' = min(chi_max, smallest n
 // with discarded weight <= eps_local), lambda^2 normalised to sum 1. The
 // eigenvalues are copied to the host to fix chi' (the next shapes depend on it).
 //
-// Arithmetic: the eigenpairs are float64, from cuSOLVER (dsyevdx for the
-// largest min(chi_max, rank) only, dsyevd when that is all of them) or, when
-// the context selects it (osmps_ctx_set_eig_solver), from the tridiagonal
-// route of eig.cu (this library's Householder tridiagonalisation, then
-// bisection, inverse iteration, Cholesky QR and blocked back-transformation
-// on emulated-float64 GEMMs). The
+// Arithmetic: the eigenpairs are float64, from the tridiagonal route of
+// eig.cu (this library's Householder tridiagonalisation, then multisection,
+// inverse iteration, Cholesky QR and blocked back-transformation on
+// emulated-float64 GEMMs; the default from Gram dimension 64 on) or from
+// cuSOLVER (dsyevdx for the largest min(chi_max, rank) only, dsyevd when
+// that is all of them; the default below 64), as osmps_ctx_set_eig_solver
+// selects. The
 // Gram matrix and the projection are float64 GEMMs: on the DMMA kernel for
 // OSMPS_PREC_FP64, on the float64-accurate emulated tensor-core GEMM for
 // every other precision.
@@ -203,7 +204,10 @@ osmps_status split_impl(osmps_ctx* ctx, const double* theta, double* A1, double*
   OSMPS_SOLVER(cusolverDnSetStream(ctx->solver, s));
   int lwork = 0, found = 0;
   double* Z = nullptr;  // eigenvectors, column-major n x nev (rows of a row-major nev x n)
-  const bool tridiag = ctx->eig_solver == OSMPS_EIG_TRIDIAG;
+  // AUTO: this library's route from Gram dimension 64 on, where it measured
+  // faster than cuSOLVER on GB300 (n = 64 ... 2048), cuSOLVER below
+  const bool tridiag = ctx->eig_solver == OSMPS_EIG_TRIDIAG ||
+                       (ctx->eig_solver == OSMPS_EIG_AUTO && n >= 64);
   if (tridiag && n >= 2) {
     double* Y = (double*)ws_get(ctx, SLOT_SPLIT_TMP2, (size_t)nev * n * 8, s, &st);
     if (!Y) return st;

@@ -152,6 +152,25 @@ def _split_case(seed, shape, decay):
     return (M / np.linalg.norm(M)).reshape(shape)
 
 
+# The Gram route resolves the discarded weight 1 - (kept sum)/||theta||^2 to a
+# few eps ||theta||^2: a cut whose oracle tail lies that close to eps_local can
+# fall on either side of it.
+DISC_RES = 8 * 2.2e-16
+
+
+def _oracle_split_at(theta, chi_max, eps, move_right, chn):
+    """The oracle's SVD split for the GPU's kept count chn: its own truncation,
+    or, where chn is one off it and the oracle's discarded weight at chn lies
+    within DISC_RES of eps (||theta|| = 1), its split truncated at chn."""
+    a_ref, b_ref, info = od.split_svd(theta, chi_max, eps, bool(move_right))
+    if chn != info["keep"]:
+        tail = float(np.sum(info["lam2"][chn:]))
+        assert abs(chn - info["keep"]) == 1 and abs(tail - eps) <= DISC_RES, \
+            (chn, info["keep"], tail, eps)
+        a_ref, b_ref, info = od.split_svd(theta, chn, 0.0, bool(move_right))
+    return a_ref, b_ref, info
+
+
 @pytest.mark.parametrize("split_prec", ["fp64", "fp64emu", "bf16x3"])
 @pytest.mark.parametrize("move_right", [1, 0])
 @pytest.mark.parametrize("shape,chi_max,eps", [((8, 2, 2, 8), 100, 0.0), ((40, 2, 2, 30), 20, 0.0),
@@ -162,13 +181,13 @@ def test_split_parity(ctx, move_right, shape, chi_max, eps, split_prec):
     on the float64-accurate emulated GEMM; eigenpairs from float64 cuSOLVER
     in both. All must give the float64 answer."""
     theta = _split_case(11, shape, 0.35)
-    a_ref, b_ref, info = od.split_svd(theta, chi_max, eps, bool(move_right))
     chi_l, d1, d2, chi_r = shape
     cap = min(chi_l * d1, d2 * chi_r)
     A1 = torch.empty(chi_l * d1 * cap, dtype=torch.float64, device="cuda:0")
     A2 = torch.empty(cap * d2 * chi_r, dtype=torch.float64, device="cuda:0")
     chn, disc, ent, lam2 = B.osmps_split(ctx, dev(theta), A1, A2, move_right, chi_max, eps,
                                          precision=split_prec)
+    a_ref, b_ref, info = _oracle_split_at(theta, chi_max, eps, move_right, chn)
     assert chn == info["keep"]
     # only the largest min(chi_max, rank) values are computed; the Gram route
     # squares the singular values, so lambda^2 carries an absolute error of a
@@ -291,7 +310,6 @@ def test_split_eigensolvers(ctx, solver, move_right, spectrum, shape, chi_max):
     # exact zeros: a tolerance stops both sides at the rank (cuts are multiples of 3 so
     # that no exact multiplet is split)
     eps = 1e-14 if spectrum == "rank_deficient" else 0.0
-    a_ref, b_ref, info = od.split_svd(theta, chi_max, eps, bool(move_right))
     cap = r
     A1 = torch.empty(chi_l * d1 * cap, dtype=torch.float64, device="cuda:0")
     A2 = torch.empty(cap * d2 * chi_r, dtype=torch.float64, device="cuda:0")
@@ -301,6 +319,7 @@ def test_split_eigensolvers(ctx, solver, move_right, spectrum, shape, chi_max):
                                              precision="fp64emu")
     finally:
         ctx.set_eig_solver("auto")
+    a_ref, b_ref, info = _oracle_split_at(theta, chi_max, eps, move_right, chn)
     assert chn == info["keep"]
     k = min(chi_max, len(info["lam2"]))
     np.testing.assert_allclose(lam2[:k], info["lam2"][:k], rtol=1e-12, atol=1e-14)
