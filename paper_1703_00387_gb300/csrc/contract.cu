@@ -396,7 +396,13 @@ osmps_status env_update_impl(osmps_ctx* ctx, int side, const double* env_in, con
     if (side == 0) return env_left_emu(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
     return env_right_emu(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
   }
-  if (precision == OSMPS_PREC_FP64) {
+  // Updates of under 2^20 multiply-adds (bond dimensions of a few tens at
+  // most) take the float64 path in every precision: they are launch-bound,
+  // and the split operands would add their 2^-16 representation error per
+  // factor where too few terms meet to average it out.
+  const double macs = (double)chi_l * (double)chi_r * (double)d *
+                      ((double)chi_l * (double)w_in + (double)chi_r * (double)w_out);
+  if (precision == OSMPS_PREC_FP64 || macs < (double)(1 << 20)) {
     if (side == 0) return env_left_f64(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
     return env_right_f64(ctx, env_in, A, W, env_out, chi_l, d, chi_r, w_in, w_out, stream);
   }

@@ -1,13 +1,14 @@
 """GPU parity of the single operations against the FP64 oracle.
 
-Bars (norm-wise relative error of the output): 1e-12 for OSMPS_PREC_FP64 and
-1e-5 for tf32x3 everywhere; bf16x3 meets 1e-5 at the chi = 1024 workload,
-where errors average over long sums, and on small shapes is held to its
-representation bound: a bf16 hi+lo pair carries 16 significant bits
-(|x - hi - lo| <= 2^-16 |x|), so one product term can be off by
-3 * 2^-16 = 4.6e-5 of its size. Shapes cover a single tile, several tiles
-with ragged tails in M, N and K, and the full chi = 1024 shape the
-benchmark times."""
+Bars (norm-wise relative error of the output): 1e-12 for OSMPS_PREC_FP64
+and the emulated float64 mode, 1e-5 for both reduced-precision modes
+(bf16x3, tf32x3) at every shape. A bf16 hi+lo pair carries 16 significant
+bits (|x - hi - lo| <= 2^-16 |x|); over the four split factors of H_eff.theta
+the norm-wise error measures about 6e-6 on every shape here. Environment
+updates of under 2^20 multiply-adds run in float64 in every precision (too
+few terms meet there for the split errors to average). Shapes cover a single
+tile, several tiles with ragged tails in M, N and K, and the full chi = 1024
+shape the benchmark times."""
 import numpy as np
 import pytest
 
@@ -18,8 +19,8 @@ from paper_1703_00387_gb300 import hamiltonians, inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "bf16x3": 5e-5, "tf32x3": 1e-5, "fp64emu": 1e-12}
-TOL_FULL = {"fp64": 1e-12, "bf16x3": 1e-5, "tf32x3": 1e-5, "fp64emu": 1e-12}
+TOL = {"fp64": 1e-12, "bf16x3": 1e-5, "tf32x3": 1e-5, "fp64emu": 1e-12}
+TOL_FULL = TOL
 
 
 @pytest.fixture(scope="module")
