@@ -200,6 +200,20 @@ osmps_status osmps_dgemm_emu(osmps_ctx* ctx, const double* A, const double* B, d
 osmps_status osmps_sytrd(osmps_ctx* ctx, double* A, int64_t n, double* d, double* e, double* tau,
                          void* stream);
 
+/* Self-test of the failure path of the bounded device waits (the paper has
+ * no counterpart: a robustness check of this library). Every wait in this
+ * library's kernels gives up after a time limit, records the failure, frees
+ * what the kernel holds and returns; the call then reports ETIMEOUT and the
+ * context stays usable. This call makes one such wait run out on purpose,
+ * with a limit of limit_us microseconds (1 .. 1e6, else EINVAL):
+ *   which = 0: a kernel that holds tensor memory waits on an mbarrier that
+ *              no thread arrives at, then frees the tensor memory;
+ *   which = 1: a cooperative grid waits at a grid barrier one of its blocks
+ *              never reaches.
+ * Returns OSMPS_ETIMEOUT when the wait gave up (the expected outcome), OK
+ * otherwise. Synchronises `stream`.                                          */
+osmps_status osmps_selftest_wait_timeout(osmps_ctx* ctx, int which, double limit_us, void* stream);
+
 /* Environment update (Sec. 3.4: the fixed sites are contracted into L and R
  * one site at a time).
  * side 0 (grow L past site k):

@@ -88,6 +88,7 @@ _SIGS = {
     "osmps_heff_apply_noalloc": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 + [_vp]),
     "osmps_dgemm_emu": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _vp]),
     "osmps_sytrd": (_c.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "osmps_selftest_wait_timeout": (_c.c_int, [_vp, _c.c_int, _c.c_double, _vp]),
     "osmps_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_c.c_int, _vp]),
     "osmps_lanczos_ground": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 +
                              [_c.c_int, _c.c_double, _c.c_int, _dp, _c.POINTER(_c.c_int), _dp, _vp]),
@@ -689,6 +690,13 @@ def osmps_sytrd(ctx, A, d, e, tau, stream=None):
     n = A.shape[0]
     _check(lib().osmps_sytrd(ctx.ptr, _dev(A, "A"), n, _dev(d, "d"), _dev(e, "e"), _dev(tau, "tau"),
                              _stream(stream)))
+
+
+def osmps_selftest_wait_timeout(ctx, which, limit_us=2000.0, stream=None):
+    """Make one bounded device wait run out on purpose (which = 0: an mbarrier
+    wait in a kernel holding tensor memory; 1: a grid barrier one block never
+    reaches). Raises OsmpsError(ETIMEOUT) when the wait gave up, as it should."""
+    _check(lib().osmps_selftest_wait_timeout(ctx.ptr, int(which), float(limit_us), _stream(stream)))
 
 
 def osmps_variance(ctx, mps, mpo, stream=None):

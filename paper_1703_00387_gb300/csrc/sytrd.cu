@@ -33,6 +33,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "gridsync.cuh"
 
 namespace osmps {
 namespace {
@@ -43,7 +44,6 @@ constexpr int ST_WARPS = ST_THREADS / 32;
 constexpr int MAXLOC = 64;        // rows per block at most
 constexpr int PW = 2 * NB + 2;    // partial sums per block: y | z | t^T v | ssq
 constexpr int P_TV = 2 * NB, P_SSQ = 2 * NB + 1;
-constexpr uint64_t BAR_LIMIT_NS = 2000000000ull;
 
 struct SytrdArgs {
   double* A;         // n x n, full symmetric (row r contiguous)
@@ -60,46 +60,6 @@ struct SytrdArgs {
   unsigned bar_base; // counter value at the start of this launch
   int* err;          // bit 0: a barrier wait gave up
 };
-
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier over the G co-resident blocks: every block adds one to
-// the counter and waits until it reaches `target`. Writes made by the block
-// before the barrier are visible to every block after it. The wait is
-// bounded; on time-out the error bit is set and false is returned in every
-// thread of the block (the caller leaves the kernel).
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* err,
-                                             int* s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
-    uint64_t t0 = 0;
-    int ok = 1;
-    for (unsigned it = 0;; ++it) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-      if ((int)(v - target) >= 0) break;
-      if ((it & 63u) == 0) {
-        const uint64_t now = gtimer();
-        if (it == 0) t0 = now;
-        else if (now - t0 > BAR_LIMIT_NS) {
-          atomicOr(err, 1);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
-}
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -44,15 +44,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity to complete: false once
+// limit_ns of wall time (%globaltimer) have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint64_t limit_ns = WAIT_LIMIT_NS) {
   uint64_t t0 = 0;
   for (uint32_t i = 0;; ++i) {
     if (mbar_try(bar, parity)) return true;
     if ((i & 255u) == 0) {
       uint64_t t = globaltimer();
       if (i == 0) t0 = t;
-      else if (t - t0 > WAIT_LIMIT_NS) return false;
+      else if (t - t0 > limit_ns) return false;
     }
   }
 }
