@@ -288,10 +288,12 @@ osmps_status split_operand(const SplitView& v, int kind, void* dst, int64_t Kp, 
 // Float64-accurate GEMM on the bf16 tensor cores (error-free slicing):
 // C[M,N] = sum_k a(m,k) b(n,k), with a and b given as views (SplitView: row
 // m / n, column k; float64 sources). C is float64, row-major, ldc. With
-// subtract, C[M,N] -= the product instead (C must not overlap a or b).
+// subtract, C[M,N] -= the product instead (C must not overlap a or b). With
+// small_on_dmma, products that the float64 DMMA kernel finishes in an
+// estimated 40 us (plain float64 views) run there instead of the emulation.
 osmps_status gemm_emu(osmps_ctx* ctx, const SplitView& a, const SplitView& b, int64_t M,
                       int64_t N, int64_t K, double* C, int64_t ldc, cudaStream_t s,
-                      bool subtract = false);
+                      bool subtract = false, bool small_on_dmma = true);
 
 // ---------------------------------------------------------------------------
 // Small contractions with an MPO tensor ("W-steps"): for every fiber

@@ -465,10 +465,29 @@ PairList make_pairs() {
 
 osmps_status gemm_emu(osmps_ctx* ctx, const SplitView& a, const SplitView& b, int64_t M,
                       int64_t N, int64_t K, double* C, int64_t ldc, cudaStream_t s,
-                      bool subtract) {
+                      bool subtract, bool small_on_dmma) {
   if (M <= 0 || N <= 0) return OSMPS_OK;
   if (K <= 0 || a.rows != M || b.rows != N || a.K != K || b.K != K)
     return set_error(OSMPS_ESHAPE, "gemm_emu: inconsistent operand views");
+  // Small products go to the float64 DMMA kernel, which is float64-accurate
+  // too: the emulation costs about 56 us even for one tile (slicing passes,
+  // 36 slice pairs), while the DMMA kernel spreads its 64 x 64 tiles over the
+  // SMs at about 8 GFLOP/s each. Taken when that estimate is under 40 us.
+  const double dmma_tiles =
+      std::min<double>((double)cdiv(M, 64) * (double)cdiv(N, 64), (double)ctx->sm_count);
+  const double dmma_us = 2.0 * (double)M * (double)N * (double)K / (dmma_tiles * 8e3);
+  if (small_on_dmma && a.n1 == 1 && b.n1 == 1 && !a.src_f32 && !b.src_f32 && dmma_us < 40.0) {
+    GemmF64 g;
+    g.M = M; g.N = N; g.K = K;
+    g.A = static_cast<const double*>(a.src); g.sam = a.s0; g.sak = a.sk;
+    g.B = static_cast<const double*>(b.src); g.sbk = b.sk; g.sbn = b.s0;
+    g.C = C; g.scm = ldc; g.scn = 1;
+    if (subtract) {
+      g.alpha = -1.0;
+      g.beta = 1.0;
+    }
+    return gemm_f64(g, s);
+  }
   const int64_t Kp = round_up(K, 64);
   if (SLICES * Kp > ((int64_t)1 << 31) || cdiv(M, EBM) * cdiv(N, EBN) > ((int64_t)1 << 31))
     return set_error(OSMPS_ESHAPE, "gemm_emu: dimensions exceed the supported range");
@@ -527,5 +546,5 @@ extern "C" osmps_status osmps_dgemm_emu(osmps_ctx* ctx, const double* A, const d
   a.src = A; a.rows = M; a.K = K; a.s0 = K; a.sk = 1;
   SplitView b;  // row n of the B operand = column n of B
   b.src = B; b.rows = N; b.K = K; b.s0 = 1; b.sk = N;
-  return gemm_emu(ctx, a, b, M, N, K, C, N, (cudaStream_t)stream);
+  return gemm_emu(ctx, a, b, M, N, K, C, N, (cudaStream_t)stream, false, false);
 }

@@ -119,8 +119,10 @@ __device__ __forceinline__ void multidot_group(const double* __restrict__ V, int
 __global__ void __launch_bounds__(DOT_THREADS, 3) k_multidot(const double* __restrict__ V, int64_t ld,
                                                           int nv, const double* __restrict__ w,
                                                           int64_t n, double* __restrict__ part,
-                                                          const int* __restrict__ jcur) {
+                                                          const int* __restrict__ jcur,
+                                                          const int* __restrict__ skip) {
   __shared__ double sh[DOT_THREADS / 32][DOT_GROUP];
+  if (skip && *skip) return;
   if (jcur) nv = jcur[0] + 1;
   const int g0 = (int)blockIdx.y * DOT_GROUP;
   if (g0 >= nv) return;
@@ -143,9 +145,13 @@ __global__ void __launch_bounds__(DOT_THREADS, 3) k_multidot(const double* __res
 // out[i] = sum_b part[i * nb + b] in a fixed order (one block per vector;
 // with jcur set, blocks past vector jcur[0] return at once).
 __global__ void k_multidot_final(const double* __restrict__ part, int nb, double* __restrict__ out,
-                                 const int* __restrict__ jcur) {
+                                 const int* __restrict__ jcur, const int* __restrict__ skip) {
   __shared__ double sh[32];
   if (jcur && (int)blockIdx.x > jcur[0]) return;
+  if (skip && *skip) {  // a skipped pass contributes nothing
+    if (threadIdx.x == 0) out[blockIdx.x] = 0.0;
+    return;
+  }
   double s = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)blockIdx.x * nb + b];
   s = warp_sum(s);
@@ -168,8 +174,10 @@ __global__ void k_multidot_final(const double* __restrict__ part, int nb, double
 template <int ACC>
 __global__ void k_combine(const double* __restrict__ V, int64_t ld, int nv,
                           const double* __restrict__ c, double* __restrict__ w, int64_t n,
-                          int mode, const int* __restrict__ jcur) {
+                          int mode, const int* __restrict__ jcur,
+                          const int* __restrict__ skip = nullptr) {
   __shared__ double cs[MAXIT];
+  if (skip && *skip) return;
   if (jcur) nv = jcur[0] + 1;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = c[i];
   __syncthreads();
@@ -532,6 +540,20 @@ int combine_blocks(int64_t n) {
   return (int)b;
 }
 
+// The second Gram-Schmidt pass is needed only where the first removed most
+// of w (Daniel-Gragg-Kaufman-Stewart test, eta = 1/sqrt 2): with orthonormal
+// Krylov vectors the projected norm is ||w'||^2 = ||w||^2 - sum_i c_i^2, so
+// the pass is skipped (flag = 1) when sum_i c_i^2 <= ||w||^2 / 2 for the
+// first pass's coefficients c (i <= jcur[0]); w2 = ||w||^2 before it.
+__global__ void k_reorth_decide(const double* __restrict__ c, const double* __restrict__ w2,
+                                const int* __restrict__ jcur, int* __restrict__ flag) {
+  const int nv = jcur[0] + 1;
+  double sq = 0.0;
+  for (int i = threadIdx.x; i < nv; i += 32) sq = fma(c[i], c[i], sq);
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (threadIdx.x == 0) *flag = (isfinite(sq) && sq <= 0.5 * w2[0]) ? 1 : 0;
+}
+
 int ew_blocks(int64_t n) {
   int64_t b = cdiv(n, 256 * 4);
   if (b < 1) b = 1;
@@ -544,15 +566,16 @@ int ew_blocks(int64_t n) {
 // jcur set, the kernels take nv = jcur[0] + 1 from the device and nv only
 // bounds it (the blocks of the final reduction).
 osmps_status project(osmps_ctx* ctx, const double* V, int64_t ld, int64_t n, int nv, double* w,
-                     double* part, double* coef, cudaStream_t s, const int* jcur = nullptr) {
+                     double* part, double* coef, cudaStream_t s, const int* jcur = nullptr,
+                     const int* skip = nullptr) {
   const int nb = dot_blocks(n, ctx->sm_count);
   const dim3 dgrid(nb, (unsigned)cdiv(nv, DOT_GROUP));
-  { k_multidot<<<dgrid, DOT_THREADS, 0, s>>>(V, ld, nv, w, n, part, jcur); note_launch(); }
-  { k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef, jcur); note_launch(); }
+  { k_multidot<<<dgrid, DOT_THREADS, 0, s>>>(V, ld, nv, w, n, part, jcur, skip); note_launch(); }
+  { k_multidot_final<<<nv, 256, 0, s>>>(part, nb, coef, jcur, skip); note_launch(); }
   if (n < ((int64_t)1 << 20)) {
-    k_combine<4><<<combine_blocks(n), 128, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur);
+    k_combine<4><<<combine_blocks(n), 128, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur, skip);
   } else {
-    k_combine<1><<<ew_blocks(n), 256, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur);
+    k_combine<1><<<ew_blocks(n), 256, 0, s>>>(V, ld, nv, coef, w, n, 0, jcur, skip);
   }
   note_launch();
   OSMPS_LAUNCH_CHECK();
@@ -696,6 +719,10 @@ osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter
   // projector rows and twice out of V[0..J], its norm, the tridiagonal solve
   // with the stopping decision, and V[J+1] (and its copy in X, when there is
   // one). final_blocks bounds J + 1.
+  // Krylov vectors of 2^16 entries and more take the second Gram-Schmidt
+  // pass only when the first asks for it; smaller ones, where the launches
+  // and not the vector traffic cost, always take both.
+  const bool twice_if_needed = n >= ((int64_t)1 << 16);
   auto step = [&](cudaStream_t q, const double* x, int final_blocks,
                   cudaGraphConditionalHandle cond, int set_cond) -> osmps_status {
     OSMPS_TRY(matvec(x, w, q));
@@ -703,8 +730,16 @@ osmps_status lanczos_core(osmps_ctx* ctx, int64_t n, double* theta, int max_iter
       OSMPS_TRY(project(ctx, P, ldp, n, kp, w, part, sc + OFF_PROJ, q));
       OSMPS_TRY(project(ctx, P, ldp, n, kp, w, part, sc + OFF_PROJ + MAX_PROJ, q));
     }
-    OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C1, q, state));
-    OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C2, q, state));
+    if (twice_if_needed) {  // the second pass only where the first removed most of w
+      int* skip = reinterpret_cast<int*>(sc + OFF_MISC + 6);
+      OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 5, q));
+      OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C1, q, state));
+      { k_reorth_decide<<<1, 32, 0, q>>>(sc + OFF_C1, sc + OFF_MISC + 5, state, skip); note_launch(); }
+      OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C2, q, state, skip));
+    } else {
+      OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C1, q, state));
+      OSMPS_TRY(project(ctx, V, ld, n, final_blocks, w, part, sc + OFF_C2, q, state));
+    }
     OSMPS_TRY(vec_norm2(ctx, w, n, sc + OFF_MISC + 3, q));
     { k_tridiag<<<1, TRI_THREADS, 0, q>>>(sc, max_iter, tol, (long long)n, cond, set_cond); note_launch(); }
     OSMPS_LAUNCH_CHECK();
