@@ -200,6 +200,48 @@ osmps_status osmps_dgemm_emu(osmps_ctx* ctx, const double* A, const double* B, d
 osmps_status osmps_sytrd(osmps_ctx* ctx, double* A, int64_t n, double* d, double* e, double* tau,
                          void* stream);
 
+/* Block operations for block-sparse (U(1)) tensors. With a conserved
+ * particle number every tensor of the sweep (Sec. 3.4 with symmetries) is a
+ * set of dense blocks, one per combination of charge sectors; theta
+ * formation (Sec. 2 "Contractions"), the per-sector Gram matrices and
+ * projections of the split (Eq. AAD_ULLUD) and the environment updates are
+ * then lists of products and copies of strided views of those blocks.
+ * All pointers are device pointers; element (r, c) of a view is at
+ * base[r * row_stride + c * col_stride], strides of either sign.          */
+typedef struct {
+  const double* A; int64_t sam, sak;   /* A (M x K)                         */
+  const double* B; int64_t sbk, sbn;   /* B (K x N)                         */
+  double* C; int64_t scm, scn;         /* C (M x N)                         */
+  int64_t M, N, K;
+  double alpha, beta;                  /* C = alpha A B + beta C            */
+} osmps_gemm_desc;
+/* Run the products in list order on `stream` (float64 DMMA kernel; entries
+ * may accumulate into the same C one after another). descs: HOST array.   */
+osmps_status osmps_gemm_list(osmps_ctx* ctx, const osmps_gemm_desc* descs, int64_t n,
+                             void* stream);
+typedef struct {
+  const double* src;                   /* NULL: the destination is zeroed   */
+  double* dst;
+  int64_t rows, cols;
+  int64_t srs, scs;                    /* source element strides            */
+  int64_t drs;                         /* destination row stride            */
+  double alpha;                        /* dst[r drs + c] = alpha src[...]   */
+} osmps_copy_desc;
+/* All copies in one launch (their destinations must not overlap); descs:
+ * HOST array, read before the call returns. Synchronises `stream`.        */
+osmps_status osmps_copy_list(osmps_ctx* ctx, const osmps_copy_desc* descs, int64_t n,
+                             void* stream);
+/* The largest nev eigenpairs of the symmetric n x n device matrix G
+ * (row-major, both triangles; overwritten) in float64: eigenvalues
+ * ascending to the HOST array ev_host (nev), eigenvectors as the rows of the
+ * device array Y (nev x n). This library's tridiagonal route from n = 64 on
+ * (OSMPS_EIG_AUTO), cuSOLVER dsyevd below. Synchronises `stream`.         */
+osmps_status osmps_sym_eig_top(osmps_ctx* ctx, double* G, int64_t n, int64_t nev,
+                               double* ev_host, double* Y, void* stream);
+/* ||x||^2 of a device vector of n >= 1 doubles, to the host.               */
+osmps_status osmps_vec_norm2(osmps_ctx* ctx, const double* x, int64_t n, double* out_host,
+                             void* stream);
+
 /* Self-test of the failure path of the bounded device waits (the paper has
  * no counterpart: a robustness check of this library). Every wait in this
  * library's kernels gives up after a time limit, records the failure, frees

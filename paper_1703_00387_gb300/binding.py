@@ -64,6 +64,17 @@ class TdvpStats(_c.Structure):
                 ("max_discarded", _c.c_double), ("seconds", _c.c_double)]
 
 
+class GemmDesc(_c.Structure):
+    _fields_ = [("A", _vp), ("sam", _i64), ("sak", _i64), ("B", _vp), ("sbk", _i64), ("sbn", _i64),
+                ("C", _vp), ("scm", _i64), ("scn", _i64), ("M", _i64), ("N", _i64), ("K", _i64),
+                ("alpha", _c.c_double), ("beta", _c.c_double)]
+
+
+class CopyDesc(_c.Structure):
+    _fields_ = [("src", _vp), ("dst", _vp), ("rows", _i64), ("cols", _i64), ("srs", _i64),
+                ("scs", _i64), ("drs", _i64), ("alpha", _c.c_double)]
+
+
 class U1Desc(_c.Structure):
     _fields_ = [("n_left", _i64), ("q_left", _c.POINTER(_i64)), ("chi_left", _c.POINTER(_i64)),
                 ("n_right", _i64), ("q_right", _c.POINTER(_i64)), ("chi_right", _c.POINTER(_i64)),
@@ -89,6 +100,10 @@ _SIGS = {
     "osmps_dgemm_emu": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _vp]),
     "osmps_sytrd": (_c.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "osmps_selftest_wait_timeout": (_c.c_int, [_vp, _c.c_int, _c.c_double, _vp]),
+    "osmps_gemm_list": (_c.c_int, [_vp, _c.POINTER(GemmDesc), _i64, _vp]),
+    "osmps_copy_list": (_c.c_int, [_vp, _c.POINTER(CopyDesc), _i64, _vp]),
+    "osmps_sym_eig_top": (_c.c_int, [_vp, _vp, _i64, _i64, _dp, _vp, _vp]),
+    "osmps_vec_norm2": (_c.c_int, [_vp, _vp, _i64, _dp, _vp]),
     "osmps_env_update": (_c.c_int, [_vp, _c.c_int, _vp, _vp, _vp, _vp] + [_i64] * 5 + [_c.c_int, _vp]),
     "osmps_lanczos_ground": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp] + [_i64] * 7 +
                              [_c.c_int, _c.c_double, _c.c_int, _dp, _c.POINTER(_c.c_int), _dp, _vp]),
@@ -697,6 +712,36 @@ def osmps_selftest_wait_timeout(ctx, which, limit_us=2000.0, stream=None):
     wait in a kernel holding tensor memory; 1: a grid barrier one block never
     reaches). Raises OsmpsError(ETIMEOUT) when the wait gave up, as it should."""
     _check(lib().osmps_selftest_wait_timeout(ctx.ptr, int(which), float(limit_us), _stream(stream)))
+
+
+def osmps_gemm_list(ctx, descs, stream=None):
+    """Run a list of float64 products of strided device views (GemmDesc
+    tuples or GemmDesc structures) in order."""
+    arr = (GemmDesc * len(descs))(*[d if isinstance(d, GemmDesc) else GemmDesc(*d) for d in descs])
+    _check(lib().osmps_gemm_list(ctx.ptr, arr, len(descs), _stream(stream)))
+
+
+def osmps_copy_list(ctx, descs, stream=None):
+    """Run a list of scaled strided 2-D copies (CopyDesc tuples) in one launch."""
+    arr = (CopyDesc * len(descs))(*[d if isinstance(d, CopyDesc) else CopyDesc(*d) for d in descs])
+    _check(lib().osmps_copy_list(ctx.ptr, arr, len(descs), _stream(stream)))
+
+
+def osmps_sym_eig_top(ctx, G, nev, Y, stream=None):
+    """Largest nev eigenpairs of the symmetric device matrix G (n x n, float64,
+    overwritten): returns the eigenvalues (ascending, numpy); Y (nev x n) gets
+    the eigenvectors as rows."""
+    n = G.shape[0]
+    ev = np.zeros(int(nev))
+    _check(lib().osmps_sym_eig_top(ctx.ptr, _dev(G, "G"), n, int(nev), ev.ctypes.data_as(_dp),
+                                   _dev(Y, "Y"), _stream(stream)))
+    return ev
+
+
+def osmps_vec_norm2(ctx, x, stream=None):
+    out = _c.c_double()
+    _check(lib().osmps_vec_norm2(ctx.ptr, _dev(x, "x"), x.numel(), _c.byref(out), _stream(stream)))
+    return out.value
 
 
 def osmps_variance(ctx, mps, mpo, stream=None):

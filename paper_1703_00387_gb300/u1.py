@@ -20,20 +20,32 @@ def bond_charges(sectors_q, sectors_chi):
 def channel_charges(W_sites):
     """Charges of every MPO bond (list of arrays, L+1 of them), from the
     nonzero pattern of the site tensors W[w,t,s,w2] (q_w2 - q_w = t - s),
-    starting from charge 0 on the left boundary channel."""
+    starting from charge 0 on the left boundary channel. A channel that no
+    operator reaches from the left (a zero coupling, e.g. a field h = 0 on
+    the first site) takes its charge from the operators it feeds on the
+    right; one connected to nothing at all gets charge 0 (its environment
+    blocks are zero whatever the charge)."""
+    unset = np.iinfo(np.int64).min
     out = [np.zeros(W_sites[0].shape[0], dtype=np.int64)]
-    for W in W_sites:
-        q_in = out[-1]
-        q_out = np.full(W.shape[3], np.iinfo(np.int64).min, dtype=np.int64)
-        w, t, s, w2 = np.nonzero(W)
-        for a, b, c, e in zip(w, t, s, w2):
-            v = q_in[a] + b - c
-            if q_out[e] != np.iinfo(np.int64).min and q_out[e] != v:
+    out += [np.full(W.shape[3], unset, dtype=np.int64) for W in W_sites]
+    nz = [np.nonzero(W) for W in W_sites]
+    changed = True
+    while changed:  # propagate along nonzeros in both directions
+        changed = False
+        for k in range(len(W_sites)):
+            for a, b, c, e in zip(*nz[k]):
+                if out[k][a] != unset and out[k + 1][e] == unset:
+                    out[k + 1][e] = out[k][a] + b - c
+                    changed = True
+                elif out[k][a] == unset and out[k + 1][e] != unset:
+                    out[k][a] = out[k + 1][e] - b + c
+                    changed = True
+    for q in out:
+        q[q == unset] = 0
+    for k in range(len(W_sites)):
+        for a, b, c, e in zip(*nz[k]):
+            if out[k + 1][e] != out[k][a] + b - c:
                 raise ValueError("the MPO does not conserve the charge")
-            q_out[e] = v
-        if (q_out == np.iinfo(np.int64).min).any():
-            raise ValueError("an MPO channel carries no operator")
-        out.append(q_out)
     return out
 
 
