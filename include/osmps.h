@@ -209,16 +209,28 @@ osmps_status osmps_sytrd(osmps_ctx* ctx, double* A, int64_t n, double* d, double
  * All pointers are device pointers; element (r, c) of a view is at
  * base[r * row_stride + c * col_stride], strides of either sign.          */
 typedef struct {
-  const double* A; int64_t sam, sak;   /* A (M x K)                         */
-  const double* B; int64_t sbk, sbn;   /* B (K x N)                         */
+  const double* A; int64_t sam, sak;   /* A (M x K) of this term            */
+  const double* B; int64_t sbk, sbn;   /* B (K x N) of this term            */
+  int64_t K;                           /* >= 1                              */
+  double alpha;
+} osmps_gemm_term;
+typedef struct {
   double* C; int64_t scm, scn;         /* C (M x N)                         */
-  int64_t M, N, K;
-  double alpha, beta;                  /* C = alpha A B + beta C            */
-} osmps_gemm_desc;
-/* Run the products in list order on `stream` (float64 DMMA kernel; entries
- * may accumulate into the same C one after another). descs: HOST array.   */
-osmps_status osmps_gemm_list(osmps_ctx* ctx, const osmps_gemm_desc* descs, int64_t n,
-                             void* stream);
+  int64_t M, N;
+  double beta;
+  int64_t term_begin, term_count;      /* its terms in the term array       */
+} osmps_gemm_out;
+/* Grouped products: for every output, C = sum over its terms of
+ * alpha A B + beta C (no terms: C = beta C), all outputs in one launch of
+ * the float64 DMMA kernel, one CTA per 64 x 64 output tile running through
+ * the terms' K ranges in order (deterministic; no atomics). Outputs must
+ * not overlap one another nor any term operand of the launch; beta = 0
+ * never reads C. outs, terms: HOST arrays, read before the call returns.
+ * EINVAL for a null pointer or a term range outside the term array,
+ * ESHAPE for negative sizes, K < 1 or more than 2^31 tiles. Synchronises
+ * `stream` (the descriptor upload).                                       */
+osmps_status osmps_gemm_grouped(osmps_ctx* ctx, const osmps_gemm_out* outs, int64_t n_out,
+                                const osmps_gemm_term* terms, int64_t n_terms, void* stream);
 typedef struct {
   const double* src;                   /* NULL: the destination is zeroed   */
   double* dst;

@@ -64,10 +64,13 @@ class TdvpStats(_c.Structure):
                 ("max_discarded", _c.c_double), ("seconds", _c.c_double)]
 
 
-class GemmDesc(_c.Structure):
-    _fields_ = [("A", _vp), ("sam", _i64), ("sak", _i64), ("B", _vp), ("sbk", _i64), ("sbn", _i64),
-                ("C", _vp), ("scm", _i64), ("scn", _i64), ("M", _i64), ("N", _i64), ("K", _i64),
-                ("alpha", _c.c_double), ("beta", _c.c_double)]
+# osmps_gemm_term / osmps_gemm_out as NumPy record types (same field order and
+# 8-byte fields, so an array of records is the C array)
+GEMM_TERM_DTYPE = np.dtype([("A", np.uint64), ("sam", np.int64), ("sak", np.int64), ("B", np.uint64),
+                            ("sbk", np.int64), ("sbn", np.int64), ("K", np.int64), ("alpha", np.float64)])
+GEMM_OUT_DTYPE = np.dtype([("C", np.uint64), ("scm", np.int64), ("scn", np.int64), ("M", np.int64),
+                           ("N", np.int64), ("beta", np.float64), ("term_begin", np.int64),
+                           ("term_count", np.int64)])
 
 
 class CopyDesc(_c.Structure):
@@ -100,7 +103,7 @@ _SIGS = {
     "osmps_dgemm_emu": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _vp]),
     "osmps_sytrd": (_c.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "osmps_selftest_wait_timeout": (_c.c_int, [_vp, _c.c_int, _c.c_double, _vp]),
-    "osmps_gemm_list": (_c.c_int, [_vp, _c.POINTER(GemmDesc), _i64, _vp]),
+    "osmps_gemm_grouped": (_c.c_int, [_vp, _vp, _i64, _vp, _i64, _vp]),
     "osmps_copy_list": (_c.c_int, [_vp, _c.POINTER(CopyDesc), _i64, _vp]),
     "osmps_sym_eig_top": (_c.c_int, [_vp, _vp, _i64, _i64, _dp, _vp, _vp]),
     "osmps_vec_norm2": (_c.c_int, [_vp, _vp, _i64, _dp, _vp]),
@@ -714,11 +717,15 @@ def osmps_selftest_wait_timeout(ctx, which, limit_us=2000.0, stream=None):
     _check(lib().osmps_selftest_wait_timeout(ctx.ptr, int(which), float(limit_us), _stream(stream)))
 
 
-def osmps_gemm_list(ctx, descs, stream=None):
-    """Run a list of float64 products of strided device views (GemmDesc
-    tuples or GemmDesc structures) in order."""
-    arr = (GemmDesc * len(descs))(*[d if isinstance(d, GemmDesc) else GemmDesc(*d) for d in descs])
-    _check(lib().osmps_gemm_list(ctx.ptr, arr, len(descs), _stream(stream)))
+def osmps_gemm_grouped(ctx, outs, terms, stream=None):
+    """Grouped float64 products of strided device views in one launch: outs
+    (GEMM_OUT_DTYPE records), terms (GEMM_TERM_DTYPE records); per output
+    C = sum over its terms of alpha A B + beta C."""
+    outs = np.ascontiguousarray(outs, dtype=GEMM_OUT_DTYPE)
+    terms = np.ascontiguousarray(terms, dtype=GEMM_TERM_DTYPE)
+    _check(lib().osmps_gemm_grouped(ctx.ptr, outs.ctypes.data if len(outs) else None, len(outs),
+                                    terms.ctypes.data if len(terms) else None, len(terms),
+                                    _stream(stream)))
 
 
 def osmps_copy_list(ctx, descs, stream=None):

@@ -20,8 +20,9 @@ Storage: a tensor is the list of its allowed entries in C order of the dense
 tensor (the library's packed format). A bond is a list of sectors (charge,
 size) in ascending charge. This module is host orchestration: it builds the
 lists of block products and copies from the sector bookkeeping and hands them
-to the library (osmps_gemm_list, osmps_copy_list, osmps_sym_eig_top,
-osmps_lanczos_ground_u1); all arithmetic runs in the library's kernels.
+to the library (osmps_gemm_grouped: one launch per stage of products,
+osmps_copy_list, osmps_sym_eig_top, osmps_lanczos_ground_u1); all
+arithmetic runs in the library's kernels.
 """
 import time
 
@@ -126,18 +127,26 @@ class EnvLayout:
 # ---------------------------------------------------------------------------
 # Operation records: (buffer, element offset) pairs, resolved by an executor
 # ---------------------------------------------------------------------------
-class Gemm:
-    """C = alpha A B + beta C on strided views: A (M x K) at (bufA, offA) with
-    element strides (sam, sak), B (K x N) likewise, C (M x N) likewise."""
-    __slots__ = ("A", "sam", "sak", "B", "sbk", "sbn", "C", "scm", "scn", "M", "N", "K",
-                 "alpha", "beta")
+class Term:
+    """alpha A B for one output: A (M x K) at (buffer, offset) with element
+    strides (sam, sak), B (K x N) likewise."""
+    __slots__ = ("A", "sam", "sak", "B", "sbk", "sbn", "K", "alpha")
 
-    def __init__(self, A, sam, sak, B, sbk, sbn, C, scm, scn, M, N, K, alpha=1.0, beta=0.0):
+    def __init__(self, A, sam, sak, B, sbk, sbn, K, alpha=1.0):
         self.A, self.sam, self.sak = A, int(sam), int(sak)
         self.B, self.sbk, self.sbn = B, int(sbk), int(sbn)
+        self.K, self.alpha = int(K), float(alpha)
+
+
+class Product:
+    """C = sum over terms of alpha A B + beta C, C (M x N) at (buffer,
+    offset) with element strides (scm, scn); no terms: C = beta C."""
+    __slots__ = ("C", "scm", "scn", "M", "N", "beta", "terms")
+
+    def __init__(self, C, scm, scn, M, N, terms=(), beta=0.0):
         self.C, self.scm, self.scn = C, int(scm), int(scn)
-        self.M, self.N, self.K = int(M), int(N), int(K)
-        self.alpha, self.beta = float(alpha), float(beta)
+        self.M, self.N, self.beta = int(M), int(N), float(beta)
+        self.terms = list(terms)
 
 
 class Copy:
@@ -167,21 +176,23 @@ class DeviceExecutor:
         buf, off = ref
         return buf.data_ptr() + 8 * int(off)
 
-    def gemms(self, ops):
-        if ops:
-            B.osmps_gemm_list(self.ctx, [(self._p(g.A), g.sam, g.sak, self._p(g.B), g.sbk, g.sbn,
-                                          self._p(g.C), g.scm, g.scn, g.M, g.N, g.K, g.alpha,
-                                          g.beta) for g in ops])
+    def products(self, ops):
+        """All products of one stage in one grouped launch (outputs disjoint)."""
+        if not ops:
+            return
+        p = self._p
+        outs, terms = [], []
+        for o in ops:
+            outs.append((p(o.C), o.scm, o.scn, o.M, o.N, o.beta, len(terms), len(o.terms)))
+            terms.extend((p(t.A), t.sam, t.sak, p(t.B), t.sbk, t.sbn, t.K, t.alpha) for t in o.terms)
+        B.osmps_gemm_grouped(self.ctx, np.array(outs, dtype=B.GEMM_OUT_DTYPE),
+                             np.array(terms, dtype=B.GEMM_TERM_DTYPE))
 
     def copies(self, ops):
         if ops:
             B.osmps_copy_list(self.ctx, [(self._p(c.src) if c.src is not None else 0,
                                           self._p(c.dst), c.rows, c.cols, c.srs, c.scs, c.drs,
                                           c.alpha) for c in ops])
-
-    def zero(self, buf, n):
-        if n > 0:
-            self.copies([Copy(None, (buf, 0), 1, n, 0, 0, n)])
 
     def norm2(self, buf, n):
         return B.osmps_vec_norm2(self.ctx, buf[:n]) if n > 0 else 0.0
@@ -219,18 +230,24 @@ class DeviceExecutor:
 # Block operations of one step
 # ---------------------------------------------------------------------------
 def theta_ops(A1, lay1, A2, lay2, mid, left, theta, layt):
-    """theta = A_k A_{k+1}: one product per (left sector i, s1)."""
+    """theta = A_k A_{k+1}: one product per block (left sector i, s1) of
+    theta, a single term A_k(i, s1) A_{k+1}(middle sector q(i) + s1); blocks
+    whose middle charge the bond does not carry are zeroed."""
     ops = []
-    for i, qi in enumerate(left.q):
-        for s1 in range(lay1.col_off.shape[1]):
+    for i in range(len(left.q)):
+        for s1 in range(layt.col_off.shape[1]):
+            if layt.col_off[i, s1] < 0:
+                continue
+            out = ((theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1,
+                   left.m[i], layt.width[i, s1])
             jm = lay1.right_sector[i, s1]
-            if jm < 0 or layt.col_off[i, s1] < 0 or lay2.row_len[jm] == 0:
+            if jm < 0:
+                ops.append(Product(*out))
                 continue
             assert lay2.row_len[jm] == layt.width[i, s1]
-            ops.append(Gemm((A1, lay1.row_off[i] + lay1.col_off[i, s1]), lay1.row_len[i], 1,
-                            (A2, lay2.row_off[jm]), lay2.row_len[jm], 1,
-                            (theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1,
-                            left.m[i], lay2.row_len[jm], mid.m[jm]))
+            ops.append(Product(*out, terms=[Term((A1, lay1.row_off[i] + lay1.col_off[i, s1]),
+                                                 lay1.row_len[i], 1, (A2, lay2.row_off[jm]),
+                                                 lay2.row_len[jm], 1, mid.m[jm])]))
     return ops
 
 
@@ -273,10 +290,13 @@ def truncation(values, tr, chi_max, eps_local, rank):
 
 def env_left_ops(Lold, elo, A, lay, Lnew, eln, W, left, mid, X):
     """L_new[b', w', b] = sum A[a', t, b'] L_old[a', w, a] W[w, t, s, w'] A[a, s, b]
-    as block products: X(i2, w) = L_old(i2, w) A(i) over all s, then one
-    product per nonzero W[w, t, s, w'] and sector pair. X: scratch buffer.
-    Returns (stage-1 ops, stage-2 ops, X elements needed)."""
-    s1_ops, s2_ops, xoff, off = [], [], {}, 0
+    in two grouped stages: X(i2, w) = L_old(i2, w) A(i), all s at once (one
+    product per bra sector i2 and channel w), then one product per block
+    (j2, w') of L_new whose terms are W[w, t, s, w'] A(i2, t)^T X(i2, w)[s]
+    over every nonzero W entry and sector pair that reaches it (blocks with
+    no term are zeroed). X: scratch buffer. Returns (stage-1 products,
+    stage-2 products, X elements needed)."""
+    s1_ops, xoff, off = [], {}, 0
     d = lay.col_off.shape[1]
     for i2 in range(len(left.q)):
         for w in range(elo.ket.shape[1]):
@@ -284,10 +304,11 @@ def env_left_ops(Lold, elo, A, lay, Lnew, eln, W, left, mid, X):
             if i < 0 or lay.row_len[i] == 0:
                 continue
             xoff[(i2, w)] = off
-            s1_ops.append(Gemm((Lold, elo.row_off[i2] + elo.col_off[i2, w]), elo.row_len[i2], 1,
-                               (A, lay.row_off[i]), lay.row_len[i], 1,
-                               (X, off), lay.row_len[i], 1, left.m[i2], lay.row_len[i], left.m[i]))
+            s1_ops.append(Product((X, off), lay.row_len[i], 1, left.m[i2], lay.row_len[i],
+                                  terms=[Term((Lold, elo.row_off[i2] + elo.col_off[i2, w]), elo.row_len[i2], 1,
+                                              (A, lay.row_off[i]), lay.row_len[i], 1, left.m[i])]))
             off += int(left.m[i2] * lay.row_len[i])
+    blocks = {}
     for (i2, w), xo in xoff.items():
         i = elo.ket[i2, w]
         for s in range(d):
@@ -303,18 +324,27 @@ def env_left_ops(Lold, elo, A, lay, Lnew, eln, W, left, mid, X):
                     if val == 0.0:
                         continue
                     assert eln.ket[j2, w2] == j
-                    s2_ops.append(Gemm((A, lay.row_off[i2] + lay.col_off[i2, t]), 1, lay.row_len[i2],
-                                       (X, xo + lay.col_off[i, s]), lay.row_len[i], 1,
-                                       (Lnew, eln.row_off[j2] + eln.col_off[j2, w2]), eln.row_len[j2], 1,
-                                       mid.m[j2], mid.m[j], left.m[i2], alpha=val, beta=1.0))
+                    blocks.setdefault((j2, w2), []).append(
+                        Term((A, lay.row_off[i2] + lay.col_off[i2, t]), 1, lay.row_len[i2],
+                             (X, xo + lay.col_off[i, s]), lay.row_len[i], 1, left.m[i2], alpha=val))
+    s2_ops = []
+    for j2 in range(len(mid.q)):
+        for w2 in range(eln.ket.shape[1]):
+            j = eln.ket[j2, w2]
+            if j < 0:
+                continue
+            s2_ops.append(Product((Lnew, eln.row_off[j2] + eln.col_off[j2, w2]), eln.row_len[j2], 1,
+                                  mid.m[j2], mid.m[j], terms=blocks.get((j2, w2), ())))
     return s1_ops, s2_ops, off
 
 
 def env_right_ops(Rold, ero, A, lay, Rnew, ern, W, mid, right, Z):
     """R_new[a2, w, a] = sum A[a2, t, c2] W[w, t, s, w2] R_old[c2, w2, c] A[a, s, c]
-    as block products: Z(j, s, w2) = A(j, s) R_old(c2, w2, c)^T, then one
-    product per nonzero W[w, t, s, w2] and sector pair."""
-    s1_ops, s2_ops, zoff, off = [], [], {}, 0
+    in two grouped stages: Z(j, s, jc2, w2) = A(j, s) R_old(jc2, w2)^T, then
+    one product per block (j2, w) of R_new whose terms are
+    W[w, t, s, w2] A(j2, t) Z(j, s, jc2, w2)^T (blocks with no term are
+    zeroed)."""
+    s1_ops, zoff, off = [], {}, 0
     d = lay.col_off.shape[1]
     for j in range(len(mid.q)):
         for s in range(d):
@@ -326,10 +356,12 @@ def env_right_ops(Rold, ero, A, lay, Rnew, ern, W, mid, right, Z):
                     if ero.ket[jc2, w2] != jc:
                         continue
                     zoff[(j, s, jc2, w2)] = off
-                    s1_ops.append(Gemm((A, lay.row_off[j] + lay.col_off[j, s]), lay.row_len[j], 1,
-                                       (Rold, ero.row_off[jc2] + ero.col_off[jc2, w2]), 1, ero.row_len[jc2],
-                                       (Z, off), right.m[jc2], 1, mid.m[j], right.m[jc2], right.m[jc]))
+                    s1_ops.append(Product((Z, off), right.m[jc2], 1, mid.m[j], right.m[jc2],
+                                          terms=[Term((A, lay.row_off[j] + lay.col_off[j, s]), lay.row_len[j], 1,
+                                                      (Rold, ero.row_off[jc2] + ero.col_off[jc2, w2]), 1,
+                                                      ero.row_len[jc2], right.m[jc])]))
                     off += int(mid.m[j] * right.m[jc2])
+    blocks = {}
     for (j, s, jc2, w2), zo in zoff.items():
         for t in range(d):
             j2 = mid.find(right.q[jc2] - t)
@@ -340,10 +372,17 @@ def env_right_ops(Rold, ero, A, lay, Rnew, ern, W, mid, right, Z):
                 if val == 0.0:
                     continue
                 assert ern.ket[j2, w] == j
-                s2_ops.append(Gemm((A, lay.row_off[j2] + lay.col_off[j2, t]), lay.row_len[j2], 1,
-                                   (Z, zo), 1, right.m[jc2],
-                                   (Rnew, ern.row_off[j2] + ern.col_off[j2, w]), ern.row_len[j2], 1,
-                                   mid.m[j2], mid.m[j], right.m[jc2], alpha=val, beta=1.0))
+                blocks.setdefault((j2, w), []).append(
+                    Term((A, lay.row_off[j2] + lay.col_off[j2, t]), lay.row_len[j2], 1,
+                         (Z, zo), 1, right.m[jc2], right.m[jc2], alpha=val))
+    s2_ops = []
+    for j2 in range(len(mid.q)):
+        for w in range(ern.ket.shape[1]):
+            j = ern.ket[j2, w]
+            if j < 0:
+                continue
+            s2_ops.append(Product((Rnew, ern.row_off[j2] + ern.col_off[j2, w]), ern.row_len[j2], 1,
+                                  mid.m[j2], mid.m[j], terms=blocks.get((j2, w), ())))
     return s1_ops, s2_ops, off
 
 
@@ -369,15 +408,15 @@ def split(ex, theta, layt, left, right, d1, d2, move_right, chi_max, eps_local):
         if move_right:   # G[g, g'] = theta_g theta_g'^T
             for (i, s1, r0) in g["rows"]:
                 for (i2, s2, r2) in g["rows"]:
-                    ops.append(Gemm((theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1,
-                                    (theta, layt.row_off[i2] + layt.col_off[i2, s2]), 1, layt.row_len[i2],
-                                    (G, r0 * gdim + r2), gdim, 1, left.m[i], left.m[i2], Wq))
+                    ops.append(Product((G, r0 * gdim + r2), gdim, 1, left.m[i], left.m[i2], terms=[
+                        Term((theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1,
+                             (theta, layt.row_off[i2] + layt.col_off[i2, s2]), 1, layt.row_len[i2], Wq)]))
         else:            # G = sum_g theta_g^T theta_g
-            for k, (i, s1, r0) in enumerate(g["rows"]):
-                a = (theta, layt.row_off[i] + layt.col_off[i, s1])
-                ops.append(Gemm(a, 1, layt.row_len[i], a, layt.row_len[i], 1, (G, 0), gdim, 1,
-                                Wq, Wq, left.m[i], beta=0.0 if k == 0 else 1.0))
-        ex.gemms(ops)
+            ops.append(Product((G, 0), gdim, 1, Wq, Wq, terms=[
+                Term((theta, layt.row_off[i] + layt.col_off[i, s1]), 1, layt.row_len[i],
+                     (theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1, left.m[i])
+                for (i, s1, r0) in g["rows"]]))
+        ex.products(ops)
         ev, Y = ex.eig_top(G, gdim, nev)
         vecs[q] = (Y, gdim, nev)
         for c in range(nev):  # c-th largest of the sector: row nev - 1 - c of Y
@@ -390,9 +429,7 @@ def split(ex, theta, layt, left, right, d1, d2, move_right, chi_max, eps_local):
     mid = Bond(sorted(kq), [kq[q] for q in sorted(kq)])
     lay1, lay2 = MpsLayout(left, mid, d1), MpsLayout(mid, right, d2)
     A1, A2 = ex.empty(lay1.size), ex.empty(lay2.size)
-    ex.zero(A1, lay1.size)
-    ex.zero(A2, lay2.size)
-    gemms, copies = [], []
+    prods, copies = [], []
     for jm, q in enumerate(mid.q):
         q = int(q)
         k = kq[q]
@@ -400,27 +437,28 @@ def split(ex, theta, layt, left, right, d1, d2, move_right, chi_max, eps_local):
         Y, gdim, nev = vecs[q]
         top = (nev - 1) * gdim  # row of the largest eigenvector; next ones at -gdim
         if move_right:
-            for n_, (i, s1, r0) in enumerate(g["rows"]):
+            terms = []
+            for (i, s1, r0) in g["rows"]:
                 # A1 block (i, s1) = U_q[rows of the group, :k]
                 copies.append(Copy((Y, top + r0), (A1, lay1.row_off[i] + lay1.col_off[i, s1]),
                                    left.m[i], k, 1, -gdim, lay1.row_len[i]))
-                # A2 rows of sector q = U_q[:, :k]^T M_q, summed over the groups
-                gemms.append(Gemm((Y, top + r0), -gdim, 1,
+                terms.append(Term((Y, top + r0), -gdim, 1,
                                   (theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1,
-                                  (A2, lay2.row_off[jm]), lay2.row_len[jm], 1,
-                                  k, g["W"], left.m[i], beta=0.0 if n_ == 0 else 1.0))
+                                  left.m[i]))
+            # A2 rows of sector q = U_q[:, :k]^T M_q (a sum over the groups' rows)
+            prods.append(Product((A2, lay2.row_off[jm]), lay2.row_len[jm], 1, k, g["W"], terms=terms))
         else:
             # A2 rows of sector q = V_q[:, :k]^T
             copies.append(Copy((Y, top), (A2, lay2.row_off[jm]), k, g["W"], -gdim, 1,
                                lay2.row_len[jm]))
             for (i, s1, r0) in g["rows"]:
                 # A1 block (i, s1) = theta_g V_q[:, :k]
-                gemms.append(Gemm((theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1,
-                                  (Y, top), 1, -gdim,
-                                  (A1, lay1.row_off[i] + lay1.col_off[i, s1]), lay1.row_len[i], 1,
-                                  left.m[i], k, g["W"]))
+                prods.append(Product((A1, lay1.row_off[i] + lay1.col_off[i, s1]), lay1.row_len[i], 1,
+                                     left.m[i], k, terms=[
+                                         Term((theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1,
+                                              (Y, top), 1, -gdim, g["W"])]))
     ex.copies(copies)
-    ex.gemms(gemms)
+    ex.products(prods)
     # renormalise the non-isometric factor (the kept Schmidt values sum to 1)
     other, size = (A2, lay2.size) if move_right else (A1, lay1.size)
     nrm2 = ex.norm2(other, size)
@@ -491,14 +529,15 @@ def random_u1_mps(ex, L, d, N, chi, seed=0):
 
 
 def u1_sweep(mps, W, n_sweeps=1, chi_max=64, eps_local=0.0, precision="tf32x3",
-             lanczos_tol=1e-10, lanczos_max_iter=100):
+             lanczos_tol=1e-10, lanczos_max_iter=100, phase_timing=False):
     """Two-site sweeps on a U(1) MPS for the MPO W (list of dense site tensors
     W[w, t, s, w2] that conserve the particle number). The state is first
     brought to right-canonical form by right-to-left splits without
     truncation; then each sweep optimises the pairs (0,1) ... (L-2,L-1) and
     back. Returns a dict with the float64 energy <psi|H|psi> / <psi|psi> of
     the final state (block environments contracted through the chain), the
-    largest discarded weight, Lanczos iterations and timings."""
+    largest discarded weight, Lanczos iterations and timings (phase_timing:
+    also seconds per phase of the steps, synchronising after each phase)."""
     ex = mps.ex
     L, d = mps.L, mps.d
     qw = channel_charges(W)
@@ -509,8 +548,7 @@ def u1_sweep(mps, W, n_sweeps=1, chi_max=64, eps_local=0.0, precision="tf32x3",
         left, mid, right = mps.bonds[k], mps.bonds[k + 1], mps.bonds[k + 2]
         layt = ThetaLayout(left, right, d, d)
         th = ex.empty(layt.size)
-        ex.zero(th, layt.size)
-        ex.gemms(theta_ops(mps.A[k], mps.layout(k), mps.A[k + 1], mps.layout(k + 1), mid, left,
+        ex.products(theta_ops(mps.A[k], mps.layout(k), mps.A[k + 1], mps.layout(k + 1), mid, left,
                            th, layt))
         return th, layt
 
@@ -533,24 +571,22 @@ def u1_sweep(mps, W, n_sweeps=1, chi_max=64, eps_local=0.0, precision="tf32x3",
         left, mid = mps.bonds[k], mps.bonds[k + 1]
         elo, eln = EnvLayout(left, qw[k]), EnvLayout(mid, qw[k + 1])
         Ln = ex.empty(eln.size)
-        ex.zero(Ln, eln.size)
         s1, s2, nx = env_left_ops(Lk, elo, mps.A[k], mps.layout(k), Ln, eln, W[k], left, mid, None)
         X = ex.empty(nx)
         s1, s2, _ = env_left_ops(Lk, elo, mps.A[k], mps.layout(k), Ln, eln, W[k], left, mid, X)
-        ex.gemms(s1)
-        ex.gemms(s2)
+        ex.products(s1)
+        ex.products(s2)
         return Ln
 
     def env_right(k, Rk1):
         mid, right = mps.bonds[k], mps.bonds[k + 1]
         ero, ern = EnvLayout(right, qw[k + 1]), EnvLayout(mid, qw[k])
         Rn = ex.empty(ern.size)
-        ex.zero(Rn, ern.size)
         _, _, nz = env_right_ops(Rk1, ero, mps.A[k], mps.layout(k), Rn, ern, W[k], mid, right, None)
         Z = ex.empty(nz)
         s1, s2, _ = env_right_ops(Rk1, ero, mps.A[k], mps.layout(k), Rn, ern, W[k], mid, right, Z)
-        ex.gemms(s1)
-        ex.gemms(s2)
+        ex.products(s1)
+        ex.products(s2)
         return Rn
 
     one = lambda: ex.upload(np.ones(1))
@@ -562,23 +598,39 @@ def u1_sweep(mps, W, n_sweeps=1, chi_max=64, eps_local=0.0, precision="tf32x3",
     t_setup = time.perf_counter() - t0
 
     iters, max_disc, energy_step, steps = 0, 0.0, None, 0
+    phase = {"theta": 0.0, "lanczos": 0.0, "split": 0.0, "env": 0.0}
+
+    def mark(name, t):
+        # phase seconds (synchronising after each phase) when asked for
+        if not phase_timing:
+            return t
+        ex.sync()
+        now = time.perf_counter()
+        phase[name] += now - t
+        return now
+
     t1 = time.perf_counter()
     schedule = list(range(L - 1)) + list(range(L - 2, -1, -1))
     for _ in range(n_sweeps):
         for n_, k in enumerate(schedule):
             move_right = n_ < L - 1
+            tp = time.perf_counter()
             th, layt = form_theta(k)
+            tp = mark("theta", tp)
             e, it = ex.ground(Lenv[k], Wd[k], Wd[k + 1], Renv[k + 2], th, mps.bonds[k],
                               mps.bonds[k + 2], d, qw[k], qw[k + 2], W[k].shape[3], precision,
                               lanczos_tol, lanczos_max_iter)
+            tp = mark("lanczos", tp)
             iters += it
             energy_step = e
             disc = do_split(k, th, layt, move_right, chi_max, eps_local)
+            tp = mark("split", tp)
             max_disc = max(max_disc, disc)
             if move_right:
                 Lenv[k + 1] = env_left(k, Lenv[k])
             else:
                 Renv[k + 1] = env_right(k + 1, Renv[k + 2])
+            mark("env", tp)
             steps += 1
     ex.sync()
     t_sweep = time.perf_counter() - t1
@@ -592,4 +644,5 @@ def u1_sweep(mps, W, n_sweeps=1, chi_max=64, eps_local=0.0, precision="tf32x3",
     t_energy = time.perf_counter() - t2
     return {"energy": h / norm2, "last_step_energy": energy_step, "max_discarded": max_disc,
             "lanczos_iters": iters, "steps": steps, "max_chi": max(b.dim for b in mps.bonds),
-            "setup_seconds": t_setup, "sweep_seconds": t_sweep, "energy_seconds": t_energy}
+            "setup_seconds": t_setup, "sweep_seconds": t_sweep, "energy_seconds": t_energy,
+            "phase_seconds": phase if phase_timing else None}

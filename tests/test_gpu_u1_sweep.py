@@ -92,3 +92,58 @@ def test_truncated_sweep_keeps_chi_max_and_bounds_the_energy(ctx):
     assert res["energy"] - e0 <= 1e-3 * abs(e0)
     assert res["max_discarded"] > 0.0
     _check_state(mps, Wo, N, res)
+
+
+def test_gemm_grouped_matches_numpy(ctx):
+    """Grouped products on strided views: several terms per output (K
+    ragged across 16-wide steps), transposed and reversed (negative-stride)
+    operands, an output with no terms (zeroed), beta accumulation, and
+    outputs spanning several 64 x 64 tiles."""
+    rng = np.random.default_rng(0)
+    buf = rng.standard_normal(200_000)
+    out = np.full(60_000, np.nan)
+    out[40_000:] = rng.standard_normal(20_000)
+    dbuf, dout = torch.from_numpy(buf).cuda(), torch.from_numpy(out.copy()).cuda()
+    pb, po = dbuf.data_ptr(), dout.data_ptr()
+
+    def view(a, off, rows, cols, rs, cs):  # element (r, c) at off + r rs + c cs, any sign
+        return a[off + rs * np.arange(rows)[:, None] + cs * np.arange(cols)[None, :]]
+
+    outs, terms, expect = [], [], []
+    # out 0: 130 x 70 at 0, row stride 70; 3 terms K = 17, 1, 40
+    specs = [
+        (0, 70, 1, 130, 70, 0.0, [(100, 17, 1, 5000, 70, 1, 17, 1.5),
+                                  (9000, 1, 130, 20000, 1, 1, 1, -2.0),     # A transposed
+                                  (30000, 40, 1, 60000, 1, 40, 40, 0.25)]),  # B transposed
+        (20000, 9, 1, 9, 9, 0.0, []),                                         # no terms: zero
+        (20100, 1, 33, 33, 20, 0.0, [(120000, 50, 1, 140000, 20, 1, 50, 1.0)]),  # C transposed
+        (40000, 100, 1, 64, 100, 0.5, [(150000 + 63 * 77, -77, 1, 170000, 100, 1, 77, 1.0)]),  # A rows reversed, beta
+    ]
+    for (co, scm, scn, M, N, beta, tl) in specs:
+        outs.append((po + 8 * co, scm, scn, M, N, beta, len(terms), len(tl)))
+        ref = np.zeros((M, N))
+        for (ao, sam, sak, bo, sbk, sbn, K, alpha) in tl:
+            terms.append((pb + 8 * ao, sam, sak, pb + 8 * bo, sbk, sbn, K, alpha))
+            ref += alpha * view(buf, ao, M, K, sam, sak) @ view(buf, bo, K, N, sbk, sbn)
+        C0 = view(out, co, M, N, scm, scn)
+        expect.append((co, M, N, scm, scn, ref + (beta * C0 if beta != 0.0 else 0.0)))
+    B.osmps_gemm_grouped(ctx, np.array(outs, dtype=B.GEMM_OUT_DTYPE), np.array(terms, dtype=B.GEMM_TERM_DTYPE))
+    got = dout.cpu().numpy()
+    for (co, M, N, scm, scn, ref) in expect:
+        np.testing.assert_allclose(view(got, co, M, N, scm, scn), ref, rtol=1e-13, atol=1e-12)
+    # untouched entries stay untouched
+    assert np.isnan(got[130 * 70: 20000]).all()
+
+
+def test_gemm_grouped_rejects_bad_ranges(ctx):
+    x = torch.zeros(64, dtype=torch.float64, device="cuda")
+    p = x.data_ptr()
+    terms = np.array([(p, 8, 1, p, 8, 1, 8, 1.0)], dtype=B.GEMM_TERM_DTYPE)
+    for bad in ((p, 8, 1, 8, 8, 0.0, 0, 2), (p, 8, 1, 8, 8, 0.0, -1, 1)):
+        with pytest.raises(B.OsmpsError) as e:
+            B.osmps_gemm_grouped(ctx, np.array([bad], dtype=B.GEMM_OUT_DTYPE), terms)
+        assert e.value.status == B.EINVAL
+    zero_k = np.array([(p, 8, 1, p, 8, 1, 0, 1.0)], dtype=B.GEMM_TERM_DTYPE)
+    with pytest.raises(B.OsmpsError) as e:
+        B.osmps_gemm_grouped(ctx, np.array([(p, 8, 1, 8, 8, 0.0, 0, 1)], dtype=B.GEMM_OUT_DTYPE), zero_k)
+    assert e.value.status == B.ESHAPE

@@ -26,13 +26,13 @@ class NumpyExecutor:
         return np.lib.stride_tricks.as_strided(buf[int(off):], (rows, cols),
                                                (rs * 8, cs * 8), writeable=True)
 
-    def gemms(self, ops):
-        for g in ops:
-            A = self.view(g.A, g.M, g.K, g.sam, g.sak)
-            Bm = self.view(g.B, g.K, g.N, g.sbk, g.sbn)
-            C = self.view(g.C, g.M, g.N, g.scm, g.scn)
-            prod = g.alpha * (A @ Bm) if g.K > 0 else 0.0
-            C[...] = prod + (g.beta * C if g.beta != 0.0 else 0.0)
+    def products(self, ops):
+        for o in ops:
+            acc = np.zeros((o.M, o.N))
+            for t in o.terms:
+                acc += t.alpha * (self.view(t.A, o.M, t.K, t.sam, t.sak) @ self.view(t.B, t.K, o.N, t.sbk, t.sbn))
+            C = self.view(o.C, o.M, o.N, o.scm, o.scn)
+            C[...] = acc + (o.beta * C if o.beta != 0.0 else 0.0)
 
     def copies(self, ops):
         vals = []
@@ -40,9 +40,6 @@ class NumpyExecutor:
             vals.append(0.0 if c.src is None else c.alpha * self.view(c.src, c.rows, c.cols, c.srs, c.scs).copy())
         for c, v in zip(ops, vals):
             self.view(c.dst, c.rows, c.cols, c.drs, 1)[...] = v
-
-    def zero(self, buf, n):
-        buf[:n] = 0.0
 
     def norm2(self, buf, n):
         return float(np.dot(buf[:n], buf[:n]))
@@ -122,8 +119,7 @@ def test_theta_formation_ops():
     ex = NumpyExecutor()
     layt = us.ThetaLayout(left, right, d, d)
     th = ex.empty(layt.size)
-    ex.zero(th, layt.size)
-    ex.gemms(us.theta_ops(A1[m1].copy(), us.MpsLayout(left, mid, d), A2[m2].copy(),
+    ex.products(us.theta_ops(A1[m1].copy(), us.MpsLayout(left, mid, d), A2[m2].copy(),
                           us.MpsLayout(mid, right, d), mid, left, th, layt))
     ref = np.tensordot(A1, A2, axes=([2], [0]))
     tm = ou1.theta_mask(left.charges(), right.charges(), d, d)
@@ -176,13 +172,12 @@ def test_environment_update_ops():
     Lold = np.where(ml, rng.standard_normal(ml.shape), 0.0)
     elo, eln = us.EnvLayout(left, qw[k]), us.EnvLayout(mid, qw[k + 1])
     Ln = ex.empty(eln.size)
-    ex.zero(Ln, eln.size)
     _, _, nx = us.env_left_ops(None, elo, None, us.MpsLayout(left, mid, d), None, eln, W[k], left, mid, None)
     X = ex.empty(nx)
     s1, s2, _ = us.env_left_ops(Lold[ml].copy(), elo, A[mA].copy(), us.MpsLayout(left, mid, d), Ln, eln,
                                 W[k], left, mid, X)
-    ex.gemms(s1)
-    ex.gemms(s2)
+    ex.products(s1)
+    ex.products(s2)
     ref = od.env_left(Lold, A, W[k])
     mln = ou1.env_mask(mid.charges(), qw[k + 1], mid.charges())
     np.testing.assert_allclose(Ln[: eln.size], ref[mln], rtol=1e-12, atol=1e-12)
@@ -192,13 +187,12 @@ def test_environment_update_ops():
     Rold = np.where(mr, rng.standard_normal(mr.shape), 0.0)
     ero, ern = us.EnvLayout(mid, qw[k + 1]), us.EnvLayout(left, qw[k])
     Rn = ex.empty(ern.size)
-    ex.zero(Rn, ern.size)
     _, _, nz = us.env_right_ops(None, ero, None, us.MpsLayout(left, mid, d), None, ern, W[k], left, mid, None)
     Z = ex.empty(nz)
     s1, s2, _ = us.env_right_ops(Rold[mr].copy(), ero, A[mA].copy(), us.MpsLayout(left, mid, d), Rn, ern,
                                  W[k], left, mid, Z)
-    ex.gemms(s1)
-    ex.gemms(s2)
+    ex.products(s1)
+    ex.products(s2)
     ref = od.env_right(Rold, A, W[k])
     mrn = ou1.env_mask(left.charges(), qw[k], left.charges())
     np.testing.assert_allclose(Rn[: ern.size], ref[mrn], rtol=1e-12, atol=1e-12)
