@@ -305,6 +305,7 @@ def run_ours(args, ws, rank, local):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = B.osmps_kernel_launches() - launches0
     prof = B.osmps_profile_read(ctx, "gemm_tc")
+    prof_other = {k: B.osmps_profile_read(ctx, k) for k in ("sytrd_panel", "gemm_emu", "gemm_f64")}
     B.osmps_profile_enable(ctx, False)
     clocks = sampler.stop()
     t_max = barrier_max(elapsed, ws)
@@ -344,7 +345,8 @@ def run_ours(args, ws, rank, local):
                    "lanczos_iters": iters, "l2": "inputs larger than L2 (each step streams ~1 GB: "
                                                  "20 Krylov vectors of 33.5 MB, 42 MB environments)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+        "roofline": roofline, "step_roofline": step_roofline(prof_other, elapsed, peaks, peak_src),
+        "clocks": clocks, "gpu_launches": launches,
     }
 
     if rank == 0 and not args.quick:
@@ -361,6 +363,7 @@ def run_ours(args, ws, rank, local):
         if not args.no_batch:
             line["batch_sweeps"] = batch_leg(B, args)
         line["u1_heff"] = u1_leg(B, ctx, args)
+        line["u1_sweep"] = u1_sweep_leg(B, ctx, args)
         line["long_range_sweep"] = long_range_leg(B, ctx, args)
         line["excited_state"] = excited_leg(B, ctx, args)
         line["tdvp"] = tdvp_leg(B, ctx, args)
@@ -372,6 +375,41 @@ def run_ours(args, ws, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+# nominal float64 rate of a GB300 (CUDA cores and DMMA alike): 152 SMs x
+# 2 FMA per clock x 2.07 GHz ~ 1.26 TFLOP/s; no measured float64 peak exists
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def step_roofline(prof, elapsed, peaks, peak_src):
+    """Per-kernel rooflines over the timed steps for the kernels the library
+    times with CUDA events: the Householder panel of the split's
+    tridiagonalisation (float64 CUDA-core arithmetic, algorithmic FLOPs of
+    the panel's A22 v products and corrections), the emulated-FP64 GEMM
+    (Gram, projections and trailing updates of the split; logical float64
+    FLOPs against the bf16 tensor peak / 36 slice products) and the float64
+    DMMA GEMM. The entry with the largest share of the step is the
+    step-level bound."""
+    out = {}
+    bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    specs = {"sytrd_panel": ("k_sytrd_panel (cooperative Householder panel)", "alu", FP64_NOMINAL_TFLOPS,
+                             "nominal float64 1.25 TFLOP/s"),
+             "gemm_emu": ("k_gemm_emu (float64-accurate GEMM on bf16 tensor cores)", "tensor", bf16 / 36.0,
+                          f"{peak_src} bf16_tflops_sustained / 36 slice products"),
+             "gemm_f64": ("k_gemm_f64 / k_gemm_grouped (float64 DMMA)", "alu", FP64_NOMINAL_TFLOPS,
+                          "nominal float64 1.25 TFLOP/s")}
+    for key, (name, bound, peak, src) in specs.items():
+        p = prof[key]
+        if p["launches"] == 0 or p["ms"] <= 0:
+            continue
+        ach = p["flops"] / (p["ms"] / 1e3) / 1e12
+        out[key] = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "peak_source": src, "launches": p["launches"],
+                    "ms_total": p["ms"], "share_of_step_time": p["ms"] / 1e3 / elapsed if elapsed > 0 else None}
+    if out:
+        out["dominant"] = max((k for k in out), key=lambda k: out[k]["share_of_step_time"] or 0.0)
+    return out
 
 
 def traffic_per_launch(prof):
@@ -639,6 +677,42 @@ def u1_leg(B, ctx, args):
         op.close()
     return {"workload": "Bose-Hubbard J=1 U=4, L=64, N=64, n<=4 (d=5), w=4, chi=512 per bond "
                         "(13 sectors each), two-site H_eff.theta at sites 31,32", **out}
+
+
+def u1_sweep_leg(B, ctx, args):
+    """Config 3 end to end: two-site sweeps of the Bose-Hubbard chain
+    (J=1, U=4, L=64, N=64, n <= 4, d=5) on a particle-number-conserving MPS
+    with block-sparse tensors: U(1) Lanczos on the grouped tcgen05 H_eff,
+    per-charge Gram eigenpairs with the truncation rule applied jointly
+    across sectors, block environment updates on the grouped float64 GEMM.
+    A seeded random U(1) MPS (chi 64) is swept once at chi_max = 128 to warm
+    up; then one timed left-right-left sweep at chi_max = 512 with
+    eps_local = 0 (the bond dimension grows to the cap), and one with
+    eps_local = 1e-12 (the converged state's own bond dimension). Seconds by
+    the host clock around each sweep (the calls synchronise), energies in
+    float64."""
+    from paper_1703_00387_gb300 import hamiltonians
+    from paper_1703_00387_gb300 import u1sweep as us
+    L, nmax, N = 64, 4, 64
+    W = hamiltonians.bose_hubbard(L, 1.0, 4.0, nmax)
+    ex = us.DeviceExecutor(ctx)
+    mps = us.random_u1_mps(ex, L, nmax + 1, N, chi=64, seed=0)
+    us.u1_sweep(mps, W, n_sweeps=1, chi_max=128, eps_local=0.0, precision=args.precision,
+                lanczos_tol=1e-10, lanczos_max_iter=LANCZOS_CAP)
+    out = {"workload": "Bose-Hubbard J=1 U=4, L=64, N=64, n<=4 (d=5), w=4: one sweep at chi_max=512 "
+                       "(eps_local=0, bond dimension saturating), then one at eps_local=1e-12; "
+                       "seeded random U(1) MPS (chi 64), one warm-up sweep at chi_max=128",
+           "precision": args.precision}
+    for key, eps in (("saturating", 0.0), ("eps_1e-12", 1e-12)):
+        l0 = B.osmps_kernel_launches()
+        r = us.u1_sweep(mps, W, n_sweeps=1, chi_max=512, eps_local=eps, precision=args.precision,
+                        lanczos_tol=1e-10, lanczos_max_iter=LANCZOS_CAP)
+        out[key] = {"sweep_seconds": r["sweep_seconds"], "canonicalize_seconds": r["setup_seconds"],
+                    "steps": r["steps"], "lanczos_iters": r["lanczos_iters"], "energy_fp64": r["energy"],
+                    "max_chi": r["max_chi"], "max_discarded": r["max_discarded"],
+                    "middle_bond_sectors": len(mps.bonds[L // 2].q),
+                    "gpu_launches": B.osmps_kernel_launches() - l0}
+    return out
 
 
 def long_range_leg(B, ctx, args):

@@ -122,7 +122,8 @@ size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx);
 typedef enum {
   OSMPS_KERNEL_GEMM_TC = 0,  /* tcgen05 split-precision GEMM                   */
   OSMPS_KERNEL_GEMM_F64 = 1, /* float64 DMMA GEMM                             */
-  OSMPS_KERNEL_GEMM_EMU = 2  /* float64-accurate GEMM on bf16 tensor cores       */
+  OSMPS_KERNEL_GEMM_EMU = 2, /* float64-accurate GEMM on bf16 tensor cores      */
+  OSMPS_KERNEL_SYTRD_PANEL = 3 /* Householder panel of the tridiagonalisation    */
 } osmps_kernel;
 /* Turn recording on (1) or off (0); both clear earlier records. Syncs the device. */
 osmps_status osmps_profile_enable(osmps_ctx* ctx, int enable);

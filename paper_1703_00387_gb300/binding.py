@@ -250,7 +250,7 @@ class Context:
             pass
 
 
-KERNEL = {"gemm_tc": 0, "gemm_f64": 1, "gemm_emu": 2}
+KERNEL = {"gemm_tc": 0, "gemm_f64": 1, "gemm_emu": 2, "sytrd_panel": 3}
 
 
 def osmps_profile_enable(ctx, enable=True):

@@ -419,9 +419,19 @@ osmps_status sytrd_tc(osmps_ctx* ctx, double* A, int64_t n, double* d, double* e
     a.col = col; a.t = t; a.part = part;
     a.bar = bar; a.bar_base = base; a.err = err;
     void* args[] = {&a};
+    // algorithmic float64 work of the panel: per column j (i columns of the
+    // panel before it, m = n - j - 1 trailing rows) the product A22 v
+    // (2 m^2) and the corrections V (W^T v) + W (V^T v) (8 m i)
+    double pf = 0.0;
+    for (int i = 0; i < nbp; ++i) {
+      const double mm = (double)(n - (k0 + i) - 1);
+      pf += 2.0 * mm * mm + 8.0 * mm * i;
+    }
+    const int ph = prof_begin(s);
     OSMPS_CUDA(cudaLaunchCooperativeKernel((void*)k_sytrd_panel, dim3(G), dim3(ST_THREADS), args,
                                            smem, s));
     note_launch();
+    prof_end(ph, s, OSMPS_KERNEL_SYTRD_PANEL, pf, 0.0);
     base += 2u * (unsigned)nbp * (unsigned)G;
     const int64_t k = k0 + nbp, m = n - k;
     if (m <= 0) break;
