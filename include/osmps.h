@@ -113,6 +113,25 @@ osmps_status osmps_ctx_set_eig_solver(osmps_ctx* ctx, int solver);
  * A context serves one host thread at a time. EINVAL for another value.     */
 typedef enum { OSMPS_LANCZOS_AUTO = 0, OSMPS_LANCZOS_HOST = 1, OSMPS_LANCZOS_GRAPH = 2 } osmps_lanczos_mode;
 osmps_status osmps_ctx_set_lanczos_mode(osmps_ctx* ctx, int mode);
+/* Identity environment channels in the split-precision H_eff.theta (Sec. 3.2:
+ * the identity corners of a lower-triangular MPO make one channel of a
+ * left-canonical L, and one of a right-canonical R, the unit matrix). When
+ * L's last (else first) channel and R's first (else last) channel equal the
+ * unit matrix to within 1e-3 per entry (built by split-precision updates
+ * from canonical tensors, it carries a few 1e-6 of rounding per site of the
+ * chain; other channels are O(1) away), both GEMM stages leave them out
+ * (theta itself feeds the W-steps; the W-steps' output for R's channel is
+ * added in the last GEMM's epilogue): (wl - 1)/wl and (wr - 1)/wr of the
+ * tensor-core work. The test reads two channels of L and R once per
+ * prepared operator and synchronises the stream.
+ *   OSMPS_IDENTITY_OFF    never;
+ *   OSMPS_IDENTITY_SOLVER operators applied many times: Lanczos, TDVP and
+ *                         excited-state solves, sweeps (default);
+ *   OSMPS_IDENTITY_ALWAYS also every osmps_heff_apply.
+ * Only for the MPO shapes with the fused W-step (d = 2; w in {1, 3, 5}).
+ * EINVAL for another value.                                                */
+typedef enum { OSMPS_IDENTITY_OFF = 0, OSMPS_IDENTITY_SOLVER = 1, OSMPS_IDENTITY_ALWAYS = 2 } osmps_identity_mode;
+osmps_status osmps_ctx_set_identity_skip(osmps_ctx* ctx, int mode);
 /* Bytes of device memory currently held by the context's workspace.         */
 size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx);
 

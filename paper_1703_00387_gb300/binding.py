@@ -95,6 +95,7 @@ _SIGS = {
     "osmps_ctx_workspace_bytes": (_c.c_size_t, [_vp]),
     "osmps_ctx_set_eig_solver": (_c.c_int, [_vp, _c.c_int]),
     "osmps_ctx_set_lanczos_mode": (_c.c_int, [_vp, _c.c_int]),
+    "osmps_ctx_set_identity_skip": (_c.c_int, [_vp, _c.c_int]),
     "osmps_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "osmps_profile_read": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_i64), _dp, _dp, _dp]),
     "osmps_kernel_launches": (_i64, []),
@@ -234,6 +235,12 @@ class Context:
         whose while-node repeats the recorded step on the device)."""
         code = {"auto": 0, "host": 1, "graph": 2}[mode] if isinstance(mode, str) else int(mode)
         _check(lib().osmps_ctx_set_lanczos_mode(self.ptr, code))
+
+    def set_identity_skip(self, mode):
+        """'off', 'solver' (default) or 'always': when the split-precision
+        H_eff.theta leaves unit-matrix environment channels out of its GEMMs."""
+        code = {"off": 0, "solver": 1, "always": 2}[mode] if isinstance(mode, str) else int(mode)
+        _check(lib().osmps_ctx_set_identity_skip(self.ptr, code))
 
     def workspace_bytes(self):
         return int(lib().osmps_ctx_workspace_bytes(self.ptr))

@@ -112,6 +112,7 @@ enum Slot {
   SLOT_CX_L,
   SLOT_CX_R,
   SLOT_CX_THETA,
+  SLOT_HEFF_IDDEV,
   SLOT_COUNT
 };
 
@@ -144,6 +145,10 @@ struct osmps_ctx {
   bool heff_ready = false;
   int heff_prec = -1;
   int64_t heff_dims[7] = {0, 0, 0, 0, 0, 0, 0};
+  // identity environment channels of the prepared operator (-1: none), and
+  // whether heff_prepare looks for them (split precisions only)
+  int heff_skip_l = -1, heff_skip_r = -1;
+  int identity_skip = OSMPS_IDENTITY_SOLVER;
   // eigensolver of the split: OSMPS_EIG_AUTO / OSMPS_EIG_CUSOLVER / OSMPS_EIG_TRIDIAG
   int eig_solver = 0;
   // Lanczos iteration driver: OSMPS_LANCZOS_AUTO / OSMPS_LANCZOS_HOST / OSMPS_LANCZOS_GRAPH
@@ -237,6 +242,7 @@ struct GemmTc {
   void* C = nullptr;
   int64_t ldc = 0;
   int out = TC_OUT_F32;
+  const float* addend = nullptr;  // TC_OUT_F64 only: C = A B^T + addend (same ldc)
 };
 osmps_status gemm_tc(osmps_ctx* ctx, const GemmTc& g, cudaStream_t stream);
 inline size_t tc_elem_bytes(int kind) { return kind == TC_BF16 ? 2 : 4; }
@@ -319,10 +325,26 @@ osmps_status fiber_contract_f32_split(const Fiber& f, const double* Mat, const f
 // Both W-steps of H_eff.theta fused (T1 -> split T3) for the d = 2 MPO
 // shapes it is specialised for; *done = false means the caller must fall back
 // to the two fiber contractions.
+// Identity environment channels: with skip_l >= 0, T1 holds the wl - 1 other
+// channels and channel skip_l is theta (L[:, skip_l, :] = 1); with
+// skip_r >= 0, the split operand holds the wr - 1 other output channels and
+// channel skip_r (R[:, skip_r, :] = 1) goes as float32 to yid (rows
+// (a2, t1, t2), chi_r columns) for the stage-4 epilogue to add.
+struct WStepIdentity {
+  const double* theta = nullptr;
+  int skip_l = -1, skip_r = -1;
+  float* yid = nullptr;
+};
+bool fused_wsteps_supported(int64_t d1, int64_t d2, int64_t wl, int64_t wm, int64_t wr);
 osmps_status fused_wsteps_f32_split(const float* T1, const double* Mat1, const double* Mat2,
                                     void* dst, int kind, int64_t chi_l, int64_t d1, int64_t d2,
                                     int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int64_t Kp,
-                                    cudaStream_t s, bool* done);
+                                    const WStepIdentity& id, cudaStream_t s, bool* done);
+// Largest |E[a, w, b] - delta_ab| over (a, b) for the channels w = 0 and
+// w = w_count - 1 of an environment E (chi x w_count x chi): two doubles to
+// dev_out (device), for the identity-channel test of heff_prepare.
+osmps_status identity_channel_deviation(const double* E, int64_t chi, int64_t w_count,
+                                        double* dev_out, cudaStream_t s);
 osmps_status zero_pad_columns(void* dst, int kind, int64_t rows, int64_t Kcols, int64_t Kp,
                               cudaStream_t stream);
 
@@ -353,7 +375,7 @@ osmps_status heff_apply_impl(osmps_ctx* ctx, const double* L, const double* W1, 
                              int64_t wr, int precision, cudaStream_t stream, bool prepared);
 osmps_status heff_prepare(osmps_ctx* ctx, const double* L, const double* W1, const double* W2,
                           const double* R, int64_t chi_l, int64_t d1, int64_t d2, int64_t chi_r,
-                          int64_t wl, int64_t wm, int64_t wr, int precision, cudaStream_t stream);
+                          int64_t wl, int64_t wm, int64_t wr, int precision, cudaStream_t stream, bool find_identity = true);
 osmps_status env_update_impl(osmps_ctx* ctx, int side, const double* env_in, const double* A,
                              const double* W, double* env_out, int64_t chi_l, int64_t d,
                              int64_t chi_r, int64_t w_in, int64_t w_out, int precision,

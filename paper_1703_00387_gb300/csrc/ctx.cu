@@ -390,6 +390,15 @@ extern "C" osmps_status osmps_ctx_set_eig_solver(osmps_ctx* ctx, int solver) {
   return OSMPS_OK;
 }
 
+extern "C" osmps_status osmps_ctx_set_identity_skip(osmps_ctx* ctx, int mode) {
+  osmps::clear_error();
+  if (!ctx) return osmps::set_error(OSMPS_EINVAL, "osmps_ctx_set_identity_skip: null context");
+  if (mode < OSMPS_IDENTITY_OFF || mode > OSMPS_IDENTITY_ALWAYS)
+    return osmps::set_error(OSMPS_EINVAL, "osmps_ctx_set_identity_skip: mode %d", mode);
+  ctx->identity_skip = mode;
+  return OSMPS_OK;
+}
+
 extern "C" osmps_status osmps_ctx_set_lanczos_mode(osmps_ctx* ctx, int mode) {
   osmps::clear_error();
   if (!ctx) return osmps::set_error(OSMPS_EINVAL, "osmps_ctx_set_lanczos_mode: null context");

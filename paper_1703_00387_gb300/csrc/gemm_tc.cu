@@ -61,7 +61,8 @@ constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + STG_BY
 template <int OUT>
 __device__ __forceinline__ void store_tile_rows(void* C, int64_t row0, int64_t col0, int64_t M,
                                                 int64_t N, int64_t ldc, const float (&acc)[EPI_COLS],
-                                                float* __restrict__ stg, int lane) {
+                                                float* __restrict__ stg, int lane,
+                                                const float* __restrict__ addend) {
 #pragma unroll
   for (int pass = 0; pass < EPI_COLS / STG_COLS; ++pass) {
 #pragma unroll
@@ -83,7 +84,8 @@ __device__ __forceinline__ void store_tile_rows(void* C, int64_t row0, int64_t c
         if (OUT == TC_OUT_F32)
           reinterpret_cast<float*>(C)[row * ldc + col] = val;
         else
-          reinterpret_cast<double*>(C)[row * ldc + col] = (double)val;
+          reinterpret_cast<double*>(C)[row * ldc + col] =
+              addend ? (double)val + (double)addend[row * ldc + col] : (double)val;
       }
     }
     __syncwarp();  // the next pass overwrites the staging block
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               void* __restrict__ C, int64_t M, int64_t N, int64_t ldc, int nkb, int kelem,
               int Kp, int tiles_n, int n_tiles, int* __restrict__ err,
-              const GroupProblem* __restrict__ probs, int n_prob) {
+              const GroupProblem* __restrict__ probs, int n_prob, const float* __restrict__ addend) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const TileJob job = tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob);
       float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * 32 * STG_COLS;
       store_tile_rows<OUT>(job.C, job.row0 + q * 32, job.col0 + part * EPI_COLS, job.M, job.N,
-                           job.ldc, acc, stg, lane);
+                           job.ldc, acc, stg, lane, addend);
     }
     if (!ok) atomicOr(err, 1);
   }
@@ -350,7 +352,8 @@ osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g,
   const int ph = prof_begin(stream);
   { k_gemm_tc<KIND, OUT><<<grid, THREADS, SMEM_BYTES, stream>>>(a, b, g.C, g.M, g.N, g.ldc, nkb,
                                                              kelem, (int)g.Kp, tiles_n, n_tiles,
-                                                             err, nullptr, 0); note_launch(); }
+                                                             err, nullptr, 0,
+                                                             OUT == TC_OUT_F64 ? g.addend : nullptr); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   const double logical = 2.0 * (double)g.M * (double)g.N * (double)(g.K > 0 ? g.K : g.Kp);
   prof_end(ph, stream, OSMPS_KERNEL_GEMM_TC, logical, 3.0 * logical);
@@ -388,7 +391,7 @@ osmps_status gemm_tc_grouped(osmps_ctx* ctx, const GemmTcGrouped& g, cudaStream_
     OSMPS_CUDA(cfg_);                                                                               \
     k_gemm_tc<K, O><<<grid, THREADS, SMEM_BYTES, stream>>>(ma, mb, g.C, 0, 0, 0, 0, kelem,          \
                                                            (int)g.Kpl, 1, (int)g.n_tiles, err,      \
-                                                           g.probs, g.n_prob);                      \
+                                                           g.probs, g.n_prob, nullptr);             \
     note_launch();                                                                                  \
   }
   if (g.kind == TC_BF16) {

@@ -55,6 +55,26 @@ __device__ __forceinline__ void split_store_f32(void* dst, int64_t off_hi, int64
   }
 }
 
+// Two consecutive values (off_hi even, so the pair is 4- or 8-byte aligned).
+template <int KIND>
+__device__ __forceinline__ void split_store2_f32(void* dst, int64_t off_hi, int64_t Kp, float a, float b) {
+  if (KIND == TC_BF16) {
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+    const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+    __nv_bfloat162 h2, l2;
+    h2.x = ha; h2.y = hb;
+    l2.x = la; l2.y = lb;
+    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(dst) + off_hi) = h2;
+    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(dst) + off_hi + Kp) = l2;
+  } else {
+    const uint32_t ha = to_tf32(a), hb = to_tf32(b);
+    const uint32_t la = to_tf32(a - __uint_as_float(ha)), lb = to_tf32(b - __uint_as_float(hb));
+    *reinterpret_cast<uint2*>(reinterpret_cast<uint32_t*>(dst) + off_hi) = make_uint2(ha, hb);
+    *reinterpret_cast<uint2*>(reinterpret_cast<uint32_t*>(dst) + off_hi + Kp) = make_uint2(la, lb);
+  }
+}
+
 __device__ __forceinline__ double load_src(const void* src, bool f32, int64_t off) {
   return f32 ? (double)reinterpret_cast<const float*>(src)[off]
              : reinterpret_cast<const double*>(src)[off];
@@ -225,76 +245,174 @@ __global__ void k_w_reorder(const double* __restrict__ W, int64_t dw, int64_t d,
 // (a2, c) the wl*d*d values T1[a2, w, s1, s2, c] are contracted with W1 and
 // then W2 in registers and written straight into the split operand
 // T3[(a2, t1, t2), (w2, c)]; the intermediate T2 never touches memory.
-template <int D, int WL, int WM, int WR, int KIND>
-__global__ void __launch_bounds__(256) k_fused_wsteps(const float* __restrict__ T1,
-                                                      const double* __restrict__ Mat1,
-                                                      const double* __restrict__ Mat2,
-                                                      void* __restrict__ dst, int64_t chi_l,
-                                                      int64_t chi_r, int64_t Kp) {
+// Identity environment channels (skip_l, skip_r >= 0): L[:, skip_l, :] = 1,
+// so T1's channel skip_l is theta itself and the stage-1 GEMM leaves it out
+// (T1 holds the other WL - 1 channels in order); R[:, skip_r, :] = 1, so
+// output channel skip_r needs no stage-4 GEMM: it goes as float32 to yid
+// (row (a2, t1, t2), column c2), which the stage-4 epilogue adds, and the
+// split operand holds the other WR - 1 channels in order.
+template <int D, int WL, int WM, int WR, int KIND, int V>
+__global__ void __launch_bounds__(256, 2) k_fused_wsteps(const float* __restrict__ T1,
+                                                         const double* __restrict__ Mat1,
+                                                         const double* __restrict__ Mat2,
+                                                         void* __restrict__ dst, int64_t chi_l,
+                                                         int64_t chi_r, int64_t Kp,
+                                                         const double* __restrict__ theta,
+                                                         int skip_l, int skip_r,
+                                                         float* __restrict__ yid) {
   constexpr int P1 = WL * D, Q1 = D * WM, P2 = WM * D, Q2 = D * WR;
-  __shared__ float m1[P1 * Q1], m2[P2 * Q2];
-  for (int i = threadIdx.x; i < P1 * Q1; i += blockDim.x) m1[i] = (float)Mat1[i];
-  for (int i = threadIdx.x; i < P2 * Q2; i += blockDim.x) m2[i] = (float)Mat2[i];
+  static_assert(P1 <= 32 && P2 <= 32, "input masks are 32-bit");
+  __shared__ float sm1[P1 * Q1], sm2[P2 * Q2];
+  __shared__ unsigned nz1[Q1], nz2[Q2];  // per output: which inputs have a nonzero W entry
+  for (int i = threadIdx.x; i < P1 * Q1; i += blockDim.x) sm1[i] = (float)Mat1[i];
+  for (int i = threadIdx.x; i < P2 * Q2; i += blockDim.x) sm2[i] = (float)Mat2[i];
+  if (threadIdx.x < Q1) nz1[threadIdx.x] = 0u;
+  if (threadIdx.x < Q2) nz2[threadIdx.x] = 0u;
   __syncthreads();
-  const int64_t total = chi_l * chi_r;
-  const int64_t Kcols = (int64_t)WR * chi_r;
+  for (int i = threadIdx.x; i < P1 * Q1; i += blockDim.x)
+    if (sm1[i] != 0.0f) atomicOr(&nz1[i % Q1], 1u << (i / Q1));
+  for (int i = threadIdx.x; i < P2 * Q2; i += blockDim.x)
+    if (sm2[i] != 0.0f) atomicOr(&nz2[i % Q2], 1u << (i / Q2));
+  __syncthreads();
+  // MPO tensors are mostly zeros (an identity in two corners and a few local
+  // operators): every multiply-add is guarded by the output's nonzero mask,
+  // a branch that is uniform over the grid, and the W entry is read from
+  // shared memory only where it is nonzero (kept in registers the ~200
+  // entries would leave one block per SM, too few loads in flight for HBM)
+  const volatile float* m1 = sm1;
+  const volatile float* m2 = sm2;
+  // V consecutive fibers c per thread (V = 2: 8-byte loads, paired stores;
+  // chi_r even)
+  const int64_t cv = chi_r / V;
+  const int64_t total = chi_l * cv;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t a2 = e / chi_r, c = e - a2 * chi_r;
-    const float* src = T1 + a2 * (WL * D * D) * chi_r + c;
-    float x[WL][D][D];
+    const int64_t a2 = e / cv, c = (e - a2 * cv) * V;
+    const int wlt = skip_l >= 0 ? WL - 1 : WL;  // channels held in T1
+    const float* src = T1 + a2 * (wlt * D * D) * chi_r + c;
+    float x[WL][D][D][V];
 #pragma unroll
     for (int w = 0; w < WL; ++w)
 #pragma unroll
       for (int s1 = 0; s1 < D; ++s1)
 #pragma unroll
-        for (int s2 = 0; s2 < D; ++s2) x[w][s1][s2] = src[((w * D + s1) * D + s2) * chi_r];
-    float mid[D][WM][D];  // T2[t1, w1, s2]
-#pragma unroll
-    for (int t1 = 0; t1 < D; ++t1)
-#pragma unroll
-      for (int w1 = 0; w1 < WM; ++w1)
-#pragma unroll
         for (int s2 = 0; s2 < D; ++s2) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int w = 0; w < WL; ++w)
-#pragma unroll
-            for (int s1 = 0; s1 < D; ++s1)
-              acc = fmaf(m1[(w * D + s1) * Q1 + t1 * WM + w1], x[w][s1][s2], acc);
-          mid[t1][w1][s2] = acc;
+          if (w == skip_l) {  // uniform branch: the identity channel is theta
+            const double* q = theta + ((a2 * D + s1) * D + s2) * chi_r + c;
+            if (V == 2) {
+              const double2 f = *reinterpret_cast<const double2*>(q);
+              x[w][s1][s2][0] = (float)f.x;
+              x[w][s1][s2][V - 1] = (float)f.y;
+            } else {
+              x[w][s1][s2][0] = (float)q[0];
+            }
+            continue;
+          }
+          const int wt = (skip_l >= 0 && w > skip_l) ? w - 1 : w;
+          const float* p = src + ((wt * D + s1) * D + s2) * chi_r;
+          if (V == 2) {
+            const float2 f = *reinterpret_cast<const float2*>(p);
+            x[w][s1][s2][0] = f.x;
+            x[w][s1][s2][V - 1] = f.y;
+          } else {
+            x[w][s1][s2][0] = p[0];
+          }
         }
+    float mid[D][WM][D][V];  // T2[t1, w1, s2]
 #pragma unroll
     for (int t1 = 0; t1 < D; ++t1)
 #pragma unroll
-      for (int t2 = 0; t2 < D; ++t2) {
-        const int64_t row = (a2 * D + t1) * D + t2;
+      for (int w1 = 0; w1 < WM; ++w1) {
+        const unsigned mask = nz1[t1 * WM + w1];
+        float acc[D][V];
 #pragma unroll
-        for (int w2 = 0; w2 < WR; ++w2) {
-          float acc = 0.0f;
+        for (int s2 = 0; s2 < D; ++s2)
 #pragma unroll
-          for (int w1 = 0; w1 < WM; ++w1)
+          for (int v = 0; v < V; ++v) acc[s2][v] = 0.0f;
 #pragma unroll
-            for (int s2 = 0; s2 < D; ++s2)
-              acc = fmaf(m2[(w1 * D + s2) * Q2 + t2 * WR + w2], mid[t1][w1][s2], acc);
-          split_store_f32<KIND>(dst, row * 2 * Kp + (int64_t)w2 * chi_r + c, Kp, acc);
+        for (int w = 0; w < WL; ++w)
+#pragma unroll
+          for (int s1 = 0; s1 < D; ++s1)
+            if (mask & (1u << (w * D + s1))) {
+              const float m = m1[(w * D + s1) * Q1 + t1 * WM + w1];
+#pragma unroll
+              for (int s2 = 0; s2 < D; ++s2)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[s2][v] = fmaf(m, x[w][s1][s2][v], acc[s2][v]);
+            }
+#pragma unroll
+        for (int s2 = 0; s2 < D; ++s2)
+#pragma unroll
+          for (int v = 0; v < V; ++v) mid[t1][w1][s2][v] = acc[s2][v];
+      }
+#pragma unroll
+    for (int t2 = 0; t2 < D; ++t2)
+#pragma unroll
+      for (int w2 = 0; w2 < WR; ++w2) {
+        const unsigned mask = nz2[t2 * WR + w2];
+        float acc[D][V];
+#pragma unroll
+        for (int t1 = 0; t1 < D; ++t1)
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[t1][v] = 0.0f;
+#pragma unroll
+        for (int w1 = 0; w1 < WM; ++w1)
+#pragma unroll
+          for (int s2 = 0; s2 < D; ++s2)
+            if (mask & (1u << (w1 * D + s2))) {
+              const float m = m2[(w1 * D + s2) * Q2 + t2 * WR + w2];
+#pragma unroll
+              for (int t1 = 0; t1 < D; ++t1)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[t1][v] = fmaf(m, mid[t1][w1][s2][v], acc[t1][v]);
+            }
+#pragma unroll
+        for (int t1 = 0; t1 < D; ++t1) {
+          const int64_t row = (a2 * D + t1) * D + t2;
+          if (w2 == skip_r) {
+            float* q = yid + row * chi_r + c;
+            if (V == 2) *reinterpret_cast<float2*>(q) = make_float2(acc[t1][0], acc[t1][V - 1]);
+            else q[0] = acc[t1][0];
+            continue;
+          }
+          const int w2t = (skip_r >= 0 && w2 > skip_r) ? w2 - 1 : w2;
+          const int64_t off = row * 2 * Kp + (int64_t)w2t * chi_r + c;
+          if (V == 2) split_store2_f32<KIND>(dst, off, Kp, acc[t1][0], acc[t1][V - 1]);
+          else split_store_f32<KIND>(dst, off, Kp, acc[t1][0]);
         }
       }
   }
-  (void)Kcols;
 }
 
 template <int D, int WL, int WM, int WR>
 bool try_fused(int64_t d, int64_t wl, int64_t wm, int64_t wr, int kind, const float* T1,
                const double* m1, const double* m2, void* dst, int64_t chi_l, int64_t chi_r,
-               int64_t Kp, cudaStream_t s) {
+               int64_t Kp, const WStepIdentity& id, cudaStream_t s, bool launch) {
   if (d != D || wl != WL || wm != WM || wr != WR) return false;
-  const int blocks = grid_for(chi_l * chi_r, 256);
+  if (!launch) return true;  // shape query only
+  const double* th = id.theta;
+  const int sl = id.skip_l, sr = id.skip_r;
+  float* yid = id.yid;
+  // two resident blocks per SM, each striding over many fibers (the
+  // per-block set-up of the W tables is then paid a few hundred times only)
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 152;
+  // pairs of fibers: 8-byte loads of T1, 16-byte loads of theta (identity
+  // channel) and paired stores, so chi_r even and theta 16-byte aligned
+  const bool pair = chi_r % 2 == 0 && (sl < 0 || (reinterpret_cast<uintptr_t>(th) & 15) == 0);
+  const int blocks = (int)std::min<int64_t>(grid_for(chi_l * (pair ? chi_r / 2 : chi_r), 256), 2 * (int64_t)sms);
+#define OSMPS_FUSED(K, V) \
+  k_fused_wsteps<D, WL, WM, WR, K, V><<<blocks, 256, 0, s>>>(T1, m1, m2, dst, chi_l, chi_r, Kp, th, sl, sr, yid)
   if (kind == TC_BF16) {
-    k_fused_wsteps<D, WL, WM, WR, TC_BF16><<<blocks, 256, 0, s>>>(T1, m1, m2, dst, chi_l, chi_r, Kp);
+    if (pair) OSMPS_FUSED(TC_BF16, 2);
+    else OSMPS_FUSED(TC_BF16, 1);
   } else {
-    k_fused_wsteps<D, WL, WM, WR, TC_TF32><<<blocks, 256, 0, s>>>(T1, m1, m2, dst, chi_l, chi_r, Kp);
+    if (pair) OSMPS_FUSED(TC_TF32, 2);
+    else OSMPS_FUSED(TC_TF32, 1);
   }
+#undef OSMPS_FUSED
   note_launch();
   return true;
 }
@@ -336,20 +454,64 @@ osmps_status fiber_contract_f32_split(const Fiber& f, const double* Mat, const f
   return fiber_dispatch<float, 2>(f, Mat, in, nullptr, dst, Kcols, Kp, s);
 }
 
+// max over (a, b) of |E[a, w, b] - delta_ab| for w = 0 (blockIdx.y = 0) and
+// w = w_count - 1 (blockIdx.y = 1), as the bit patterns of non-negative
+// doubles (ordered like the values) combined by atomicMax
+__global__ void k_identity_deviation(const double* __restrict__ E, int64_t chi, int64_t w_count,
+                                     unsigned long long* __restrict__ out) {
+  const int64_t w = blockIdx.y == 0 ? 0 : w_count - 1;
+  const int64_t total = chi * chi;
+  double m = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / chi, b = e - a * chi;
+    const double v = E[(a * w_count + w) * chi + b] - (a == b ? 1.0 : 0.0);
+    const double av = fabs(v);
+    m = (av > m || av != av) ? (av != av ? INFINITY : av) : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&out[blockIdx.y], (unsigned long long)__double_as_longlong(m));
+}
+
+static bool fused_dispatch(int64_t d1, int64_t d2, int64_t wl, int64_t wm, int64_t wr, int kind,
+                           const float* T1, const double* Mat1, const double* Mat2, void* dst,
+                           int64_t chi_l, int64_t chi_r, int64_t Kp, const WStepIdentity& id,
+                           cudaStream_t s, bool launch) {
+  if (d1 != d2) return false;
+  const int64_t d = d1;
+#define OSMPS_TRY_FUSED(a, b, c, e) \
+  try_fused<a, b, c, e>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, id, s, launch)
+  return OSMPS_TRY_FUSED(2, 5, 5, 5) || OSMPS_TRY_FUSED(2, 1, 5, 5) || OSMPS_TRY_FUSED(2, 5, 5, 1) ||
+         OSMPS_TRY_FUSED(2, 3, 3, 3) || OSMPS_TRY_FUSED(2, 1, 3, 3) || OSMPS_TRY_FUSED(2, 3, 3, 1);
+#undef OSMPS_TRY_FUSED
+}
+
+osmps_status identity_channel_deviation(const double* E, int64_t chi, int64_t w_count,
+                                        double* dev_out, cudaStream_t s) {
+  OSMPS_CUDA(cudaMemsetAsync(dev_out, 0, 2 * sizeof(double), s));
+  if (chi <= 0 || w_count <= 0) return OSMPS_OK;
+  const int bx = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(chi * chi, 256 * 8), 1024));
+  k_identity_deviation<<<dim3(bx, 2), 256, 0, s>>>(E, chi, w_count,
+                                                  reinterpret_cast<unsigned long long*>(dev_out));
+  note_launch();
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
+
+bool fused_wsteps_supported(int64_t d1, int64_t d2, int64_t wl, int64_t wm, int64_t wr) {
+  return fused_dispatch(d1, d2, wl, wm, wr, TC_BF16, nullptr, nullptr, nullptr, nullptr, 0, 0, 0,
+                        WStepIdentity{}, nullptr, false);
+}
+
 osmps_status fused_wsteps_f32_split(const float* T1, const double* Mat1, const double* Mat2,
                                     void* dst, int kind, int64_t chi_l, int64_t d1, int64_t d2,
                                     int64_t chi_r, int64_t wl, int64_t wm, int64_t wr, int64_t Kp,
-                                    cudaStream_t s, bool* done) {
+                                    const WStepIdentity& id, cudaStream_t s, bool* done) {
   *done = false;
-  if (d1 != d2) return OSMPS_OK;
-  const int64_t d = d1;
-  bool ok = try_fused<2, 5, 5, 5>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
-            try_fused<2, 1, 5, 5>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
-            try_fused<2, 5, 5, 1>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
-            try_fused<2, 3, 3, 3>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
-            try_fused<2, 1, 3, 3>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s) ||
-            try_fused<2, 3, 3, 1>(d, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, s);
-  if (!ok) return OSMPS_OK;
+  if ((id.skip_l >= 0 && !id.theta) || (id.skip_r >= 0 && !id.yid))
+    return set_error(OSMPS_EINVAL, "fused W-steps: identity channel without its buffer");
+  if (!fused_dispatch(d1, d2, wl, wm, wr, kind, T1, Mat1, Mat2, dst, chi_l, chi_r, Kp, id, s, true))
+    return OSMPS_OK;
   OSMPS_LAUNCH_CHECK();
   *done = true;
   return OSMPS_OK;
