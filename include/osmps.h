@@ -287,6 +287,12 @@ osmps_status osmps_vec_norm2(osmps_ctx* ctx, const double* x, int64_t n, double*
  * Returns OSMPS_ETIMEOUT when the wait gave up (the expected outcome), OK
  * otherwise. Synchronises `stream`.                                          */
 osmps_status osmps_selftest_wait_timeout(osmps_ctx* ctx, int which, double limit_us, void* stream);
+/* Test support: y32[i] = (float)x64[i] (round to nearest, ties to even) and
+ * y64[i] = (double)x32[i] computed with the integer-field conversions the
+ * kernels use where the float64 pipe would be the bottleneck (device arrays
+ * of n elements). Results must equal the IEEE conversions bit for bit.    */
+osmps_status osmps_selftest_convert(osmps_ctx* ctx, const double* x64, float* y32,
+                                    const float* x32, double* y64, int64_t n, void* stream);
 
 /* Environment update (Sec. 3.4: the fixed sites are contracted into L and R
  * one site at a time).

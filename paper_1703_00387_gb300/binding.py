@@ -104,6 +104,7 @@ _SIGS = {
     "osmps_dgemm_emu": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _i64, _vp]),
     "osmps_sytrd": (_c.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "osmps_selftest_wait_timeout": (_c.c_int, [_vp, _c.c_int, _c.c_double, _vp]),
+    "osmps_selftest_convert": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, _vp]),
     "osmps_gemm_grouped": (_c.c_int, [_vp, _vp, _i64, _vp, _i64, _vp]),
     "osmps_copy_list": (_c.c_int, [_vp, _c.POINTER(CopyDesc), _i64, _vp]),
     "osmps_sym_eig_top": (_c.c_int, [_vp, _vp, _i64, _i64, _dp, _vp, _vp]),
@@ -722,6 +723,21 @@ def osmps_selftest_wait_timeout(ctx, which, limit_us=2000.0, stream=None):
     wait in a kernel holding tensor memory; 1: a grid barrier one block never
     reaches). Raises OsmpsError(ETIMEOUT) when the wait gave up, as it should."""
     _check(lib().osmps_selftest_wait_timeout(ctx.ptr, int(which), float(limit_us), _stream(stream)))
+
+
+def osmps_selftest_convert(ctx, x64, x32, stream=None):
+    """(float32 of x64, float64 of x32) by the library's integer-field
+    conversions (device tensors of equal length)."""
+    import torch
+    if not (isinstance(x32, torch.Tensor) and x32.is_cuda and x32.dtype == torch.float32
+            and x32.is_contiguous()) or x32.numel() != x64.numel():
+        raise TypeError("x32 must be a contiguous float32 CUDA tensor as long as x64")
+    y32 = torch.empty(x64.numel(), dtype=torch.float32, device=x64.device)
+    y64 = torch.empty(x32.numel(), dtype=torch.float64, device=x32.device)
+    _check(lib().osmps_selftest_convert(ctx.ptr, _dev(x64, "x64"), _vp(y32.data_ptr()),
+                                        _vp(x32.data_ptr()), _dev(y64, "y64"), x64.numel(),
+                                        _stream(stream)))
+    return y32, y64
 
 
 def osmps_gemm_grouped(ctx, outs, terms, stream=None):

@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "ieee.cuh"
 #include "tcgen05.cuh"
 
 namespace osmps {
@@ -75,17 +76,39 @@ __device__ __forceinline__ void store_tile_rows(void* C, int64_t row0, int64_t c
     __syncwarp();
     const int cc = lane & 15;
     const int64_t col = col0 + STG_COLS * pass + cc;
+    if (OUT != TC_OUT_F32 && addend) {
+      // the addend's values of eight rows are requested before the first of
+      // their stores, so their latency is paid twice per pass, not per row;
+      // the sum is formed in float32 (both terms are float32 results) and
+      // widened by integer fields (the float64 pipe is narrow)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float add[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int64_t row = row0 + 2 * (8 * h + i) + (lane >> 4);
+          add[i] = (row < M && col < N) ? addend[row * ldc + col] : 0.0f;
+        }
 #pragma unroll 4
-    for (int i = 0; i < 16; ++i) {
-      const int rr = 2 * i + (lane >> 4);
-      const float val = stg[rr * STG_COLS + (((cc >> 2) ^ (rr & 3)) << 2) + (cc & 3)];
-      const int64_t row = row0 + rr;
-      if (row < M && col < N) {
-        if (OUT == TC_OUT_F32)
-          reinterpret_cast<float*>(C)[row * ldc + col] = val;
-        else
-          reinterpret_cast<double*>(C)[row * ldc + col] =
-              addend ? (double)val + (double)addend[row * ldc + col] : (double)val;
+        for (int i = 0; i < 8; ++i) {
+          const int rr = 2 * (8 * h + i) + (lane >> 4);
+          const float val = stg[rr * STG_COLS + (((cc >> 2) ^ (rr & 3)) << 2) + (cc & 3)];
+          const int64_t row = row0 + rr;
+          if (row < M && col < N) reinterpret_cast<double*>(C)[row * ldc + col] = f32_to_f64(val + add[i]);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int i = 0; i < 16; ++i) {
+        const int rr = 2 * i + (lane >> 4);
+        const float val = stg[rr * STG_COLS + (((cc >> 2) ^ (rr & 3)) << 2) + (cc & 3)];
+        const int64_t row = row0 + rr;
+        if (row < M && col < N) {
+          if (OUT == TC_OUT_F32)
+            reinterpret_cast<float*>(C)[row * ldc + col] = val;
+          else
+            reinterpret_cast<double*>(C)[row * ldc + col] = (double)val;
+        }
       }
     }
     __syncwarp();  // the next pass overwrites the staging block

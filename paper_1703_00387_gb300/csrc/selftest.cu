@@ -11,6 +11,7 @@
 // Nothing faults, traps or spins without a bound; the context stays usable.
 #include "common.cuh"
 #include "gridsync.cuh"
+#include "ieee.cuh"
 #include "tcgen05.cuh"
 
 namespace osmps {
@@ -54,10 +55,36 @@ __global__ void k_selftest_grid(unsigned* bar, uint64_t limit_ns, int* __restric
   grid_barrier(bar, gridDim.x, err, &s_ok, limit_ns);
 }
 
+__global__ void k_selftest_convert(const double* __restrict__ x64, float* __restrict__ y32,
+                                   const float* __restrict__ x32, double* __restrict__ y64, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    y32[i] = f64_to_f32_rn(x64[i]);
+    y64[i] = f32_to_f64(x32[i]);
+  }
+}
+
 }  // namespace
 }  // namespace osmps
 
 using namespace osmps;
+
+extern "C" osmps_status osmps_selftest_convert(osmps_ctx* ctx, const double* x64, float* y32,
+                                               const float* x32, double* y64, int64_t n, void* stream) {
+  clear_error();
+  if (!ctx || (n > 0 && (!x64 || !y32 || !x32 || !y64)))
+    return set_error(OSMPS_EINVAL, "osmps_selftest_convert: null argument");
+  if (n < 0) return set_error(OSMPS_EINVAL, "osmps_selftest_convert: n=%lld", (long long)n);
+  if (n == 0) return OSMPS_OK;
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  k_selftest_convert<<<blocks, 256, 0, s>>>(x64, y32, x32, y64, n);
+  note_launch();
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
 
 extern "C" osmps_status osmps_selftest_wait_timeout(osmps_ctx* ctx, int which, double limit_us,
                                                     void* stream) {

@@ -2,7 +2,8 @@
 device memory:
 
 * repeated H_eff.theta products (and optionally one full two-site step) at a
-  given bond dimension;
+  given bond dimension; --identity gives L and R the unit-matrix channels of
+  a canonical MPS;
 * --lanczos-solve: one 20-step Lanczos solve on a symmetric operator, after 3
   untimed solves, between the profiler's start and stop (for
   `ncu --profile-from-start off`);
@@ -14,6 +15,7 @@ device memory:
   the profiler's start and stop.
 
     python -m paper_1703_00387_gb300.profile_heff --chi 1024 --prec bf16x3 --reps 3
+    python -m paper_1703_00387_gb300.profile_heff --chi 1024 --prec bf16x3 --reps 3 --identity
     python -m paper_1703_00387_gb300.profile_heff --chi 1024 --step
     python -m paper_1703_00387_gb300.profile_heff --lanczos-solve --chi 32 --lanczos-mode host
     python -m paper_1703_00387_gb300.profile_heff --u1
@@ -39,6 +41,9 @@ def main():
     ap.add_argument("--u1", action="store_true")
     ap.add_argument("--tdvp", action="store_true")
     ap.add_argument("--tdvp-L", type=int, default=32)
+    ap.add_argument("--identity", action="store_true",
+                    help="environments of a canonical MPS: L's last and R's first channel the "
+                         "unit matrix (left out of the GEMMs, with identity skipping 'always')")
     args = ap.parse_args()
     if args.lanczos_solve:
         return lanczos_solve(args)
@@ -58,6 +63,10 @@ def main():
         np.random.default_rng(3).standard_normal((w, d, d, w))
     Lh = inputs.random_symmetric_env(chi, w, seed=1)
     Rh = inputs.random_symmetric_env(chi, w, seed=2)
+    if args.identity:
+        Lh[:, w - 1, :] = np.eye(chi)
+        Rh[:, 0, :] = np.eye(chi)
+        ctx.set_identity_skip("always")
     th = np.random.default_rng(3).standard_normal((chi, d, d, chi))
     L, Wt, R, x = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (Lh, W, Rh, th))
     y = torch.empty_like(x)

@@ -28,6 +28,13 @@ CHAINS = [("tfi", 10, 32, 1.0), ("xxz", 12, 16, 1.0), ("tfi", 8, 16, 0.5), ("xxz
           ("tfi", 12, 24, 1.5), ("xxz", 10, 32, 1.3), ("tfi", 6, 8, 1.2)]
 
 
+def _xxz_ground_energy(L, delta):
+    from scipy.sparse.linalg import eigsh
+    from oracle import mpo as ompo
+    H = ompo.mpo_to_dense(ompo.xxz_mpo(L, 1.0, delta, 0.0))
+    return float(eigsh(H, k=1, which="SA", tol=1e-13)[0][0])
+
+
 def _mpo_W(model, L, p):
     return hamiltonians.ising(L, 1.0, p) if model == "tfi" else hamiltonians.xxz(L, 1.0, p, 0.0)
 
@@ -53,6 +60,12 @@ def test_batch_equals_sequential_and_exact(ctxs):
         if model == "tfi" and chi >= 2 ** (L // 2):  # exact bond dimension
             e = exact.ising_free_fermion_energy(L, 1.0, p)
             assert abs(stats[i]["energy"] - e) <= 1e-9 * abs(e)
+        if model == "xxz":  # exact diagonalisation of the oracle's own MPO
+            e = _xxz_ground_energy(L, p)
+            if chi >= 2 ** (L // 2):
+                assert abs(stats[i]["energy"] - e) <= 1e-9 * abs(e)
+            else:  # truncated: variational, and close
+                assert e - 1e-10 <= stats[i]["energy"] <= e + 1e-3 * abs(e)
     for x in mps + mpo + mps2 + mpo2:
         x.close()
 
