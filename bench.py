@@ -346,6 +346,7 @@ def run_ours(args, ws, rank, local):
                                                  "20 Krylov vectors of 33.5 MB, 42 MB environments)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": roofline, "step_roofline": step_roofline(prof_other, elapsed, peaks, peak_src),
+        "tile_tuning": ctx.tuning(),
         "clocks": clocks, "gpu_launches": launches,
     }
 

@@ -132,6 +132,29 @@ osmps_status osmps_ctx_set_lanczos_mode(osmps_ctx* ctx, int mode);
  * EINVAL for another value.                                                */
 typedef enum { OSMPS_IDENTITY_OFF = 0, OSMPS_IDENTITY_SOLVER = 1, OSMPS_IDENTITY_ALWAYS = 2 } osmps_identity_mode;
 osmps_status osmps_ctx_set_identity_skip(osmps_ctx* ctx, int mode);
+/* Tile-width autotuning of the tcgen05 GEMMs (H_eff stages, environment
+ * updates, the U(1) grouped products). Each output tile is 128 rows by 256,
+ * 128 or 64 columns; the arithmetic per element does not depend on the
+ * width, so results are bit-identical. With OSMPS_AUTOTUNE_ON (default) the
+ * first product of a size class (output tiles counted at 128 x 64, K in
+ * steps of 512; grouped: problem count, tile count, K) that runs outside
+ * stream capture and kernel profiling is run at all three widths, each
+ * timed with CUDA events after one untimed run, and the fastest is kept in
+ * the context for the class; later products of the class use it. With
+ * OSMPS_AUTOTUNE_OFF every product uses 256 (unless a choice was set).
+ * EINVAL for another mode.                                                  */
+typedef enum { OSMPS_AUTOTUNE_OFF = 0, OSMPS_AUTOTUNE_ON = 1 } osmps_autotune_mode;
+osmps_status osmps_ctx_set_autotune(osmps_ctx* ctx, int mode);
+/* The context's tuning table: number of entries, and entry i (0-based):
+ * key[6] (class fields), the chosen width, and the measured microseconds
+ * at widths 256, 128, 64 (0 for a choice set by osmps_ctx_set_tuning).
+ * HOST outputs; EINVAL for i out of range.                                 */
+int64_t osmps_ctx_tuning_count(const osmps_ctx* ctx);
+osmps_status osmps_ctx_tuning_entry(const osmps_ctx* ctx, int64_t i, int64_t* key, int* width,
+                                    float* us3);
+/* Set (or replace) the width for a class key, e.g. from a table saved by an
+ * earlier run. EINVAL for a width other than 64, 128, 256.                 */
+osmps_status osmps_ctx_set_tuning(osmps_ctx* ctx, const int64_t* key, int width);
 /* Bytes of device memory currently held by the context's workspace.         */
 size_t osmps_ctx_workspace_bytes(const osmps_ctx* ctx);
 

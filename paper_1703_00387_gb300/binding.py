@@ -96,6 +96,11 @@ _SIGS = {
     "osmps_ctx_set_eig_solver": (_c.c_int, [_vp, _c.c_int]),
     "osmps_ctx_set_lanczos_mode": (_c.c_int, [_vp, _c.c_int]),
     "osmps_ctx_set_identity_skip": (_c.c_int, [_vp, _c.c_int]),
+    "osmps_ctx_set_autotune": (_c.c_int, [_vp, _c.c_int]),
+    "osmps_ctx_tuning_count": (_i64, [_vp]),
+    "osmps_ctx_tuning_entry": (_c.c_int, [_vp, _i64, _c.POINTER(_i64), _c.POINTER(_c.c_int),
+                                          _c.POINTER(_c.c_float)]),
+    "osmps_ctx_set_tuning": (_c.c_int, [_vp, _c.POINTER(_i64), _c.c_int]),
     "osmps_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "osmps_profile_read": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_i64), _dp, _dp, _dp]),
     "osmps_kernel_launches": (_i64, []),
@@ -242,6 +247,28 @@ class Context:
         H_eff.theta leaves unit-matrix environment channels out of its GEMMs."""
         code = {"off": 0, "solver": 1, "always": 2}[mode] if isinstance(mode, str) else int(mode)
         _check(lib().osmps_ctx_set_identity_skip(self.ptr, code))
+
+    def set_autotune(self, on):
+        """Measure the tcgen05 GEMM tile width per size class on first use (True,
+        the default) or always use 256 columns (False)."""
+        _check(lib().osmps_ctx_set_autotune(self.ptr, 1 if on else 0))
+
+    def tuning(self):
+        """The tile-width table: list of dicts (key, width, us at 256/128/64)."""
+        out = []
+        for i in range(int(lib().osmps_ctx_tuning_count(self.ptr))):
+            key = (_i64 * 6)()
+            w = _c.c_int()
+            us = (_c.c_float * 3)()
+            _check(lib().osmps_ctx_tuning_entry(self.ptr, i, key, _c.byref(w), us))
+            out.append({"key": [int(k) for k in key], "width": w.value,
+                        "us": {"256": us[0], "128": us[1], "64": us[2]}})
+        return out
+
+    def set_tuning(self, key, width):
+        """Set the tile width of a size class (key: 6 integers, as in tuning())."""
+        k = (_i64 * 6)(*[int(x) for x in key])
+        _check(lib().osmps_ctx_set_tuning(self.ptr, k, int(width)))
 
     def workspace_bytes(self):
         return int(lib().osmps_ctx_workspace_bytes(self.ptr))

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libosmps.so")
 SOURCES = ["ctx.cu", "gemm_f64.cu", "gemm_tc.cu", "ops.cu", "contract.cu", "lanczos.cu",
            "split.cu", "sweep.cu", "noalloc.cu", "gemm_emu.cu", "grad.cu", "batch.cu", "u1.cu", "eig.cu", "sytrd.cu", "excited.cu",
-           "tdvp.cu", "selftest.cu", "blocks.cu"]
+           "tdvp.cu", "selftest.cu", "blocks.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

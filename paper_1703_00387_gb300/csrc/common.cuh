@@ -157,6 +157,15 @@ struct osmps_ctx {
   // that makes workspace growth an error while a capture is open
   cudaStream_t capture_stream = nullptr;
   bool capturing = false;
+  // tcgen05 GEMM tile widths chosen by measurement (OSMPS_AUTOTUNE_ON) per
+  // size class: key, chosen width, microseconds at widths 256 / 128 / 64
+  int tc_autotune = OSMPS_AUTOTUNE_ON;
+  struct TcTuned {
+    int64_t key[6];
+    int bn;
+    float us[3];
+  };
+  std::vector<TcTuned> tc_tuned;
   // Recorded Lanczos step graphs kept for replay (lanczos.cu), least recently
   // used first out, and a count of workspace (re)allocations that every
   // graph's key includes (a graph holds workspace addresses).
@@ -261,10 +270,12 @@ struct GroupProblem {
   int pad;
   int64_t c_off, ldc;  // element offset of the problem's C[0,0], row stride
 };
-// Fills tile0 / tiles_n (128 x 256 tiles) and returns the total tile count.
-int64_t group_tiles(GroupProblem* probs, int n_prob);
+// Fill tile0 / tiles_n for tile width bn (64, 128 or 256); returns the tile count.
+int64_t group_tiles(GroupProblem* probs, int n_prob, int bn);
+bool tc_tile_width_ok(int bn);
 struct GemmTcGrouped {
   int kind = TC_BF16, out = TC_OUT_F32;
+  int bn = 256;             // tile width the problem table was built for
   const void* A = nullptr;  // packed operand rows, 2 * Kpl elements each
   int64_t rowsA = 0;
   const void* B = nullptr;
@@ -277,6 +288,24 @@ struct GemmTcGrouped {
   double logical_flops = 0.0;  // for profiling records
 };
 osmps_status gemm_tc_grouped(osmps_ctx* ctx, const GemmTcGrouped& g, cudaStream_t stream);
+
+// Tile-width autotuning of the tcgen05 GEMMs (csrc/tune.cu). A size class
+// (plain: tiles of the output at 128 x 64 granularity and K in 512s; grouped:
+// problem count, 128 x 64 tile count, K) maps to the width measured fastest
+// the first time the class ran; 0 = not yet measured.
+struct TcKey {
+  int64_t v[6];
+};
+TcKey tc_key(int grouped, int kind, int out, int64_t a, int64_t b, int64_t c);
+int tc_tuned_width(osmps_ctx* ctx, const TcKey& key);
+// true when a first product of an unmeasured class may be timed now (tuning
+// on, no stream capture, no kernel profiling in progress)
+bool tc_may_tune(osmps_ctx* ctx);
+// us[w] = mean CUDA-event time of reps runs of fn on stream
+osmps_status tc_time_launches(osmps_ctx* ctx, cudaStream_t stream, int reps, float* us,
+                              const std::function<osmps_status(cudaStream_t)>& fn);
+// store the fastest of widths[0..2] (times us) for key; returns it
+int tc_record_tuning(osmps_ctx* ctx, const TcKey& key, const int* widths, const float* us);
 
 // Split a float64 (or float32) matrix view into the hi|lo operand layout.
 // Source element (row r, col k) with r = r0*n1 + r1 (r1 < n1) lives at

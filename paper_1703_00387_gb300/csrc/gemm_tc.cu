@@ -37,21 +37,30 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128;
-constexpr int BN = 256;
 constexpr int KSLICE_BYTES = 128;  // K bytes per stage row = one 128B swizzle span
-constexpr int STAGES = 4;
 constexpr int A_STAGE = BM * KSLICE_BYTES;  // 16 KB
-constexpr int B_STAGE = BN * KSLICE_BYTES;  // 32 KB
-constexpr int STAGE_BYTES = A_STAGE + B_STAGE;
 constexpr int EPI_WARPS = 16;                // 4 lane quarters x 4 column quarters
-constexpr int EPI_COLS = BN / 4;             // columns per epilogue thread
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int CHUNK = 4;                     // K slices (x 4 MMAs) per TMEM partial sum
-constexpr uint32_t TMEM_COLS = 512;          // two 256-column accumulator buffers
 // epilogue staging: per epilogue warp 32 rows x 16 columns of float32
 constexpr int STG_COLS = 16;
 constexpr int STG_BYTES = EPI_WARPS * 32 * STG_COLS * 4;  // 32 KB
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + STG_BYTES;
+
+// Tile width BN (256, 128 or 64 output columns): the B stage, the ring depth
+// (about 192 KB of stages), the epilogue columns per thread and the two TMEM
+// accumulator buffers follow from it. The arithmetic per output element
+// (K order, partial sums, promotion) does not depend on BN, so every width
+// gives the same bits.
+template <int BN>
+struct TcTile {
+  static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
+  static constexpr int B_STAGE = BN * KSLICE_BYTES;
+  static constexpr int STAGE_BYTES = A_STAGE + B_STAGE;
+  static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;  // 4 / 6 / 8
+  static constexpr int EPI_COLS = BN / 4;                     // columns per epilogue thread
+  static constexpr uint32_t TMEM_COLS = 2 * BN;               // two accumulator buffers
+  static constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + STG_BYTES;
+};
 
 // One epilogue warp's 32 x 64 results (lane = row, acc = its 64 columns) to
 // global memory, through its 32 x 16 float32 staging block in 4 passes: the
@@ -59,7 +68,7 @@ constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256 + STG_BY
 // half-warp stores 16 consecutive columns of one row, so a store instruction
 // covers 2 rows x 16 columns (4 full sectors for float32, 8 for float64)
 // instead of touching 32 rows.
-template <int OUT>
+template <int OUT, int EPI_COLS>
 __device__ __forceinline__ void store_tile_rows(void* C, int64_t row0, int64_t col0, int64_t M,
                                                 int64_t N, int64_t ldc, const float (&acc)[EPI_COLS],
                                                 float* __restrict__ stg, int lane,
@@ -131,7 +140,7 @@ struct TileJob {
   void* C;
 };
 
-template <int OUT>
+template <int OUT, int BN>
 __device__ __forceinline__ TileJob tile_job(int tile, void* C, int64_t M, int64_t N, int64_t ldc,
                                             int nkb, int tiles_n,
                                             const GroupProblem* __restrict__ probs, int n_prob) {
@@ -167,12 +176,16 @@ __device__ __forceinline__ TileJob tile_job(int tile, void* C, int64_t M, int64_
   return j;
 }
 
-template <int KIND, int OUT>
+template <int KIND, int OUT, int BN>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               void* __restrict__ C, int64_t M, int64_t N, int64_t ldc, int nkb, int kelem,
               int Kp, int tiles_n, int n_tiles, int* __restrict__ err,
               const GroupProblem* __restrict__ probs, int n_prob, const float* __restrict__ addend) {
+  using T = TcTile<BN>;
+  constexpr int STAGES = T::STAGES, B_STAGE = T::B_STAGE, STAGE_BYTES = T::STAGE_BYTES;
+  constexpr int EPI_COLS = T::EPI_COLS;
+  constexpr uint32_t TMEM_COLS = T::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -214,7 +227,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t issued = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      const TileJob job = tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob);
+      const TileJob job = tile_job<OUT, BN>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob);
       const int total = 3 * job.nkb;  // K slices over the three products
       for (int it = 0; it < total; ++it, ++g) {
         const int s = g % STAGES;
@@ -239,7 +252,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t g = 0, gc = 0;  // slices / chunks consumed by this CTA
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      const int total = 3 * tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob).nkb;
+      const int total = 3 * tile_job<OUT, BN>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob).nkb;
       for (int it = 0; it < total && ok; ++it, ++g) {
         const bool first = (it % CHUNK) == 0;
         const uint32_t buf = gc & 1u;
@@ -279,7 +292,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const int nchunk =
-          (3 * tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob).nkb + CHUNK - 1) / CHUNK;
+          (3 * tile_job<OUT, BN>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob).nkb + CHUNK - 1) / CHUNK;
       float acc[EPI_COLS];
 #pragma unroll
       for (int j = 0; j < EPI_COLS; ++j) acc[j] = 0.0f;
@@ -304,9 +317,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (!ok) break;
       // decoded again after the K loop so its fields are not live during it
-      const TileJob job = tile_job<OUT>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob);
+      const TileJob job = tile_job<OUT, BN>(tile, C, M, N, ldc, nkb, tiles_n, probs, n_prob);
       float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * 32 * STG_COLS;
-      store_tile_rows<OUT>(job.C, job.row0 + q * 32, job.col0 + part * EPI_COLS, job.M, job.N,
+      store_tile_rows<OUT, EPI_COLS>(job.C, job.row0 + q * 32, job.col0 + part * EPI_COLS, job.M, job.N,
                            job.ldc, acc, stg, lane, addend);
     }
     if (!ok) atomicOr(err, 1);
@@ -360,12 +373,13 @@ osmps_status tc_make_map(CUtensorMap* map, const void* base, int kind, int64_t r
 
 namespace {
 
-template <int KIND, int OUT>
+template <int KIND, int OUT, int BN>
 osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g, int* err,
                     int sm_count, cudaStream_t stream) {
+  using T = TcTile<BN>;
   // thread-safe one-time setup (function-local static initialisation)
   static const cudaError_t configured = cudaFuncSetAttribute(
-      k_gemm_tc<KIND, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+      k_gemm_tc<KIND, OUT, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM_BYTES);
   OSMPS_CUDA(configured);
   const int kelem = KSLICE_BYTES / (int)tc_elem_bytes(KIND);
   const int nkb = (int)(g.Kp / kelem);
@@ -373,22 +387,65 @@ osmps_status launch(const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g,
   const int n_tiles = tiles_n * (int)cdiv(g.M, BM);
   const int grid = std::min(n_tiles, sm_count);
   const int ph = prof_begin(stream);
-  { k_gemm_tc<KIND, OUT><<<grid, THREADS, SMEM_BYTES, stream>>>(a, b, g.C, g.M, g.N, g.ldc, nkb,
-                                                             kelem, (int)g.Kp, tiles_n, n_tiles,
-                                                             err, nullptr, 0,
-                                                             OUT == TC_OUT_F64 ? g.addend : nullptr); note_launch(); }
+  { k_gemm_tc<KIND, OUT, BN><<<grid, THREADS, T::SMEM_BYTES, stream>>>(
+        a, b, g.C, g.M, g.N, g.ldc, nkb, kelem, (int)g.Kp, tiles_n, n_tiles, err, nullptr, 0,
+        OUT == TC_OUT_F64 ? g.addend : nullptr); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   const double logical = 2.0 * (double)g.M * (double)g.N * (double)(g.K > 0 ? g.K : g.Kp);
   prof_end(ph, stream, OSMPS_KERNEL_GEMM_TC, logical, 3.0 * logical);
   return OSMPS_OK;
 }
 
+template <int KIND, int OUT>
+osmps_status launch_bn(int bn, const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g, int* err,
+                       int sm_count, cudaStream_t stream) {
+  if (bn == 64) return launch<KIND, OUT, 64>(a, b, g, err, sm_count, stream);
+  if (bn == 128) return launch<KIND, OUT, 128>(a, b, g, err, sm_count, stream);
+  return launch<KIND, OUT, 256>(a, b, g, err, sm_count, stream);
+}
+
+osmps_status launch_any(int bn, const CUtensorMap& a, const CUtensorMap& b, const GemmTc& g, int* err,
+                        int sm_count, cudaStream_t stream) {
+  if (g.kind == TC_BF16) {
+    if (g.out == TC_OUT_F32) return launch_bn<TC_BF16, TC_OUT_F32>(bn, a, b, g, err, sm_count, stream);
+    return launch_bn<TC_BF16, TC_OUT_F64>(bn, a, b, g, err, sm_count, stream);
+  }
+  if (g.out == TC_OUT_F32) return launch_bn<TC_TF32, TC_OUT_F32>(bn, a, b, g, err, sm_count, stream);
+  return launch_bn<TC_TF32, TC_OUT_F64>(bn, a, b, g, err, sm_count, stream);
+}
+
+template <int KIND, int OUT, int BN>
+osmps_status launch_grouped(const CUtensorMap& ma, const CUtensorMap& mb, const GemmTcGrouped& g,
+                            int64_t n_tiles, int* err, int sm_count, cudaStream_t stream) {
+  using T = TcTile<BN>;
+  static const cudaError_t cfg = cudaFuncSetAttribute(
+      k_gemm_tc<KIND, OUT, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM_BYTES);
+  OSMPS_CUDA(cfg);
+  const int kelem = KSLICE_BYTES / (int)tc_elem_bytes(KIND);
+  const int grid = (int)std::min<int64_t>(n_tiles, sm_count);
+  k_gemm_tc<KIND, OUT, BN><<<grid, THREADS, T::SMEM_BYTES, stream>>>(
+      ma, mb, g.C, 0, 0, 0, 0, kelem, (int)g.Kpl, 1, (int)n_tiles, err, g.probs, g.n_prob, nullptr);
+  note_launch();
+  return OSMPS_OK;
+}
+
+template <int KIND, int OUT>
+osmps_status launch_grouped_bn(int bn, const CUtensorMap& ma, const CUtensorMap& mb,
+                               const GemmTcGrouped& g, int64_t n_tiles, int* err, int sm_count,
+                               cudaStream_t stream) {
+  if (bn == 64) return launch_grouped<KIND, OUT, 64>(ma, mb, g, n_tiles, err, sm_count, stream);
+  if (bn == 128) return launch_grouped<KIND, OUT, 128>(ma, mb, g, n_tiles, err, sm_count, stream);
+  return launch_grouped<KIND, OUT, 256>(ma, mb, g, n_tiles, err, sm_count, stream);
+}
+
 }  // namespace
 
-int64_t group_tiles(GroupProblem* probs, int n_prob) {
+bool tc_tile_width_ok(int bn) { return bn == 64 || bn == 128 || bn == 256; }
+
+int64_t group_tiles(GroupProblem* probs, int n_prob, int bn) {
   int64_t t = 0;
   for (int i = 0; i < n_prob; ++i) {
-    probs[i].tiles_n = (int)cdiv(probs[i].N, BN);
+    probs[i].tiles_n = (int)cdiv(probs[i].N, bn);
     probs[i].tile0 = (int)t;
     t += (int64_t)probs[i].tiles_n * cdiv(probs[i].M, BM);
   }
@@ -400,31 +457,23 @@ osmps_status gemm_tc_grouped(osmps_ctx* ctx, const GemmTcGrouped& g, cudaStream_
   if (g.Kpl <= 0 || g.Kpl % 64 != 0 || 2 * g.Kpl > (int64_t)1 << 31 || g.n_tiles > ((int64_t)1 << 31) ||
       g.rowsA > ((int64_t)1 << 31) || g.rowsB > ((int64_t)1 << 31))
     return set_error(OSMPS_ESHAPE, "gemm_tc_grouped: bad packed operand shape");
+  if (!tc_tile_width_ok(g.bn)) return set_error(OSMPS_EINVAL, "gemm_tc_grouped: tile width %d", g.bn);
   CUtensorMap ma, mb;
   OSMPS_TRY(tc_make_map(&ma, g.A, g.kind, g.rowsA, 2 * g.Kpl, BM));
-  OSMPS_TRY(tc_make_map(&mb, g.B, g.kind, g.rowsB, 2 * g.Kpl, BN));
-  const int kelem = KSLICE_BYTES / (int)tc_elem_bytes(g.kind);
-  const int grid = (int)std::min<int64_t>(g.n_tiles, ctx->sm_count);
+  OSMPS_TRY(tc_make_map(&mb, g.B, g.kind, g.rowsB, 2 * g.Kpl, g.bn));
   const int ph = prof_begin(stream);
   int* err = ctx->dev_flags;
-#define OSMPS_GROUPED_LAUNCH(K, O)                                                                   \
-  {                                                                                                 \
-    static const cudaError_t cfg_ = cudaFuncSetAttribute(                                           \
-        k_gemm_tc<K, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);             \
-    OSMPS_CUDA(cfg_);                                                                               \
-    k_gemm_tc<K, O><<<grid, THREADS, SMEM_BYTES, stream>>>(ma, mb, g.C, 0, 0, 0, 0, kelem,          \
-                                                           (int)g.Kpl, 1, (int)g.n_tiles, err,      \
-                                                           g.probs, g.n_prob, nullptr);             \
-    note_launch();                                                                                  \
-  }
   if (g.kind == TC_BF16) {
-    if (g.out == TC_OUT_F32) OSMPS_GROUPED_LAUNCH(TC_BF16, TC_OUT_F32)
-    else OSMPS_GROUPED_LAUNCH(TC_BF16, TC_OUT_F64)
+    if (g.out == TC_OUT_F32)
+      OSMPS_TRY((launch_grouped_bn<TC_BF16, TC_OUT_F32>(g.bn, ma, mb, g, g.n_tiles, err, ctx->sm_count, stream)));
+    else
+      OSMPS_TRY((launch_grouped_bn<TC_BF16, TC_OUT_F64>(g.bn, ma, mb, g, g.n_tiles, err, ctx->sm_count, stream)));
   } else {
-    if (g.out == TC_OUT_F32) OSMPS_GROUPED_LAUNCH(TC_TF32, TC_OUT_F32)
-    else OSMPS_GROUPED_LAUNCH(TC_TF32, TC_OUT_F64)
+    if (g.out == TC_OUT_F32)
+      OSMPS_TRY((launch_grouped_bn<TC_TF32, TC_OUT_F32>(g.bn, ma, mb, g, g.n_tiles, err, ctx->sm_count, stream)));
+    else
+      OSMPS_TRY((launch_grouped_bn<TC_TF32, TC_OUT_F64>(g.bn, ma, mb, g, g.n_tiles, err, ctx->sm_count, stream)));
   }
-#undef OSMPS_GROUPED_LAUNCH
   OSMPS_LAUNCH_CHECK();
   prof_end(ph, stream, OSMPS_KERNEL_GEMM_TC, g.logical_flops, 3.0 * g.logical_flops);
   return OSMPS_OK;
@@ -438,16 +487,32 @@ osmps_status gemm_tc(osmps_ctx* ctx, const GemmTc& g, cudaStream_t stream) {
   if (2 * g.Kp > (int64_t)1 << 31 || cdiv(g.M, BM) > 65535 || g.M > ((int64_t)1 << 31) ||
       g.N > ((int64_t)1 << 31))
     return set_error(OSMPS_ESHAPE, "gemm_tc: dimensions exceed the supported range");
-  CUtensorMap ma, mb;
-  OSMPS_TRY(tc_make_map(&ma, g.A, g.kind, g.M, 2 * g.Kp, BM));
-  OSMPS_TRY(tc_make_map(&mb, g.B, g.kind, g.N, 2 * g.Kp, BN));
   int* err = ctx->dev_flags;
-  if (g.kind == TC_BF16) {
-    if (g.out == TC_OUT_F32) return launch<TC_BF16, TC_OUT_F32>(ma, mb, g, err, ctx->sm_count, stream);
-    return launch<TC_BF16, TC_OUT_F64>(ma, mb, g, err, ctx->sm_count, stream);
+  CUtensorMap ma;
+  OSMPS_TRY(tc_make_map(&ma, g.A, g.kind, g.M, 2 * g.Kp, BM));
+  const TcKey key = tc_key(0, g.kind, g.out, cdiv(g.M, BM), cdiv(g.N, 64), cdiv(g.Kp, 512));
+  int bn = tc_tuned_width(ctx, key);
+  if (bn == 0 && tc_may_tune(ctx)) {
+    // Autotuning: the first product of a size class is run at every tile
+    // width, each timed on the stream after one untimed run (the outputs are
+    // the same bits); the fastest width is kept for the class.
+    float us[3] = {0.f, 0.f, 0.f};
+    const int widths[3] = {256, 128, 64};
+    for (int w = 0; w < 3; ++w) {
+      CUtensorMap mb;
+      OSMPS_TRY(tc_make_map(&mb, g.B, g.kind, g.N, 2 * g.Kp, widths[w]));
+      OSMPS_TRY(launch_any(widths[w], ma, mb, g, err, ctx->sm_count, stream));
+      OSMPS_TRY(tc_time_launches(ctx, stream, 2, &us[w], [&](cudaStream_t s) {
+        return launch_any(widths[w], ma, mb, g, err, ctx->sm_count, s);
+      }));
+    }
+    bn = tc_record_tuning(ctx, key, widths, us);
+    return OSMPS_OK;  // the last timed run left the product in C
   }
-  if (g.out == TC_OUT_F32) return launch<TC_TF32, TC_OUT_F32>(ma, mb, g, err, ctx->sm_count, stream);
-  return launch<TC_TF32, TC_OUT_F64>(ma, mb, g, err, ctx->sm_count, stream);
+  if (bn == 0) bn = 256;
+  CUtensorMap mb;
+  OSMPS_TRY(tc_make_map(&mb, g.B, g.kind, g.N, 2 * g.Kp, bn));
+  return launch_any(bn, ma, mb, g, err, ctx->sm_count, stream);
 }
 
 }  // namespace osmps

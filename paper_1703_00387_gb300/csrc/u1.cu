@@ -46,6 +46,10 @@ struct osmps_u1_heff {
   // device memory
   int64_t* d_tab = nullptr;
   osmps::GroupProblem* d_prob = nullptr;
+  // tile width each grouped stage's table is built for, and whether it is
+  // settled (measured or taken from the context's tuning table)
+  int bn1 = 256, bn4 = 256;
+  bool settled1 = false, settled4 = false;
   uint8_t* d_buf = nullptr;
   // offsets (int64 elements) of the tables inside d_tab
   int64_t t_lsec = 0, t_ql = 0, t_qr = 0, t_qwl = 0, t_rowlen = 0, t_t1off = 0, t_rs1 = 0, t_cs = 0,
@@ -515,8 +519,8 @@ osmps_status u1_build(osmps_u1_heff* h) {
   h->n_Y = nY;
   if (h->rowsA1 > (1 << 30) || h->rowsB1 > (1 << 30) || h->rowsA4 > 65535 || nth > ((int64_t)1 << 40))
     return set_error(OSMPS_EUNSUPPORTED, "u1 plan: block structure too large");
-  h->tiles1 = group_tiles(h->p1.data(), (int)h->p1.size());
-  h->tiles4 = group_tiles(h->p4.data(), (int)h->p4.size());
+  h->tiles1 = group_tiles(h->p1.data(), (int)h->p1.size(), 256);
+  h->tiles4 = group_tiles(h->p4.data(), (int)h->p4.size(), 256);
 
   h->t_lsec = put(lsec);
   h->t_ql = put(h->ql);
@@ -566,10 +570,12 @@ osmps_status u1_prepare_kind(osmps_u1_heff* h, const double* L, const double* W1
   if (h->kind_loaded != KIND) {
     // K slices per problem depend on the operand type (128 bytes of K per slice)
     const int kelem = KIND == TC_BF16 ? 64 : 32;
+    // kept in the host tables too: a table rebuilt for another tile width is
+    // uploaded from them
+    for (size_t i = 0; i < h->p1.size(); ++i) h->p1[i].nkb = (int)(h->kp1[i] / kelem);
+    for (size_t i = 0; i < h->p4.size(); ++i) h->p4[i].nkb = (int)(h->kp4[i] / kelem);
     std::vector<GroupProblem> all(h->p1);
     all.insert(all.end(), h->p4.begin(), h->p4.end());
-    for (size_t i = 0; i < h->p1.size(); ++i) all[i].nkb = (int)(h->kp1[i] / kelem);
-    for (size_t i = 0; i < h->p4.size(); ++i) all[h->p1.size() + i].nkb = (int)(h->kp4[i] / kelem);
     OSMPS_CUDA(cudaStreamSynchronize(s));  // earlier launches may still read the table
     if (!all.empty())
       OSMPS_CUDA(cudaMemcpy(h->d_prob, all.data(), all.size() * sizeof(GroupProblem),
@@ -593,6 +599,51 @@ osmps_status u1_prepare_kind(osmps_u1_heff* h, const double* L, const double* W1
   OSMPS_LAUNCH_CHECK();
   h->prepared_kind = KIND;
   return OSMPS_OK;
+}
+
+// Rebuild and upload stage st's problem table for tile width bn.
+osmps_status u1_table_width(osmps_u1_heff* h, int st, int bn, cudaStream_t s) {
+  std::vector<GroupProblem>& p = st == 1 ? h->p1 : h->p4;
+  int& cur = st == 1 ? h->bn1 : h->bn4;
+  if (cur == bn || p.empty()) return OSMPS_OK;
+  (st == 1 ? h->tiles1 : h->tiles4) = group_tiles(p.data(), (int)p.size(), bn);
+  GroupProblem* dst = h->d_prob + (st == 1 ? 0 : h->p1.size());
+  OSMPS_CUDA(cudaMemcpyAsync(dst, p.data(), p.size() * sizeof(GroupProblem), cudaMemcpyHostToDevice, s));
+  OSMPS_CUDA(cudaStreamSynchronize(s));  // the host table is rebuilt in place next time
+  cur = bn;
+  return OSMPS_OK;
+}
+
+// One grouped stage with its settled tile width: on the plan's first product
+// outside capture, the width comes from the context's tuning table for the
+// stage's size class, or is measured (all three widths, the fastest kept).
+osmps_status u1_grouped(osmps_ctx* ctx, osmps_u1_heff* h, int st, GemmTcGrouped g, cudaStream_t s) {
+  bool& settled = st == 1 ? h->settled1 : h->settled4;
+  std::vector<GroupProblem>& p = st == 1 ? h->p1 : h->p4;
+  if (!settled && !ctx->capturing) {
+    int64_t t64 = 0;
+    for (const GroupProblem& q : p) t64 += cdiv(q.M, 128) * cdiv(q.N, 64);
+    const TcKey key = tc_key(1, g.kind, g.out, (int64_t)p.size(), t64, cdiv(g.Kpl, 512));
+    int bn = tc_tuned_width(ctx, key);
+    if (bn == 0 && tc_may_tune(ctx)) {
+      const int widths[3] = {256, 128, 64};
+      float us[3] = {0.f, 0.f, 0.f};
+      for (int w = 0; w < 3; ++w) {
+        OSMPS_TRY(u1_table_width(h, st, widths[w], s));
+        g.bn = widths[w];
+        g.n_tiles = st == 1 ? h->tiles1 : h->tiles4;
+        OSMPS_TRY(gemm_tc_grouped(ctx, g, s));
+        OSMPS_TRY(tc_time_launches(ctx, s, 2, &us[w], [&](cudaStream_t q) { return gemm_tc_grouped(ctx, g, q); }));
+      }
+      bn = tc_record_tuning(ctx, key, widths, us);
+    }
+    if (bn == 0) bn = 256;
+    OSMPS_TRY(u1_table_width(h, st, bn, s));
+    settled = true;
+  }
+  g.bn = st == 1 ? h->bn1 : h->bn4;
+  g.n_tiles = st == 1 ? h->tiles1 : h->tiles4;
+  return gemm_tc_grouped(ctx, g, s);
 }
 
 template <int KIND>
@@ -620,9 +671,8 @@ osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* theta
     g.C = B + h->o_T1;
     g.probs = h->d_prob;
     g.n_prob = (int)h->p1.size();
-    g.n_tiles = h->tiles1;
     g.logical_flops = h->flops1;
-    OSMPS_TRY(gemm_tc_grouped(ctx, g, s));
+    OSMPS_TRY(u1_grouped(ctx, h, 1, g, s));
   }
   // stages 2 + 3
   if (h->rowsA4 > 0) {
@@ -672,9 +722,8 @@ osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* theta
     g.C = B + h->o_Y;
     g.probs = h->d_prob + h->p1.size();
     g.n_prob = (int)h->p4.size();
-    g.n_tiles = h->tiles4;
     g.logical_flops = h->flops4;
-    OSMPS_TRY(gemm_tc_grouped(ctx, g, s));
+    OSMPS_TRY(u1_grouped(ctx, h, 4, g, s));
   }
   if (h->rowsA4 > 0) {
     k_u1_scatter<<<(unsigned)cdiv(h->rowsA4, 8), 256, 0, s>>>(reinterpret_cast<const double*>(B + h->o_Y), T + h->t_ysrc,
