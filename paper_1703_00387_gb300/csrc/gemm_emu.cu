@@ -8,15 +8,16 @@
 //     and cut into S = 8 balanced base-128 digits q_p (|q_p| <= 128), so
 //     x = 2^e sum_p q_p 2^(-7(p+1)); the slices hold the integers q_p, exact
 //     in bf16 (all of this with integer arithmetic on the IEEE bits);
-//   * a slice pair (i, j) gives integer products q_i q_j of at most 2^14, so
-//     a run of 256 of them sums to less than 2^22: exact in the float32 TMEM
-//     accumulator;
-//   * the epilogue adds those exact integers in int32 per slice diagonal
+//   * a slice pair (i, j) gives integer products q_i q_j of at most 2^14,
+//     so a run of 1024 of them sums to at most 2^24: exact in the float32
+//     TMEM accumulator, integers being exact there up to 2^24 (tested with
+//     every top digit at 128);
+//   * the epilogue converts those exact integers and adds them per slice diagonal
 //     i + j (same unit 2^(-7(i+j+2))), over the 36 pairs with i + j <= 7
 //     (the dropped pairs are below 2^-56 of the row scales);
 //   * pairs on one diagonal share the unit, so a TMEM partial sum runs over
-//     up to 4 K blocks of 64 across the pairs of a diagonal (at K = 64 the
-//     36 pairs take 12 epilogue rounds, not 36);
+//     up to 16 K blocks of 64 across the pairs of a diagonal (at K = 64 the
+//     36 pairs take 8 epilogue rounds, not 36);
 //   * the diagonals are combined exactly in int64, Horner fashion in steps
 //     of 2^7, within groups of consecutive diagonals (two groups of four
 //     while K <= 2^17, whose sums stay below 2^53); each group sum becomes
@@ -52,7 +53,12 @@ constexpr int E_STAGE = E_A_STAGE + E_B_STAGE;
 constexpr int E_EPI_WARPS = 16;
 constexpr int E_EPI_COLS = EBN / 4;
 constexpr int E_THREADS = 64 + 32 * E_EPI_WARPS;
-constexpr int E_CHUNK = 4;  // 64-element K slices per exact partial sum (256 products)
+// 64-element K slices per exact partial sum: products are at most 2^14 (the
+// pair of top digits, |d_0| <= 128), so 16 slices (1024 products) stay
+// within 2^24. (Diagonals other than 0 could run 32 slices, their products
+// being at most 2^13; measured slightly slower, the epilogue then drains in
+// longer, fewer bursts.)
+constexpr int E_CHUNK = 16;
 constexpr uint32_t E_TMEM_COLS = 512;   // 2 x 128 accumulator columns, then the float64 sums
 constexpr uint32_t E_ACC_COL0 = 256;    // float64 group sums: two 32-bit columns per tile column
 constexpr size_t E_SMEM = (size_t)ESTAGES * E_STAGE + 1024 + 256;
@@ -74,6 +80,20 @@ __device__ __forceinline__ double i64_ldexp(long long x, int k) {
   const unsigned long long frac = (a << (52 - e)) & 0xFFFFFFFFFFFFFull;
   return __longlong_as_double((long long)(((unsigned long long)(x < 0) << 63) |
                                           ((unsigned long long)E << 52) | frac));
+}
+
+// Tile t -> (m0, n0) in groups of E_GROUP_M tile rows, columns walked within
+// a group: the tiles that run at the same time then share E_GROUP_M A row
+// slabs and fewer B column slabs than a row-major walk, so more of the slice
+// operands stay in L2 between the pairs' passes.
+constexpr int E_GROUP_M = 8;
+__device__ __forceinline__ void emu_tile(int tile, int tiles_m, int tiles_n, int& m0, int& n0) {
+  const int per_group = E_GROUP_M * tiles_n;
+  const int g = tile / per_group, first = g * E_GROUP_M;
+  const int rows = min(tiles_m - first, E_GROUP_M);
+  const int local = tile - g * per_group;
+  m0 = (first + local % rows) * EBM;
+  n0 = (local / rows) * EBN;
 }
 
 // Close a diagonal group of the epilogue: its sums H (the last diagonal `cur`
@@ -165,7 +185,8 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     uint32_t g = 0, issued = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      const int m0 = (tile / tiles_n) * EBM, n0 = (tile % tiles_n) * EBN;
+      int m0, n0;
+      emu_tile(tile, n_tiles / tiles_n, tiles_n, m0, n0);
       for (int q = 0; q < npairs && ok; ++q) {
         const int xa = pl.a[q] * Kp, xb = pl.b[q] * Kp;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
@@ -232,7 +253,8 @@ __global__ void __launch_bounds__(E_THREADS, 1)
     uint32_t gc = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      const int m0 = (tile / tiles_n) * EBM, n0 = (tile % tiles_n) * EBN;
+      int m0, n0;
+      emu_tile(tile, n_tiles / tiles_n, tiles_n, m0, n0);
       const int64_t row = (int64_t)m0 + qd * 32 + lane;
       const int64_t col0 = (int64_t)n0 + part * E_EPI_COLS;
       const int ea = row < M ? eA[row] : 0;
@@ -271,9 +293,8 @@ __global__ void __launch_bounds__(E_THREADS, 1)
             tmem_ld16(base + 16 * j, r);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              // exact integer (|v| < 2^22): v + 1.5*2^23 has v in its low mantissa bits
-              const float v = __uint_as_float(r[i]) + 12582912.0f;
-              H[16 * j + i] += (int)(__float_as_uint(v) - 0x4B400000u);
+              // an exact integer of magnitude <= 2^24: converted exactly
+              H[16 * j + i] += (long long)__float2int_rn(__uint_as_float(r[i]));
             }
           }
           tc_fence_before();

@@ -41,6 +41,9 @@ def main():
     ap.add_argument("--u1", action="store_true")
     ap.add_argument("--tdvp", action="store_true")
     ap.add_argument("--tdvp-L", type=int, default=32)
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the tcgen05 GEMMs pick their tile width by timing (off by default: "
+                         "timings under a profiler are distorted; 256 columns)")
     ap.add_argument("--identity", action="store_true",
                     help="environments of a canonical MPS: L's last and R's first channel the "
                          "unit matrix (left out of the GEMMs, with identity skipping 'always')")
@@ -58,6 +61,7 @@ def main():
 
     dev = torch.device("cuda:0")
     ctx = B.Context(0)
+    ctx.set_autotune(args.autotune)
     chi, d, w = args.chi, args.d, args.w
     W = hamiltonians.xxz(8, 1.0, 1.0, 0.0)[3] if (d, w) == (2, 5) else \
         np.random.default_rng(3).standard_normal((w, d, d, w))
