@@ -49,7 +49,11 @@ def _xxz_operator(L, k, chi, seed):
 
 
 def _both(ctx, run):
-    """run() -> (result tuple, output tensor); once per driver."""
+    """run() -> (result tuple, output tensor); once per driver, after one
+    untimed run (the first product of a size class times the GEMM tile
+    widths, launches that neither driver repeats)."""
+    run()
+    torch.cuda.synchronize()
     out = {}
     for mode in ("host", "graph"):
         ctx.set_lanczos_mode(mode)
