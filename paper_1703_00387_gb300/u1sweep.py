@@ -162,11 +162,16 @@ class Copy:
 
 class DeviceExecutor:
     """Runs operation records on the GPU through the library (buffers are
-    float64 CUDA tensors)."""
+    float64 CUDA tensors). eig_workers: how many sector eigensolves of a
+    split may run at once (1: one after another on ctx); eig_solver: the
+    eigensolver route of the worker contexts ('auto' when None)."""
 
-    def __init__(self, ctx):
+    def __init__(self, ctx, eig_workers=8, eig_solver=None):
         import torch
         self.ctx, self.torch = ctx, torch
+        self.eig_workers, self.eig_solver = int(eig_workers), eig_solver
+        self._pool = None
+        self._sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
     def empty(self, n):
         return self.torch.empty(max(int(n), 1), dtype=self.torch.float64, device="cuda")
@@ -203,6 +208,58 @@ class DeviceExecutor:
         Y = self.empty(nev * n)
         ev = B.osmps_sym_eig_top(self.ctx, G[: n * n].view(n, n), nev, Y[: nev * n].view(nev, n))
         return ev, Y
+
+    def eig_top_many(self, jobs):
+        """eig_top for every (G, n, nev) of jobs: the sectors of one split are
+        independent, so up to eig_workers of them run at once, each on a
+        worker thread with its own context and stream. The Householder panels
+        of this library's eigensolver are cooperative launches of
+        min(SMs, n / 8) blocks from n = 64 on, which must all be resident: the
+        solves running together are kept within one block per SM. Largest
+        first, as the sectors' costs differ the most."""
+        if self.eig_workers <= 1 or len(jobs) <= 1:
+            return [self.eig_top(*j) for j in jobs]
+        import threading
+        from concurrent.futures import ThreadPoolExecutor
+        if self._pool is None:
+            self._tls = threading.local()
+            self._cond = threading.Condition()
+            self._busy = [0]
+            self._pool = ThreadPoolExecutor(max_workers=self.eig_workers)
+        budget = self._sms
+        torch = self.torch
+        ready = torch.cuda.Event()
+        ready.record()  # the Gram matrices, written on this thread's stream
+
+        def blocks(n):
+            return 0 if n < 64 else max(1, min(budget, 160, (n + 7) // 8))
+
+        def run(job):
+            G, n, nev = job
+            tl = self._tls
+            if not hasattr(tl, "ctx"):
+                tl.ctx = B.Context(self.ctx.device)
+                if self.eig_solver is not None:
+                    tl.ctx.set_eig_solver(self.eig_solver)
+                tl.stream = torch.cuda.Stream()
+            need = blocks(n)
+            with self._cond:
+                self._cond.wait_for(lambda: self._busy[0] + need <= budget)
+                self._busy[0] += need
+            try:
+                tl.stream.wait_event(ready)
+                Y = torch.empty(max(nev * n, 1), dtype=torch.float64, device="cuda")
+                ev = B.osmps_sym_eig_top(tl.ctx, G[: n * n].view(n, n), nev, Y[: nev * n].view(nev, n),
+                                         stream=tl.stream)  # synchronises tl.stream
+                return ev, Y
+            finally:
+                with self._cond:
+                    self._busy[0] -= need
+                    self._cond.notify_all()
+
+        order = sorted(range(len(jobs)), key=lambda i: -jobs[i][1])
+        futures = {i: self._pool.submit(run, jobs[i]) for i in order}
+        return [futures[i].result() for i in range(len(jobs))]
 
     def upload(self, a):
         return self.torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to("cuda")
@@ -396,7 +453,7 @@ def split(ex, theta, layt, left, right, d1, d2, move_right, chi_max, eps_local):
     tr = ex.norm2(theta, layt.size)
     if not (tr > 0.0) or not np.isfinite(tr):
         raise B.OsmpsError(B.ENAN, "u1 split: theta has zero or non-finite norm")
-    spectra, vecs, rank = [], {}, 0
+    spectra, vecs, rank, jobs = [], {}, 0, []
     for q, g in sorted(groups.items()):
         n, Wq = g["n"], g["W"]
         gdim = n if move_right else Wq          # Gram of the rows (L->R) or columns (R->L)
@@ -417,7 +474,9 @@ def split(ex, theta, layt, left, right, d1, d2, move_right, chi_max, eps_local):
                      (theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1, left.m[i])
                 for (i, s1, r0) in g["rows"]]))
         ex.products(ops)
-        ev, Y = ex.eig_top(G, gdim, nev)
+        jobs.append((q, G, gdim, nev))
+    results = ex.eig_top_many([(G, gdim, nev) for (_, G, gdim, nev) in jobs])
+    for (q, _, gdim, nev), (ev, Y) in zip(jobs, results):
         vecs[q] = (Y, gdim, nev)
         for c in range(nev):  # c-th largest of the sector: row nev - 1 - c of Y
             spectra.append((float(ev[nev - 1 - c]), q, c))

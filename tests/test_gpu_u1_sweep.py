@@ -94,6 +94,30 @@ def test_truncated_sweep_keeps_chi_max_and_bounds_the_energy(ctx):
     _check_state(mps, Wo, N, res)
 
 
+def test_concurrent_sector_eigensolves_match_sequential(ctx):
+    """The split's sector eigensolves on four worker contexts at once (the
+    Householder panels of the larger sectors as concurrent cooperative
+    launches) give the same sweep as one after another on one context."""
+    L, nmax, N = 16, 3, 16
+    W = hamiltonians.bose_hubbard(L, 1.0, 4.0, nmax)
+    runs = []
+    for workers in (1, 4):
+        ex = us.DeviceExecutor(ctx, eig_workers=workers)
+        sizes = []
+        many = ex.eig_top_many
+        ex.eig_top_many = lambda jobs, many=many, sizes=sizes: (sizes.extend(j[1] for j in jobs),
+                                                                many(jobs))[1]
+        mps = us.random_u1_mps(ex, L, nmax + 1, N, chi=32, seed=7)
+        res = us.u1_sweep(mps, W, n_sweeps=2, chi_max=96, eps_local=0.0, precision="tf32x3",
+                          lanczos_tol=1e-10, lanczos_max_iter=60)
+        assert max(sizes) >= 64  # some sectors take the cooperative route
+        runs.append((res["energy"], res["max_discarded"], [b.dim for b in mps.bonds],
+                     [b.m.tolist() for b in mps.bonds]))
+    (e1, d1, dims1, m1), (e4, d4, dims4, m4) = runs
+    assert dims1 == dims4 and m1 == m4
+    assert abs(e1 - e4) <= 1e-12 * abs(e1) and abs(d1 - d4) <= 1e-12 + 1e-9 * d1
+
+
 def test_gemm_grouped_matches_numpy(ctx):
     """Grouped products on strided views: several terms per output (K
     ragged across 16-wide steps), transposed and reversed (negative-stride)

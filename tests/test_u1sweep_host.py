@@ -48,6 +48,9 @@ class NumpyExecutor:
         w, v = np.linalg.eigh(G[: n * n].reshape(n, n))
         return w[n - nev:], np.ascontiguousarray(v[:, n - nev:].T).ravel()
 
+    def eig_top_many(self, jobs):
+        return [self.eig_top(*j) for j in jobs]
+
     def upload(self, a):
         return np.array(a, dtype=np.float64).ravel()
 
