@@ -345,45 +345,58 @@ def truncation(values, tr, chi_max, eps_local, rank):
     return order[:keep], max(1.0 - kept, 0.0), float(-(p * np.log(p)).sum())
 
 
+def _nonzero_w(W, group):
+    """Nonzero entries of W[w, t, s, w2] as lists of (key..., value) grouped
+    by the axes in `group`, each list in C order of the remaining axes."""
+    out = {}
+    for idx in zip(*np.nonzero(W)):
+        idx = tuple(int(x) for x in idx)
+        key = tuple(idx[a] for a in group)
+        rest = tuple(idx[a] for a in range(4) if a not in group)
+        out.setdefault(key, []).append(rest + (float(W[idx]),))
+    return out
+
+
+def _scratch(X, n):
+    """X itself, or X(n) when X is an allocator."""
+    return X(n) if callable(X) else X
+
+
 def env_left_ops(Lold, elo, A, lay, Lnew, eln, W, left, mid, X):
     """L_new[b', w', b] = sum A[a', t, b'] L_old[a', w, a] W[w, t, s, w'] A[a, s, b]
     in two grouped stages: X(i2, w) = L_old(i2, w) A(i), all s at once (one
     product per bra sector i2 and channel w), then one product per block
     (j2, w') of L_new whose terms are W[w, t, s, w'] A(i2, t)^T X(i2, w)[s]
     over every nonzero W entry and sector pair that reaches it (blocks with
-    no term are zeroed). X: scratch buffer. Returns (stage-1 products,
-    stage-2 products, X elements needed)."""
-    s1_ops, xoff, off = [], {}, 0
-    d = lay.col_off.shape[1]
+    no term are zeroed). X: scratch buffer, or a function that allocates one
+    of the size it is given. Returns (stage-1 products, stage-2 products, X
+    elements needed)."""
+    xoff, off = [], 0
     for i2 in range(len(left.q)):
         for w in range(elo.ket.shape[1]):
-            i = elo.ket[i2, w]
+            i = int(elo.ket[i2, w])
             if i < 0 or lay.row_len[i] == 0:
                 continue
-            xoff[(i2, w)] = off
-            s1_ops.append(Product((X, off), lay.row_len[i], 1, left.m[i2], lay.row_len[i],
-                                  terms=[Term((Lold, elo.row_off[i2] + elo.col_off[i2, w]), elo.row_len[i2], 1,
-                                              (A, lay.row_off[i]), lay.row_len[i], 1, left.m[i])]))
+            xoff.append((i2, w, i, off))
             off += int(left.m[i2] * lay.row_len[i])
+    X = _scratch(X, off)
+    s1_ops = [Product((X, xo), lay.row_len[i], 1, left.m[i2], lay.row_len[i],
+                      terms=[Term((Lold, elo.row_off[i2] + elo.col_off[i2, w]), elo.row_len[i2], 1,
+                                  (A, lay.row_off[i]), lay.row_len[i], 1, left.m[i])])
+              for (i2, w, i, xo) in xoff]
+    nzw = _nonzero_w(W, (0,))  # per w: (t, s, w2, value); ordered by s below
+    by_w = {w: sorted(v, key=lambda e: (e[1], e[0], e[2])) for (w,), v in nzw.items()}
+    rs, co, rl, ro = lay.right_sector, lay.col_off, lay.row_len, lay.row_off
     blocks = {}
-    for (i2, w), xo in xoff.items():
-        i = elo.ket[i2, w]
-        for s in range(d):
-            j = lay.right_sector[i, s]
-            if j < 0:
+    for (i2, w, i, xo) in xoff:
+        m2 = left.m[i2]
+        for (t, s_, w2, val) in by_w.get(w, ()):
+            j, j2 = rs[i, s_], rs[i2, t]
+            if j < 0 or j2 < 0:
                 continue
-            for t in range(d):
-                j2 = lay.right_sector[i2, t]
-                if j2 < 0:
-                    continue
-                for w2 in range(W.shape[3]):
-                    val = W[w, t, s, w2]
-                    if val == 0.0:
-                        continue
-                    assert eln.ket[j2, w2] == j
-                    blocks.setdefault((j2, w2), []).append(
-                        Term((A, lay.row_off[i2] + lay.col_off[i2, t]), 1, lay.row_len[i2],
-                             (X, xo + lay.col_off[i, s]), lay.row_len[i], 1, left.m[i2], alpha=val))
+            assert eln.ket[j2, w2] == j
+            blocks.setdefault((int(j2), w2), []).append(
+                Term((A, ro[i2] + co[i2, t]), 1, rl[i2], (X, xo + co[i, s_]), rl[i], 1, m2, alpha=val))
     s2_ops = []
     for j2 in range(len(mid.q)):
         for w2 in range(eln.ket.shape[1]):
@@ -400,38 +413,46 @@ def env_right_ops(Rold, ero, A, lay, Rnew, ern, W, mid, right, Z):
     in two grouped stages: Z(j, s, jc2, w2) = A(j, s) R_old(jc2, w2)^T, then
     one product per block (j2, w) of R_new whose terms are
     W[w, t, s, w2] A(j2, t) Z(j, s, jc2, w2)^T (blocks with no term are
-    zeroed)."""
-    s1_ops, zoff, off = [], {}, 0
+    zeroed). Z: scratch buffer, or a function that allocates one of the size
+    it is given."""
+    # the (jc2, w2) pairs of R_old whose ket sector is jc, in C order
+    by_ket = {}
+    for jc2 in range(len(right.q)):
+        for w2 in range(ero.ket.shape[1]):
+            if ero.ket[jc2, w2] >= 0:
+                by_ket.setdefault(int(ero.ket[jc2, w2]), []).append((jc2, w2))
+    zoff, off = [], 0
     d = lay.col_off.shape[1]
     for j in range(len(mid.q)):
-        for s in range(d):
-            jc = lay.right_sector[j, s]
+        for s_ in range(d):
+            jc = int(lay.right_sector[j, s_])
             if jc < 0:
                 continue
-            for jc2 in range(len(right.q)):
-                for w2 in range(ero.ket.shape[1]):
-                    if ero.ket[jc2, w2] != jc:
-                        continue
-                    zoff[(j, s, jc2, w2)] = off
-                    s1_ops.append(Product((Z, off), right.m[jc2], 1, mid.m[j], right.m[jc2],
-                                          terms=[Term((A, lay.row_off[j] + lay.col_off[j, s]), lay.row_len[j], 1,
-                                                      (Rold, ero.row_off[jc2] + ero.col_off[jc2, w2]), 1,
-                                                      ero.row_len[jc2], right.m[jc])]))
-                    off += int(mid.m[j] * right.m[jc2])
+            for (jc2, w2) in by_ket.get(jc, ()):
+                zoff.append((j, s_, jc, jc2, w2, off))
+                off += int(mid.m[j] * right.m[jc2])
+    Z = _scratch(Z, off)
+    s1_ops = [Product((Z, zo), right.m[jc2], 1, mid.m[j], right.m[jc2],
+                      terms=[Term((A, lay.row_off[j] + lay.col_off[j, s_]), lay.row_len[j], 1,
+                                  (Rold, ero.row_off[jc2] + ero.col_off[jc2, w2]), 1,
+                                  ero.row_len[jc2], right.m[jc])])
+              for (j, s_, jc, jc2, w2, zo) in zoff]
+    nzw = _nonzero_w(W, (2, 3))  # per (s, w2): (w, t, value); ordered by t below
+    by_sw = {k: sorted(v, key=lambda e: (e[1], e[0])) for k, v in nzw.items()}
+    rs, co, rl, ro = lay.right_sector, lay.col_off, lay.row_len, lay.row_off
     blocks = {}
-    for (j, s, jc2, w2), zo in zoff.items():
-        for t in range(d):
-            j2 = mid.find(right.q[jc2] - t)
-            if j2 < 0 or lay.right_sector[j2, t] != jc2:
+    for (j, s_, jc, jc2, w2, zo) in zoff:
+        terms = by_sw.get((s_, w2))
+        if not terms:
+            continue
+        qc2, mc2 = right.q[jc2], right.m[jc2]
+        for (w, t, val) in terms:
+            j2 = mid.find(qc2 - t)
+            if j2 < 0 or rs[j2, t] != jc2:
                 continue
-            for w in range(W.shape[0]):
-                val = W[w, t, s, w2]
-                if val == 0.0:
-                    continue
-                assert ern.ket[j2, w] == j
-                blocks.setdefault((j2, w), []).append(
-                    Term((A, lay.row_off[j2] + lay.col_off[j2, t]), lay.row_len[j2], 1,
-                         (Z, zo), 1, right.m[jc2], right.m[jc2], alpha=val))
+            assert ern.ket[j2, w] == j
+            blocks.setdefault((j2, w), []).append(
+                Term((A, ro[j2] + co[j2, t]), rl[j2], 1, (Z, zo), 1, mc2, mc2, alpha=val))
     s2_ops = []
     for j2 in range(len(mid.q)):
         for w in range(ern.ket.shape[1]):
@@ -453,7 +474,7 @@ def split(ex, theta, layt, left, right, d1, d2, move_right, chi_max, eps_local):
     tr = ex.norm2(theta, layt.size)
     if not (tr > 0.0) or not np.isfinite(tr):
         raise B.OsmpsError(B.ENAN, "u1 split: theta has zero or non-finite norm")
-    spectra, vecs, rank, jobs = [], {}, 0, []
+    vecs, jobs, ops = {}, [], []
     for q, g in sorted(groups.items()):
         n, Wq = g["n"], g["W"]
         gdim = n if move_right else Wq          # Gram of the rows (L->R) or columns (R->L)
@@ -461,7 +482,6 @@ def split(ex, theta, layt, left, right, d1, d2, move_right, chi_max, eps_local):
         if nev < 1:
             continue
         G = ex.empty(gdim * gdim)
-        ops = []
         if move_right:   # G[g, g'] = theta_g theta_g'^T
             for (i, s1, r0) in g["rows"]:
                 for (i2, s2, r2) in g["rows"]:
@@ -473,18 +493,23 @@ def split(ex, theta, layt, left, right, d1, d2, move_right, chi_max, eps_local):
                 Term((theta, layt.row_off[i] + layt.col_off[i, s1]), 1, layt.row_len[i],
                      (theta, layt.row_off[i] + layt.col_off[i, s1]), layt.row_len[i], 1, left.m[i])
                 for (i, s1, r0) in g["rows"]]))
-        ex.products(ops)
         jobs.append((q, G, gdim, nev))
+    if not jobs:
+        raise B.OsmpsError(B.ESHAPE, "u1 split: no middle sector carries a state")
+    ex.products(ops)  # every sector's Gram matrix in one grouped launch
     results = ex.eig_top_many([(G, gdim, nev) for (_, G, gdim, nev) in jobs])
+    # the joint spectrum: sector by sector (ascending charge), largest first
+    # within a sector (the c-th largest is row nev - 1 - c of Y)
+    vals, qs = [], []
     for (q, _, gdim, nev), (ev, Y) in zip(jobs, results):
         vecs[q] = (Y, gdim, nev)
-        for c in range(nev):  # c-th largest of the sector: row nev - 1 - c of Y
-            spectra.append((float(ev[nev - 1 - c]), q, c))
-        rank += nev
-    keep_idx, discarded, entropy = truncation([x[0] for x in spectra], tr, chi_max, eps_local, rank)
-    kq = {}
-    for t in keep_idx:
-        kq[spectra[t][1]] = kq.get(spectra[t][1], 0) + 1
+        vals.append(np.asarray(ev[:nev], dtype=np.float64)[::-1])
+        qs.append(np.full(nev, q, dtype=np.int64))
+    vals, qs = np.concatenate(vals), np.concatenate(qs)
+    rank = len(vals)
+    keep_idx, discarded, entropy = truncation(vals, tr, chi_max, eps_local, rank)
+    kept_q, kept_n = np.unique(qs[keep_idx], return_counts=True)
+    kq = {int(q): int(c) for q, c in zip(kept_q, kept_n)}
     mid = Bond(sorted(kq), [kq[q] for q in sorted(kq)])
     lay1, lay2 = MpsLayout(left, mid, d1), MpsLayout(mid, right, d2)
     A1, A2 = ex.empty(lay1.size), ex.empty(lay2.size)
@@ -630,9 +655,7 @@ def u1_sweep(mps, W, n_sweeps=1, chi_max=64, eps_local=0.0, precision="tf32x3",
         left, mid = mps.bonds[k], mps.bonds[k + 1]
         elo, eln = EnvLayout(left, qw[k]), EnvLayout(mid, qw[k + 1])
         Ln = ex.empty(eln.size)
-        s1, s2, nx = env_left_ops(Lk, elo, mps.A[k], mps.layout(k), Ln, eln, W[k], left, mid, None)
-        X = ex.empty(nx)
-        s1, s2, _ = env_left_ops(Lk, elo, mps.A[k], mps.layout(k), Ln, eln, W[k], left, mid, X)
+        s1, s2, _ = env_left_ops(Lk, elo, mps.A[k], mps.layout(k), Ln, eln, W[k], left, mid, ex.empty)
         ex.products(s1)
         ex.products(s2)
         return Ln
@@ -641,9 +664,7 @@ def u1_sweep(mps, W, n_sweeps=1, chi_max=64, eps_local=0.0, precision="tf32x3",
         mid, right = mps.bonds[k], mps.bonds[k + 1]
         ero, ern = EnvLayout(right, qw[k + 1]), EnvLayout(mid, qw[k])
         Rn = ex.empty(ern.size)
-        _, _, nz = env_right_ops(Rk1, ero, mps.A[k], mps.layout(k), Rn, ern, W[k], mid, right, None)
-        Z = ex.empty(nz)
-        s1, s2, _ = env_right_ops(Rk1, ero, mps.A[k], mps.layout(k), Rn, ern, W[k], mid, right, Z)
+        s1, s2, _ = env_right_ops(Rk1, ero, mps.A[k], mps.layout(k), Rn, ern, W[k], mid, right, ex.empty)
         ex.products(s1)
         ex.products(s2)
         return Rn
