@@ -395,21 +395,27 @@ __global__ void __launch_bounds__(NT) k_trtri_upper(const double* __restrict__ U
   for (int i = c; i >= 1; --i) {
     const double xi = sx[i & 1];
     double unext[RPT];
+    // a warp whose rows in slot k are all >= i has nothing left to do there
+    // (x_r is final once the step passes r): the test is the same for every
+    // lane of the warp, so such warps skip the float64 instructions instead of
+    // issuing them with every lane masked off
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       const int r = t + NT * k;
-      unext[k] = r < i - 1 ? U[(int64_t)(i - 1) * m + r] : 0.0;
+      unext[k] = (t & ~31) + NT * k < i - 1 && r < i - 1 ? U[(int64_t)(i - 1) * m + r] : 0.0;
     }
     const double rnext = rd[i - 1];
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
       const int r = t + NT * k;
-      if (r < i) xr[k] = fma(-ucur[k], xi, xr[k]);
-      if (r == i - 1) {
-        xr[k] *= rnext;
-        sx[(i - 1) & 1] = xr[k];
+      if ((t & ~31) + NT * k < i) {
+        if (r < i) xr[k] = fma(-ucur[k], xi, xr[k]);
+        if (r == i - 1) {
+          xr[k] *= rnext;
+          sx[(i - 1) & 1] = xr[k];
+        }
+        ucur[k] = unext[k];
       }
-      ucur[k] = unext[k];
     }
     __syncthreads();
   }

@@ -187,21 +187,42 @@ __global__ void __launch_bounds__(ST_THREADS, 1) k_sytrd_panel(SytrdArgs a) {
       a.Vp[(size_t)jj * n + r] = v;
       sV[loc][jj] = v;
     }
-    // t = A22 v on this block's rows, one warp per row, four partial sums
+    // t = A22 v on this block's rows, one warp per row. The row is read from
+    // L2 in 16-byte pairs, eight per lane in flight (the loop is bound by the
+    // latency of these loads, not by the float64 pipe): element j+1 alone when
+    // its address is not 16-byte aligned, then pairs, then a last odd element.
     if (j < n - 1) {
       for (int loc = warp; loc < cnt; loc += ST_WARPS) {
         const int r = b + G * loc;
         if (r < j + 1) continue;
         const double* row = a.A + (size_t)r * n;
+        const int k1 = j + 1;
+        const int ka = k1 + (int)((reinterpret_cast<uintptr_t>(row + k1) >> 3) & 1);  // 16-byte aligned
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int k = j + 1 + lane;
-        for (; k + 96 < n; k += 128) {
-          s0 = fma(row[k], sv[k], s0);
-          s1 = fma(row[k + 32], sv[k + 32], s1);
-          s2 = fma(row[k + 64], sv[k + 64], s2);
-          s3 = fma(row[k + 96], sv[k + 96], s3);
+        if (lane == 0 && ka > k1) s0 = row[k1] * sv[k1];
+        const int np2 = ka < n ? (n - ka) >> 1 : 0;  // pairs (ka + 2p, ka + 2p + 1)
+        const double2* row2 = reinterpret_cast<const double2*>(row + ka);
+        const double* svp = sv + ka;
+        int p = lane;
+        for (; p + 224 < np2; p += 256) {
+          double2 x[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) x[u] = row2[p + 32 * u];
+#pragma unroll
+          for (int u = 0; u < 8; u += 2) {
+            const int k = 2 * (p + 32 * u);
+            s0 = fma(x[u].x, svp[k], s0);
+            s1 = fma(x[u].y, svp[k + 1], s1);
+            s2 = fma(x[u + 1].x, svp[k + 64], s2);
+            s3 = fma(x[u + 1].y, svp[k + 65], s3);
+          }
         }
-        for (; k < n; k += 32) s0 = fma(row[k], sv[k], s0);
+        for (; p < np2; p += 32) {
+          const double2 x = row2[p];
+          s0 = fma(x.x, svp[2 * p], s0);
+          s1 = fma(x.y, svp[2 * p + 1], s1);
+        }
+        if (lane == 1 && ka < n && ((n - ka) & 1)) s2 = fma(row[n - 1], sv[n - 1], s2);
         const double tr = warp_sum((s0 + s1) + (s2 + s3));
         if (lane == 0) {
           st[loc] = tr;

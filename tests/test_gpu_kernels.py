@@ -337,16 +337,20 @@ def test_split_eigensolvers(ctx, solver, move_right, spectrum, shape, chi_max):
         assert od.right_isometry_defect(b) < 1e-12
 
 
-@pytest.mark.parametrize("n", [2, 37, 300, 1000])
-def test_sytrd_matches_lapack(ctx, n):
+@pytest.mark.parametrize("n,offset", [(2, 0), (37, 0), (300, 0), (301, 1), (1000, 0)])
+def test_sytrd_matches_lapack(ctx, n, offset):
     """osmps_sytrd (cooperative panels + emulated-GEMM trailing updates)
     against LAPACK dsytrd: Q^T G Q = T with Q rebuilt from the stored
-    reflectors, the spectrum of T, and d, e, tau (same reflector convention)."""
+    reflectors, the spectrum of T, and d, e, tau (same reflector convention).
+    offset 1: the matrix starts 8 bytes past a 16-byte boundary, so every row
+    of an odd n begins on the other parity for the panel's paired loads."""
     from scipy.linalg import lapack
     rng = np.random.default_rng(n)
     M = rng.standard_normal((n, n))
     G = M @ M.T
-    A = dev(G.copy())
+    A = torch.empty(n * n + offset, dtype=torch.float64, device="cuda:0")[offset:].view(n, n)
+    A.copy_(dev(G.copy()))
+    assert (A.data_ptr() % 16 == 8) == bool(offset)
     d = torch.empty(n, dtype=torch.float64, device="cuda:0")
     e = torch.empty(max(n - 1, 1), dtype=torch.float64, device="cuda:0")
     tau = torch.empty(max(n - 1, 1), dtype=torch.float64, device="cuda:0")
