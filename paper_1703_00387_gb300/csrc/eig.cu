@@ -197,10 +197,18 @@ __device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t a, uint64
 // superdiagonal of U, the multiplier and whether rows i, i+1 were swapped (a
 // swap puts e[i+1] on the second superdiagonal, so that needs no storage).
 // Work arrays are interleaved across eigenvalues (W[i * nev + j]) so that
-// neighbouring threads touch neighbouring addresses.
+// neighbouring threads touch neighbouring addresses. The two sweeps of each
+// solve carry a dependence chain of one or three float64 operations per row,
+// and the row's stored factors come from L2: they are loaded IV_AHEAD rows at
+// a time into registers before that chunk's chain runs, so the chain does not
+// wait for one load round trip per row. (The arithmetic and its order are
+// those of the plain row loop.)
+constexpr int IV_AHEAD = 8;
+
 __global__ void k_inviter(const double* __restrict__ d, const double* __restrict__ e, int n,
                           int nev, const double* __restrict__ ev,
-                          const double* __restrict__ bounds, double* __restrict__ W,
+                          const double* __restrict__ bounds, double* __restrict__ rcp,
+                          double* __restrict__ mu, double* __restrict__ ml, double* __restrict__ x,
                           unsigned char* __restrict__ piv, double* __restrict__ Z, uint64_t seed) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nev) return;
@@ -218,10 +226,8 @@ __global__ void k_inviter(const double* __restrict__ d, const double* __restrict
     return;
   }
   const int64_t ld = nev;
-  double* rcp = W;                        // 1 / pivot of row i (tiny pivots replaced)
-  double* mu = W + (int64_t)n * ld;       // first superdiagonal of U
-  double* ml = W + 2 * (int64_t)n * ld;   // multipliers
-  double* x = W + 3 * (int64_t)n * ld;    // right-hand side / solution
+  // rcp: 1 / pivot of row i (tiny pivots replaced); mu: first superdiagonal
+  // of U; ml: multipliers; x: right-hand side / solution
 #define AT(a, i) a[(int64_t)(i) * ld + j]
   auto store_pivot = [&](int i, double p) {
     if (fabs(p) < tiny) p = p < 0.0 ? -tiny : tiny;  // a zero (or tiny) pivot becomes a tiny one
@@ -252,9 +258,32 @@ __global__ void k_inviter(const double* __restrict__ d, const double* __restrict
   }
   store_pivot(n - 1, di);
   for (int pass = 0; pass < 2; ++pass) {
-    // forward: the row swaps and multipliers applied to the right-hand side
+    // forward: the row swaps and multipliers applied to the right-hand side;
+    // row i reads x[i+1] (the previous solve, or the start vector) before row
+    // i+1 overwrites it, as in the plain loop
     double xi = pass == 0 ? hash_uniform(seed, (uint64_t)j, 0) : AT(x, 0);
-    for (int i = 0; i + 1 < n; ++i) {
+    int i = 0;
+    for (; i + IV_AHEAD < n; i += IV_AHEAD) {
+      double fq[IV_AHEAD], xq[IV_AHEAD];
+      unsigned char pq[IV_AHEAD];
+#pragma unroll
+      for (int u = 0; u < IV_AHEAD; ++u) {
+        fq[u] = AT(ml, i + u);
+        pq[u] = AT(piv, i + u);
+        xq[u] = pass == 0 ? hash_uniform(seed, (uint64_t)j, (uint64_t)(i + u + 1)) : AT(x, i + u + 1);
+      }
+#pragma unroll
+      for (int u = 0; u < IV_AHEAD; ++u) {
+        if (pq[u] == 0) {
+          AT(x, i + u) = xi;
+          xi = fma(-fq[u], xi, xq[u]);
+        } else {
+          AT(x, i + u) = xq[u];
+          xi = fma(-fq[u], xq[u], xi);
+        }
+      }
+    }
+    for (; i + 1 < n; ++i) {
       const double xn = pass == 0 ? hash_uniform(seed, (uint64_t)j, (uint64_t)(i + 1)) : AT(x, i + 1);
       const double f = AT(ml, i);
       if (AT(piv, i) == 0) {
@@ -268,21 +297,47 @@ __global__ void k_inviter(const double* __restrict__ d, const double* __restrict
     AT(x, n - 1) = xi;
     // back substitution with U (second superdiagonal e[i+1] where rows swapped)
     double x1 = 0.0, x2 = 0.0, nrm = 0.0;
-    for (int i = n - 1; i >= 0; --i) {
-      double v = AT(x, i);
-      if (i + 1 < n) v = fma(-AT(mu, i), x1, v);
-      if (i + 2 < n && AT(piv, i)) v = fma(-e[i + 1], x2, v);
-      v *= AT(rcp, i);
-      AT(x, i) = v;
+    int r = n - 1;
+    for (; r + 1 >= IV_AHEAD; r -= IV_AHEAD) {  // rows r, r-1, .., r-IV_AHEAD+1 (all >= 0)
+      double vq[IV_AHEAD], mq[IV_AHEAD], eq[IV_AHEAD], rq[IV_AHEAD];
+      unsigned char pq[IV_AHEAD];
+#pragma unroll
+      for (int u = 0; u < IV_AHEAD; ++u) {
+        const int ii = r - u;
+        vq[u] = AT(x, ii);
+        mq[u] = ii + 1 < n ? AT(mu, ii) : 0.0;
+        pq[u] = ii + 2 < n ? AT(piv, ii) : 0;
+        eq[u] = ii + 2 < n ? e[ii + 1] : 0.0;
+        rq[u] = AT(rcp, ii);
+      }
+#pragma unroll
+      for (int u = 0; u < IV_AHEAD; ++u) {
+        const int ii = r - u;
+        double v = vq[u];
+        if (ii + 1 < n) v = fma(-mq[u], x1, v);
+        if (pq[u]) v = fma(-eq[u], x2, v);
+        v *= rq[u];
+        AT(x, ii) = v;
+        nrm = fma(v, v, nrm);
+        x2 = x1;
+        x1 = v;
+      }
+    }
+    for (; r >= 0; --r) {
+      double v = AT(x, r);
+      if (r + 1 < n) v = fma(-AT(mu, r), x1, v);
+      if (r + 2 < n && AT(piv, r)) v = fma(-e[r + 1], x2, v);
+      v *= AT(rcp, r);
+      AT(x, r) = v;
       nrm = fma(v, v, nrm);
       x2 = x1;
       x1 = v;
     }
     const double sc = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
     if (pass == 0)
-      for (int i = 0; i < n; ++i) AT(x, i) *= sc;
+      for (int k = 0; k < n; ++k) AT(x, k) *= sc;
     else
-      for (int i = 0; i < n; ++i) Z[(int64_t)i * nev + col] = AT(x, i) * sc;
+      for (int k = 0; k < n; ++k) Z[(int64_t)k * nev + col] = AT(x, k) * sc;
   }
 #undef AT
 }
@@ -560,7 +615,8 @@ osmps_status eig_top(osmps_ctx* ctx, double* G, int64_t n, int64_t nev, double* 
   if (!Z) return st;
   double* Z2 = Z + n * nev;
   // 8 eigenvalues per block: the sequential chains spread over the SMs
-  { k_inviter<<<(int)cdiv(nev, 8), 8, 0, s>>>(dvec, evec, (int)n, (int)nev, ev, bounds, Wk, pivk,
+  { k_inviter<<<(int)cdiv(nev, 8), 8, 0, s>>>(dvec, evec, (int)n, (int)nev, ev, bounds, Wk,
+                                              Wk + n * nev, Wk + 2 * n * nev, Wk + 3 * n * nev, pivk,
                                               Z, 0x5DEECE66Dull); note_launch(); }
   OSMPS_LAUNCH_CHECK();
   const int64_t mbmax = std::min<int64_t>(WY, n - 1);
