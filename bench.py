@@ -713,6 +713,8 @@ def u1_sweep_leg(B, ctx, args):
                     "max_chi": r["max_chi"], "max_discarded": r["max_discarded"],
                     "middle_bond_sectors": len(mps.bonds[L // 2].q),
                     "gpu_launches": B.osmps_kernel_launches() - l0}
+    out["eig_workers"] = ex.eig_workers
+    ex.close()
     return out
 
 

@@ -225,6 +225,7 @@ class DeviceExecutor:
             self._tls = threading.local()
             self._cond = threading.Condition()
             self._busy = [0]
+            self._workers = []  # (context, stream) of every worker thread
             self._pool = ThreadPoolExecutor(max_workers=self.eig_workers)
         budget = self._sms
         torch = self.torch
@@ -242,6 +243,8 @@ class DeviceExecutor:
                 if self.eig_solver is not None:
                     tl.ctx.set_eig_solver(self.eig_solver)
                 tl.stream = torch.cuda.Stream()
+                with self._cond:
+                    self._workers.append((tl.ctx, tl.stream))
             need = blocks(n)
             with self._cond:
                 self._cond.wait_for(lambda: self._busy[0] + need <= budget)
@@ -260,6 +263,15 @@ class DeviceExecutor:
         order = sorted(range(len(jobs)), key=lambda i: -jobs[i][1])
         futures = {i: self._pool.submit(run, jobs[i]) for i in order}
         return [futures[i].result() for i in range(len(jobs))]
+
+    def close(self):
+        """Stop the eigensolve workers and release their contexts."""
+        if self._pool is not None:
+            self._pool.shutdown(wait=True)
+            for c, st in self._workers:
+                st.synchronize()
+                c.close()
+            self._pool, self._workers = None, []
 
     def upload(self, a):
         return self.torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to("cuda")

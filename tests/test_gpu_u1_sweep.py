@@ -113,6 +113,7 @@ def test_concurrent_sector_eigensolves_match_sequential(ctx):
         assert max(sizes) >= 64  # some sectors take the cooperative route
         runs.append((res["energy"], res["max_discarded"], [b.dim for b in mps.bonds],
                      [b.m.tolist() for b in mps.bonds]))
+        ex.close()
     (e1, d1, dims1, m1), (e4, d4, dims4, m4) = runs
     assert dims1 == dims4 and m1 == m4
     assert abs(e1 - e4) <= 1e-12 * abs(e1) and abs(d1 - d4) <= 1e-12 + 1e-9 * d1
