@@ -665,7 +665,10 @@ def u1_leg(B, ctx, args):
         ms = e0.elapsed_time(e1) / reps
         prep_ms = p0.elapsed_time(p1)
         prof = B.osmps_profile_read(ctx, "gemm_tc")
+        wst = B.osmps_profile_read(ctx, "u1_wstep")  # "flops" = algorithmic bytes
         B.osmps_profile_enable(ctx, False)
+        peaks, peak_src = load_peaks()
+        w_gbs = wst["flops"] / (wst["ms"] / 1e3) / 1e9 if wst["ms"] > 0 else None
         dense = 2.0 * 25 * 512 * 512 * (4 * 512 + 4 * 512)
         out[prec] = {"ms_per_product": ms, "prepare_ms": prep_ms,
                      "block_gemm_tflops": pl.flops / (ms / 1e3) / 1e12,
@@ -674,7 +677,17 @@ def u1_leg(B, ctx, args):
                      "grouped_gemm_launches": prof["launches"],
                      "grouped_gemm_issued_tflops": (prof["tensor_flops"] / (prof["ms"] / 1e3) / 1e12
                                                    if prof["ms"] > 0 else None),
-                     "n_theta": pl.n_theta, "n_theta_dense": 512 * 25 * 512}
+                     "n_theta": pl.n_theta, "n_theta_dense": 512 * 25 * 512,
+                     "wstep": {"kernel": "k_u1_wsteps_seg (fused sector W-step)", "bound": "hbm",
+                               "bytes_per_launch": wst["flops"] / max(wst["launches"], 1),
+                               "bytes_basis": "T1 read once (float32) + split stage-4 operand entries "
+                                              "written once (2 pieces)",
+                               "avg_launch_ms": wst["ms"] / max(wst["launches"], 1),
+                               "achieved": w_gbs, "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                               "frac": w_gbs / peaks["hbm_gbs"] if w_gbs else None,
+                               "peak_source": f"{peak_src} hbm_gbs",
+                               "share_of_product": wst["ms"] / (ms * reps) if ms > 0 else None,
+                               "n_T1": pl.n_T1, "n_A4": pl.n_A4}}
         op.close()
     return {"workload": "Bose-Hubbard J=1 U=4, L=64, N=64, n<=4 (d=5), w=4, chi=512 per bond "
                         "(13 sectors each), two-site H_eff.theta at sites 31,32", **out}

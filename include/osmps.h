@@ -165,7 +165,9 @@ typedef enum {
   OSMPS_KERNEL_GEMM_TC = 0,  /* tcgen05 split-precision GEMM                   */
   OSMPS_KERNEL_GEMM_F64 = 1, /* float64 DMMA GEMM                             */
   OSMPS_KERNEL_GEMM_EMU = 2, /* float64-accurate GEMM on bf16 tensor cores      */
-  OSMPS_KERNEL_SYTRD_PANEL = 3 /* Householder panel of the tridiagonalisation    */
+  OSMPS_KERNEL_SYTRD_PANEL = 3, /* Householder panel of the tridiagonalisation  */
+  OSMPS_KERNEL_U1_WSTEP = 4     /* fused W-step of the U(1) H_eff (its "flops"
+                                 * field carries algorithmic bytes instead)     */
 } osmps_kernel;
 /* Turn recording on (1) or off (0); both clear earlier records. Syncs the device. */
 osmps_status osmps_profile_enable(osmps_ctx* ctx, int enable);
@@ -620,6 +622,12 @@ osmps_status osmps_u1_heff_destroy(osmps_u1_heff* plan);
  * any may be NULL.                                                          */
 osmps_status osmps_u1_heff_sizes(const osmps_u1_heff* plan, int64_t* n_theta, int64_t* n_L,
                                  int64_t* n_R, double* flops);
+/* Element counts of the plan's intermediates: n_t1 float32 entries of the
+ * stage-1 output T1, n_a4 entries of the stage-4 A operand that the fused
+ * W-step writes (each as two split pieces), n_y float64 entries of the
+ * stage-4 output. Host outputs, any may be NULL.                            */
+osmps_status osmps_u1_heff_stage_sizes(const osmps_u1_heff* plan, int64_t* n_t1, int64_t* n_a4,
+                                       int64_t* n_y);
 /* Convert the operator (packed L and R, dense W1 and W2) into the plan's
  * tensor-core operands for `precision` (OSMPS_PREC_BF16X3 or TF32X3; others
  * EUNSUPPORTED). The operator stays prepared until the next prepare.       */

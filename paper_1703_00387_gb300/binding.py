@@ -155,6 +155,7 @@ _SIGS = {
     "osmps_u1_heff_create": (_c.c_int, [_vp, _c.POINTER(U1Desc), _c.POINTER(_vp)]),
     "osmps_u1_heff_destroy": (_c.c_int, [_vp]),
     "osmps_u1_heff_sizes": (_c.c_int, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64), _dp]),
+    "osmps_u1_heff_stage_sizes": (_c.c_int, [_vp, _c.POINTER(_i64), _c.POINTER(_i64), _c.POINTER(_i64)]),
     "osmps_heff_apply_u1": (_c.c_int, [_vp, _vp] + [_vp] * 6 + [_c.c_int, _vp]),
     "osmps_u1_heff_prepare": (_c.c_int, [_vp, _vp] + [_vp] * 4 + [_c.c_int, _vp]),
     "osmps_u1_heff_apply": (_c.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -285,7 +286,7 @@ class Context:
             pass
 
 
-KERNEL = {"gemm_tc": 0, "gemm_f64": 1, "gemm_emu": 2, "sytrd_panel": 3}
+KERNEL = {"gemm_tc": 0, "gemm_f64": 1, "gemm_emu": 2, "sytrd_panel": 3, "u1_wstep": 4}
 
 
 def osmps_profile_enable(ctx, enable=True):
@@ -689,6 +690,10 @@ class U1Heff:
         _check(lib().osmps_u1_heff_sizes(self.ptr, _c.byref(nt), _c.byref(nl), _c.byref(nr),
                                          _c.byref(fl)))
         self.n_theta, self.n_L, self.n_R, self.flops = nt.value, nl.value, nr.value, fl.value
+        t1, a4, ny = _i64(), _i64(), _i64()
+        _check(lib().osmps_u1_heff_stage_sizes(self.ptr, _c.byref(t1), _c.byref(a4), _c.byref(ny)))
+        # intermediates: stage-1 output entries, W-step output entries, stage-4 output entries
+        self.n_T1, self.n_A4, self.n_Y = t1.value, a4.value, ny.value
 
     def close(self):
         if self.ptr:

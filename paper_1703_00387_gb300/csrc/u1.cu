@@ -41,6 +41,7 @@ struct osmps_u1_heff {
   std::vector<int64_t> kp1, kp4;
   int64_t tiles1 = 0, rowsA1 = 0, rowsB1 = 0, Kpl1 = 64, n_T1 = 0;
   int64_t tiles4 = 0, rowsA4 = 0, rowsB4 = 0, Kpl4 = 64, n_Y = 0;
+  int64_t n_A4 = 0;  // stage-4 A entries the W-step writes (sum over rows of the row's K)
   int kind_loaded = -1;    // operand type of the problem table on the device
   int prepared_kind = -1;  // operand type of the prepared L, R operands (-1: none)
   // device memory
@@ -495,6 +496,7 @@ osmps_status u1_build(osmps_u1_heff* h) {
       }
     const int64_t M = (int64_t)ylen.size() - row0;
     if (M == 0 || K == 0) continue;  // rows (if any) stay zero in y
+    h->n_A4 += M * K;
     GroupProblem p = {};
     p.a_row0 = (int)row0;
     p.b_row0 = (int)b4src.size();
@@ -702,11 +704,17 @@ osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* theta
     a.wr = (int)h->wr;
     dim3 grid((unsigned)std::max<int64_t>(1, cdiv(h->Kpl4, 256)), (unsigned)h->rowsA4);
     const size_t sm = wu_smem_bytes(h->wl, h->d1, h->d2, h->wr);
+    // algorithmic bytes: T1 read once (float32), the split operand's entries
+    // written once (two pieces of 2 or 4 bytes)
+    const double wbytes = 4.0 * (double)h->n_T1 +
+                          (KIND == TC_BF16 ? 4.0 : 8.0) * (double)h->n_A4;
+    const int ph = prof_begin(s);
     if (sm <= 48 * 1024)
       k_u1_wsteps_seg<KIND><<<(unsigned)h->rowsA4, 128, sm, s>>>(a, B + h->o_A4);
     else
       k_u1_wsteps<KIND><<<grid, 256, 0, s>>>(a, B + h->o_A4);
     note_launch();
+    prof_end(ph, s, OSMPS_KERNEL_U1_WSTEP, wbytes, 0.0);
     OSMPS_LAUNCH_CHECK();
   }
   // stage 4
@@ -806,6 +814,16 @@ osmps_status osmps_u1_heff_sizes(const osmps_u1_heff* h, int64_t* n_theta, int64
   if (n_L) *n_L = h->n_L;
   if (n_R) *n_R = h->n_R;
   if (flops) *flops = h->flops1 + h->flops4;
+  return OSMPS_OK;
+}
+
+osmps_status osmps_u1_heff_stage_sizes(const osmps_u1_heff* h, int64_t* n_t1, int64_t* n_a4,
+                                       int64_t* n_y) {
+  clear_error();
+  if (!h) return set_error(OSMPS_EINVAL, "osmps_u1_heff_stage_sizes: null handle");
+  if (n_t1) *n_t1 = h->n_T1;
+  if (n_a4) *n_a4 = h->n_A4;
+  if (n_y) *n_y = h->n_Y;
   return OSMPS_OK;
 }
 

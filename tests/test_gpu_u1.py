@@ -177,3 +177,41 @@ def test_u1_prepare_apply_matches_combined(ctx):
     torch.cuda.synchronize()
     assert torch.equal(y1, y2)
     op.close()
+
+
+@pytest.mark.parametrize("prec,piece_bytes", [("bf16x3", 2), ("tf32x3", 4)])
+def test_u1_wstep_profile_counts_its_bytes(ctx, prec, piece_bytes):
+    """The fused W-step's profile record: one launch per product, credited
+    with 4 n_T1 + 2 piece_bytes n_A4 bytes, where n_A4 (the stage-4 A entries)
+    is counted here from its definition: for every right sector j of c2 and
+    every left sector reached by q(c2) - t1 - t2, chi_left rows of K_j = sum
+    over the right channels w2 of the size of the sector q(c2) - q_w2."""
+    left, right, nmax, sites = CASES["multi_tile"]
+    d = nmax + 1
+    Wp = hamiltonians.bose_hubbard(8, 1.0, 4.0, nmax)
+    qp = pu1.channel_charges(Wp)
+    k1, k2 = sites
+    q_wr = qp[k2 + 1]
+    op = pu1.U1Operator(ctx, left, right, d, d, Wp[k1], Wp[k2], qp[k1], q_wr)
+    (ql, chil), (qr, chir) = left, right
+    n_a4 = 0
+    for j, qj in enumerate(qr):
+        K = sum(chir[qr.index(qj - q)] for q in q_wr if (qj - q) in qr)
+        rows = sum(chil[ql.index(qj - t1 - t2)] for t1 in range(d) for t2 in range(d)
+                   if (qj - t1 - t2) in ql)
+        n_a4 += rows * K
+    assert op.plan.n_A4 == n_a4 > 0 and op.plan.n_T1 > 0
+    t = [dev(np.zeros(op.plan.n_L)), dev(Wp[k1]), dev(Wp[k2]), dev(np.zeros(op.plan.n_R)),
+         dev(np.ones(op.plan.n_theta))]
+    y = torch.empty_like(t[4])
+    B.osmps_heff_apply_u1(ctx, op.plan, *t, y, precision=prec)  # warm-up (tile tuning)
+    B.osmps_profile_enable(ctx, True)
+    try:
+        for _ in range(3):
+            B.osmps_heff_apply_u1(ctx, op.plan, *t, y, precision=prec)
+        p = B.osmps_profile_read(ctx, "u1_wstep")
+    finally:
+        B.osmps_profile_enable(ctx, False)
+        op.close()
+    assert p["launches"] == 3 and p["ms"] > 0.0
+    assert p["flops"] == 3 * (4 * op.plan.n_T1 + 2 * piece_bytes * n_a4)
