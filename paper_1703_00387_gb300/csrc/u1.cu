@@ -56,7 +56,7 @@ struct osmps_u1_heff {
   int64_t t_lsec = 0, t_ql = 0, t_qr = 0, t_qwl = 0, t_rowlen = 0, t_t1off = 0, t_rs1 = 0, t_cs = 0,
           t_a1src = 0, t_a1len = 0, t_b1base = 0, t_b1stride = 0, t_b1len = 0, t_a4row = 0,
           t_a4col = 0, t_a4kp = 0, t_b4src = 0, t_b4len = 0, t_ysrc = 0, t_ydst = 0, t_ylen = 0,
-          t_seg = 0, t_pseg = 0;
+          t_seg = 0, t_pseg = 0, t_rowbase = 0, t_c0tab = 0;
   // byte offsets of the buffers inside d_buf
   size_t o_A1 = 0, o_B1 = 0, o_T1 = 0, o_A4 = 0, o_B4 = 0, o_Wc = 0, o_Y = 0;
 };
@@ -177,6 +177,9 @@ struct WstepArgs {
   const int64_t* a4kp;    // per T3 row: {column base of its problem, K, Kp}
   const int64_t* seg;     // column runs of one (w2, sector of c): {w2, sector, first k, length}
   const int64_t* pseg;    // per stage-4 problem (output sector j): {first run, run count}
+  const int64_t* rowbase; // [r wl + w]: T1 offset of T3 row r's channel-w row, or -1
+  const int64_t* c0tab;   // [ia2 nin + (w d1 + s1) d2 + s2]: first T1 column of (s1, s2)
+                          // in the ket sector q(a2) - q_w, or -1
   int64_t rows, Kpl, qmin, nq;
   int d1, d2, wl, wr;
 };
@@ -247,33 +250,15 @@ __global__ void __launch_bounds__(128) k_u1_wsteps_seg(WstepArgs a, void* __rest
   float* twt = reinterpret_cast<float*>(reinterpret_cast<int64_t*>(wsh + wr * nin + ((wr * nin) & 1)) +
                                         (blockDim.x >> 5) * nterm_max) +
                (threadIdx.x >> 5) * nterm_max;
-  const int64_t j = a.a4row[4 * r], t12 = a.a4row[4 * r + 1], ia2 = a.a4row[4 * r + 2],
-                a2 = a.a4row[4 * r + 3];
+  // the row's lookups come from tables the plan resolved on the host (two
+  // dependent loads instead of a chain through the sector tables)
+  const int64_t j = a.a4row[4 * r], t12 = a.a4row[4 * r + 1], ia2 = a.a4row[4 * r + 2];
   const int64_t K = a.a4kp[3 * r + 1], Kp = a.a4kp[3 * r + 2];
-  const int64_t qa2 = a.ql[ia2];
   for (int w = threadIdx.x; w < wl; w += blockDim.x) {
-    const int64_t qa = qa2 - a.qwl[w];
-    int64_t b = -1;
-    if (qa >= a.qmin && qa < a.qmin + a.nq) {
-      const int64_t ia = a.lsec[qa - a.qmin];
-      if (ia >= 0) {
-        const int64_t rs = a.rs1[ia * wl + w];
-        if (rs >= 0) b = a.t1off[ia] + (rs + a2) * a.rowlen[ia];
-      }
-    }
-    base[w] = b;
-    qaw[w] = qa;
+    base[w] = a.rowbase[r * wl + w];
+    qaw[w] = a.ql[ia2] - a.qwl[w];
   }
-  for (int i = threadIdx.x; i < nin; i += blockDim.x) {
-    const int w = i / (d1 * d2), ss = i % (d1 * d2);
-    const int64_t qa = qa2 - a.qwl[w];
-    int64_t c0 = -1;
-    if (qa >= a.qmin && qa < a.qmin + a.nq) {
-      const int64_t ia = a.lsec[qa - a.qmin];
-      if (ia >= 0) c0 = a.cs[ia * d1 * d2 + ss];
-    }
-    c0t[i] = c0;
-  }
+  for (int i = threadIdx.x; i < nin; i += blockDim.x) c0t[i] = a.c0tab[ia2 * nin + i];
   for (int i = threadIdx.x; i < wr * nin; i += blockDim.x) wsh[i] = a.Wc[t12 * wr * nin + i];
   __syncthreads();
   for (int64_t k = K + threadIdx.x; k < Kp; k += blockDim.x)  // zero padding
@@ -517,6 +502,30 @@ osmps_status u1_build(osmps_u1_heff* h) {
   }
   h->rowsA4 = (int64_t)ylen.size();
   h->rowsB4 = (int64_t)b4src.size();
+  // the W-step's per-row and per-sector lookups, resolved once: for T3 row r
+  // (sector ia2 of a2, a2 within it) and left channel w, the T1 row of the
+  // ket sector q(a2) - q_w; for sector ia2, the first T1 column of (s1, s2)
+  auto ket_sector = [&](int64_t qa) {
+    return (qa >= h->qmin && qa < h->qmin + h->nq) ? lsec[qa - h->qmin] : (int64_t)-1;
+  };
+  const int64_t nin = wl * d1 * d2;
+  std::vector<int64_t> rowbase((size_t)std::max<int64_t>(h->rowsA4 * wl, 1), -1);
+  for (int64_t r = 0; r < h->rowsA4; ++r) {
+    const int64_t ia2 = a4row[4 * r + 2], a2 = a4row[4 * r + 3];
+    for (int64_t w = 0; w < wl; ++w) {
+      const int64_t ia = ket_sector(h->ql[ia2] - h->qwl[w]);
+      if (ia < 0) continue;
+      const int64_t rs = rs1[ia * wl + w];
+      if (rs >= 0) rowbase[r * wl + w] = t1off[ia] + (rs + a2) * rowlen[ia];
+    }
+  }
+  std::vector<int64_t> c0tab((size_t)std::max<int64_t>(nl * nin, 1), -1);
+  for (int64_t ia2 = 0; ia2 < nl; ++ia2)
+    for (int64_t i = 0; i < nin; ++i) {
+      const int64_t w = i / (d1 * d2), ss = i % (d1 * d2);
+      const int64_t ia = ket_sector(h->ql[ia2] - h->qwl[w]);
+      if (ia >= 0) c0tab[ia2 * nin + i] = cs[ia * d1 * d2 + ss];
+    }
   h->Kpl4 = kpmax4;
   h->n_Y = nY;
   if (h->rowsA1 > (1 << 30) || h->rowsB1 > (1 << 30) || h->rowsA4 > 65535 || nth > ((int64_t)1 << 40))
@@ -541,6 +550,8 @@ osmps_status u1_build(osmps_u1_heff* h) {
   h->t_a4col = put(a4col);
   h->t_a4kp = put(a4kp);
   h->t_seg = put(seg);
+  h->t_rowbase = put(rowbase);
+  h->t_c0tab = put(c0tab);
   h->t_pseg = put(pseg);
   h->t_b4src = put(b4src);
   h->t_b4len = put(b4len);
@@ -694,6 +705,8 @@ osmps_status u1_apply_kind(osmps_ctx* ctx, osmps_u1_heff* h, const double* theta
     a.a4kp = T + h->t_a4kp;
     a.seg = T + h->t_seg;
     a.pseg = T + h->t_pseg;
+    a.rowbase = T + h->t_rowbase;
+    a.c0tab = T + h->t_c0tab;
     a.rows = h->rowsA4;
     a.Kpl = h->Kpl4;
     a.qmin = h->qmin;
