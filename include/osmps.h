@@ -318,6 +318,12 @@ osmps_status osmps_selftest_wait_timeout(osmps_ctx* ctx, int which, double limit
  * of n elements). Results must equal the IEEE conversions bit for bit.    */
 osmps_status osmps_selftest_convert(osmps_ctx* ctx, const double* x64, float* y32,
                                     const float* x32, double* y64, int64_t n, void* stream);
+/* Test support: the bf16 rounding of n doubles (device arrays) by the
+ * integer-field route the U(1) operand split uses (y_int) and by CUDA's
+ * __double2bfloat16 (y_hw), as raw 16-bit patterns. EINVAL for a null
+ * pointer with n > 0 or n < 0.                                              */
+osmps_status osmps_selftest_bf16(osmps_ctx* ctx, const double* x, uint16_t* y_int, uint16_t* y_hw,
+                                 int64_t n, void* stream);
 
 /* Environment update (Sec. 3.4: the fixed sites are contracted into L and R
  * one site at a time).

@@ -110,6 +110,7 @@ _SIGS = {
     "osmps_sytrd": (_c.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "osmps_selftest_wait_timeout": (_c.c_int, [_vp, _c.c_int, _c.c_double, _vp]),
     "osmps_selftest_convert": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "osmps_selftest_bf16": (_c.c_int, [_vp, _vp, _vp, _vp, _i64, _vp]),
     "osmps_gemm_grouped": (_c.c_int, [_vp, _vp, _i64, _vp, _i64, _vp]),
     "osmps_copy_list": (_c.c_int, [_vp, _c.POINTER(CopyDesc), _i64, _vp]),
     "osmps_sym_eig_top": (_c.c_int, [_vp, _vp, _i64, _i64, _dp, _vp, _vp]),
@@ -770,6 +771,17 @@ def osmps_selftest_convert(ctx, x64, x32, stream=None):
                                         _vp(x32.data_ptr()), _dev(y64, "y64"), x64.numel(),
                                         _stream(stream)))
     return y32, y64
+
+
+def osmps_selftest_bf16(ctx, x, stream=None):
+    """(integer-field, CUDA) bf16 roundings of the float64 device tensor x as
+    int16 tensors of raw bit patterns."""
+    import torch
+    yi = torch.empty(x.numel(), dtype=torch.int16, device=x.device)
+    yh = torch.empty(x.numel(), dtype=torch.int16, device=x.device)
+    _check(lib().osmps_selftest_bf16(ctx.ptr, _dev(x, "x"), _vp(yi.data_ptr()), _vp(yh.data_ptr()),
+                                     x.numel(), _stream(stream)))
+    return yi, yh
 
 
 def osmps_gemm_grouped(ctx, outs, terms, stream=None):

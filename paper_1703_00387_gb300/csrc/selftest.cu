@@ -64,10 +64,36 @@ __global__ void k_selftest_convert(const double* __restrict__ x64, float* __rest
   }
 }
 
+__global__ void k_selftest_bf16(const double* __restrict__ x, uint16_t* __restrict__ y_int,
+                                uint16_t* __restrict__ y_hw, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    y_int[i] = __bfloat16_as_ushort(f64_to_bf16_rn(x[i]));
+    y_hw[i] = __bfloat16_as_ushort(__double2bfloat16(x[i]));
+  }
+}
+
 }  // namespace
 }  // namespace osmps
 
 using namespace osmps;
+
+extern "C" osmps_status osmps_selftest_bf16(osmps_ctx* ctx, const double* x, uint16_t* y_int,
+                                            uint16_t* y_hw, int64_t n, void* stream) {
+  clear_error();
+  if (!ctx || (n > 0 && (!x || !y_int || !y_hw)))
+    return set_error(OSMPS_EINVAL, "osmps_selftest_bf16: null argument");
+  if (n < 0) return set_error(OSMPS_EINVAL, "osmps_selftest_bf16: n=%lld", (long long)n);
+  if (n == 0) return OSMPS_OK;
+  OSMPS_CUDA(cudaSetDevice(ctx->device));
+  CtxScope scope_(ctx);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  k_selftest_bf16<<<blocks, 256, 0, s>>>(x, y_int, y_hw, n);
+  note_launch();
+  OSMPS_LAUNCH_CHECK();
+  return OSMPS_OK;
+}
 
 extern "C" osmps_status osmps_selftest_convert(osmps_ctx* ctx, const double* x64, float* y32,
                                                const float* x32, double* y64, int64_t n, void* stream) {

@@ -27,6 +27,7 @@
 #include <atomic>
 
 #include "common.cuh"
+#include "ieee.cuh"
 
 struct osmps_u1_heff {
   osmps_ctx* ctx = nullptr;
@@ -89,19 +90,22 @@ __device__ __forceinline__ void store_split_f(void* dst, int64_t off_hi, int64_t
   }
 }
 
-// Split of a float64 value: hi = round(x), lo = round(x - hi) in the operand type.
+// Split of a float64 value: hi = round(x), lo = round(x - hi) in the operand
+// type. The roundings and the widening of hi use the integer fields
+// (ieee.cuh); only the exact subtraction x - hi runs on GB300's narrow
+// float64 pipe. Bit for bit the split of the hardware conversions.
 template <int KIND>
 __device__ __forceinline__ void store_split_d(void* dst, int64_t off_hi, int64_t Kpl, double x) {
   if (KIND == TC_BF16) {
-    const __nv_bfloat16 h = __double2bfloat16(x);
-    const __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
+    const __nv_bfloat16 h = f64_to_bf16_rn(x);
+    const __nv_bfloat16 l = f64_to_bf16_rn(x - f32_to_f64(__bfloat162float(h)));
     reinterpret_cast<__nv_bfloat16*>(dst)[off_hi] = h;
     reinterpret_cast<__nv_bfloat16*>(dst)[off_hi + Kpl] = l;
   } else {
     uint32_t h, l;
-    const float xf = (float)x;
+    const float xf = f64_to_f32_rn(x);
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(xf));
-    const float r = (float)(x - (double)__uint_as_float(h));
+    const float r = f64_to_f32_rn(x - f32_to_f64(__uint_as_float(h)));
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
     reinterpret_cast<uint32_t*>(dst)[off_hi] = h;
     reinterpret_cast<uint32_t*>(dst)[off_hi + Kpl] = l;

@@ -60,3 +60,24 @@ def test_conversions_match_ieee(ctx):
     nan = np.isnan(r64)
     assert np.isnan(g64[nan]).all()
     np.testing.assert_array_equal(g64[~nan].view(np.uint64), r64[~nan].view(np.uint64))
+
+
+def test_bf16_rounding_matches_cuda(ctx):
+    """The U(1) operand split rounds float64 to bf16 through float32 rounded
+    to odd (integer fields): bit for bit CUDA's __double2bfloat16 on random
+    values over the float range and beyond, on values exactly halfway
+    between two bf16 numbers (both parities, which a plain double rounding
+    through float would get wrong when float rounds onto the halfway point),
+    carries into the exponent, zeros, infinities, subnormals and NaN."""
+    rng = np.random.default_rng(1)
+    n = 1 << 20
+    x = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-140, 135, n)) * rng.choice([-1.0, 1.0], n)
+    edge = [0.0, -0.0, np.inf, -np.inf, np.nan, 1e-300, -1e-300, 1e300, 3.4e38, -3.4e38,
+            float(np.finfo(np.float32).tiny), float(np.finfo(np.float32).tiny) / 3]
+    for k in range(8):
+        m = 1.0 + (2 * k + 1) * 2.0 ** -8  # halfway between bf16 neighbours
+        edge += [m, -m, m + 2.0 ** -40, m - 2.0 ** -40, m + 2.0 ** -52, m * 2.0 ** 100]
+    edge += [2.0 - 2.0 ** -9, 2.0 - 2.0 ** -30, 1.0 + 2.0 ** -8 + 2.0 ** -33]
+    x = np.concatenate([x, np.array(edge)])
+    yi, yh = B.osmps_selftest_bf16(ctx, torch.from_numpy(x).cuda())
+    np.testing.assert_array_equal(yi.cpu().numpy(), yh.cpu().numpy())
