@@ -160,6 +160,42 @@ class Copy:
         self.alpha = float(alpha)
 
 
+class BlockBudget:
+    """At most `total` blocks of cooperative launches in flight at once, held
+    by threads that acquire a number of blocks before their solve and
+    release it after. A cooperative grid's blocks must all be resident: with
+    one block per SM counted, grids running together never wait on each
+    other for room, only on kernels that end on their own."""
+
+    def __init__(self, total):
+        import threading
+        self.total, self.busy = int(total), 0
+        self._cond = threading.Condition()
+
+    def acquire(self, need):
+        if need > self.total:
+            raise ValueError(f"{need} blocks requested of a budget of {self.total}")
+        with self._cond:
+            self._cond.wait_for(lambda: self.busy + need <= self.total)
+            self.busy += need
+
+    def release(self, need):
+        with self._cond:
+            self.busy -= need
+            self._cond.notify_all()
+
+
+def coop_blocks(n, sms, solver=None):
+    """Blocks of the Householder panel's cooperative launch for an n x n
+    eigenproblem: min(SMs, 160, ceil(n / 8)) on the library's own route
+    (from n = 64 under 'auto', from n = 2 under 'tridiag'), 0 where cuSOLVER
+    solves it (no cooperative launch)."""
+    own_from = {None: 64, "auto": 64, "tridiag": 2}.get(solver)
+    if own_from is None or n < own_from:
+        return 0
+    return max(1, min(sms, 160, (n + 7) // 8))
+
+
 class DeviceExecutor:
     """Runs operation records on the GPU through the library (buffers are
     float64 CUDA tensors). eig_workers: how many sector eigensolves of a
@@ -223,17 +259,13 @@ class DeviceExecutor:
         from concurrent.futures import ThreadPoolExecutor
         if self._pool is None:
             self._tls = threading.local()
-            self._cond = threading.Condition()
-            self._busy = [0]
+            self._lock = threading.Lock()
+            self._budget = BlockBudget(self._sms)
             self._workers = []  # (context, stream) of every worker thread
             self._pool = ThreadPoolExecutor(max_workers=self.eig_workers)
-        budget = self._sms
         torch = self.torch
         ready = torch.cuda.Event()
         ready.record()  # the Gram matrices, written on this thread's stream
-
-        def blocks(n):
-            return 0 if n < 64 else max(1, min(budget, 160, (n + 7) // 8))
 
         def run(job):
             G, n, nev = job
@@ -243,12 +275,10 @@ class DeviceExecutor:
                 if self.eig_solver is not None:
                     tl.ctx.set_eig_solver(self.eig_solver)
                 tl.stream = torch.cuda.Stream()
-                with self._cond:
+                with self._lock:
                     self._workers.append((tl.ctx, tl.stream))
-            need = blocks(n)
-            with self._cond:
-                self._cond.wait_for(lambda: self._busy[0] + need <= budget)
-                self._busy[0] += need
+            need = coop_blocks(n, self._sms, self.eig_solver)
+            self._budget.acquire(need)
             try:
                 tl.stream.wait_event(ready)
                 Y = torch.empty(max(nev * n, 1), dtype=torch.float64, device="cuda")
@@ -256,9 +286,7 @@ class DeviceExecutor:
                                          stream=tl.stream)  # synchronises tl.stream
                 return ev, Y
             finally:
-                with self._cond:
-                    self._busy[0] -= need
-                    self._cond.notify_all()
+                self._budget.release(need)
 
         order = sorted(range(len(jobs)), key=lambda i: -jobs[i][1])
         futures = {i: self._pool.submit(run, jobs[i]) for i in order}

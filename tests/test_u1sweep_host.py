@@ -261,3 +261,150 @@ def test_xxz_sweep_orchestration_with_empty_field_channel():
     idx = np.nonzero(n_of == N)[0]
     e0 = np.linalg.eigvalsh(H[np.ix_(idx, idx)])[0]
     assert abs(res["energy"] - e0) <= 1e-10 * abs(e0)
+
+
+class _Buf:
+    """A device buffer stand-in that only knows its length."""
+
+    def __init__(self, n):
+        self.n = max(int(n), 1)
+
+
+class BoundsExecutor:
+    """Checks every operation a sweep hands to the library, without running
+    it: each strided view (output, A and B operands of every term, copy
+    source and destination, the Gram matrix of every eigensolve) lies inside
+    its buffer, a grouped stage writes no buffer it reads, and the outputs of
+    one stage never overlap (the grouped GEMM runs them concurrently)."""
+
+    def __init__(self):
+        self.rng = np.random.default_rng(0)
+        self.views = 0
+
+    @staticmethod
+    def _span(off, rows, cols, rs, cs):
+        assert rows >= 1 and cols >= 1
+        lo = off + min(0, (rows - 1) * rs) + min(0, (cols - 1) * cs)
+        hi = off + max(0, (rows - 1) * rs) + max(0, (cols - 1) * cs)
+        return lo, hi
+
+    def _check(self, ref, rows, cols, rs, cs):
+        buf, off = ref
+        lo, hi = self._span(int(off), rows, cols, rs, cs)
+        assert 0 <= lo and hi < buf.n, (lo, hi, buf.n)
+        self.views += 1
+
+    def empty(self, n):
+        return _Buf(n)
+
+    def upload(self, a):
+        return _Buf(np.size(a))
+
+    def download(self, buf, n):
+        assert n <= buf.n
+        return np.ones(n)
+
+    def sync(self):
+        pass
+
+    def norm2(self, buf, n):
+        assert n <= buf.n
+        return 1.0
+
+    def ground(self, Lk, W1, W2, Rk, theta, left, right, d, q_wl, q_wr, wm, precision, tol, max_iter):
+        assert int(ou1.theta_mask(left.charges(), right.charges(), d, d).sum()) <= theta.n
+        return -1.0, 1
+
+    def products(self, ops):
+        written, read = set(), set()
+        rows = []
+        for o in ops:
+            self._check(o.C, o.M, o.N, o.scm, o.scn)
+            written.add(id(o.C[0]))
+            if o.scn == 1:
+                off = int(o.C[1])
+                rows += [(id(o.C[0]), off + r * o.scm, off + r * o.scm + o.N) for r in range(o.M)]
+            for t in o.terms:
+                assert t.K >= 1
+                self._check(t.A, o.M, t.K, t.sam, t.sak)
+                self._check(t.B, t.K, o.N, t.sbk, t.sbn)
+                read.update((id(t.A[0]), id(t.B[0])))
+        assert not (written & read)
+        rows.sort()
+        for (b0, _, e0), (b1, s1, _) in zip(rows, rows[1:]):
+            assert b0 != b1 or e0 <= s1  # output rows of one stage are disjoint
+
+    def copies(self, ops):
+        for c in ops:
+            if c.src is not None:
+                self._check(c.src, c.rows, c.cols, c.srs, c.scs)
+            self._check(c.dst, c.rows, c.cols, c.drs, 1)
+
+    def eig_top_many(self, jobs):
+        out = []
+        for G, n, nev in jobs:
+            assert 1 <= nev <= n and n * n <= G.n
+            out.append((np.sort(np.exp(-0.05 * np.arange(nev)) * self.rng.uniform(0.5, 1.0)), _Buf(nev * n)))
+        tot = sum(e.sum() for e, _ in out)
+        return [(e / tot, y) for e, y in out]
+
+
+@pytest.mark.parametrize("model", ["bose_hubbard", "xxz"])
+def test_sweep_block_lists_stay_inside_their_buffers(model):
+    """A whole sweep's block operations (canonicalisation, theta, split with
+    truncation at chi_max, both environment updates, the final energy) at
+    bond dimensions where the sectors span many blocks, checked for bounds
+    and overlaps before they could ever reach a GPU."""
+    if model == "bose_hubbard":
+        L, d, N = 12, 4, 12
+        W = hamiltonians.bose_hubbard(L, 1.0, 4.0, d - 1)
+    else:
+        L, d, N = 16, 2, 8
+        W = hamiltonians.xxz(L, 1.0, 0.7, 0.0)
+    ex = BoundsExecutor()
+    mps = us.random_u1_mps(ex, L, d, N, chi=32, seed=4)
+    res = us.u1_sweep(mps, W, n_sweeps=1, chi_max=48, eps_local=0.0)
+    assert res["max_chi"] <= 48 and res["max_chi"] > 16
+    assert ex.views > 10000
+
+
+def test_coop_blocks_follow_the_panel_grid():
+    """The budget counts the panel grid the library launches: ceil(n / 8)
+    blocks, at most one per SM and at most 160, only where its own route
+    solves (auto: n >= 64; tridiag: n >= 2; cuSOLVER: never)."""
+    assert us.coop_blocks(63, 152) == 0 and us.coop_blocks(64, 152) == 8
+    assert us.coop_blocks(195, 152) == 25 and us.coop_blocks(2048, 152) == 152
+    assert us.coop_blocks(4096, 200) == 160
+    assert us.coop_blocks(10, 152, "tridiag") == 2 and us.coop_blocks(1000, 152, "cusolver") == 0
+
+
+def test_block_budget_never_oversubscribes():
+    """Threads acquiring random block counts (up to the whole budget) hold
+    at most the budget between them at any time, and all of them finish."""
+    import threading
+    budget = us.BlockBudget(152)
+    state = {"held": 0, "peak": 0}
+    lock = threading.Lock()
+
+    def worker(seed):
+        rng = np.random.default_rng(seed)
+        for _ in range(300):
+            need = int(rng.choice([0, 8, 25, 64, 152]))
+            budget.acquire(need)
+            with lock:
+                state["held"] += need
+                state["peak"] = max(state["peak"], state["held"])
+                assert state["held"] <= 152
+            with lock:
+                state["held"] -= need
+            budget.release(need)
+
+    threads = [threading.Thread(target=worker, args=(s,)) for s in range(8)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=60)
+    assert not any(t.is_alive() for t in threads)
+    assert budget.busy == 0 and 0 < state["peak"] <= 152
+    with pytest.raises(ValueError):
+        budget.acquire(153)
